@@ -1,0 +1,793 @@
+/*
+ * pp_oracle.c -- plain, slow, FP64 CPU oracle for the pair-number hot path of
+ * "Pulse shape optimization for electron-positron production in rotating
+ * fields" (Fillion-Gourdeau, Hebenstreit, Gagnon, MacLean; arXiv 1704.08919).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path links, loads or calls
+ * this file: it is used by tests/, by __graft_entry__.smoke() and by the
+ * cpu_baseline / reference legs of bench.py.  It shares no source, header,
+ * table or helper with the CUDA library.
+ *
+ * Every routine follows a passage of the paper, step by step, in FP64 with no
+ * blocking, fusion or reordering:
+ *   - B-spline spectral model ............ Sec. III, Eqs. (coeff_basis_E/phi),
+ *                                           Cox-de Boor recursion, clamped knots
+ *   - multimode field, potential, fluence . Sec. III, Eqs. (field), (energy);
+ *                                           DE renormalisation, Sec. IV.B
+ *   - momentum-space Dirac equation ...... Sec. II.A, Eqs. (kin_mom), (free_spin1),
+ *                                           (wf_init), (dirac_eq_mom)
+ *   - pair density ....................... Sec. II.A, Eq. (pair_prod_homo)
+ *   - total density (momentum integral) .. Sec. II.A last paragraph, Eq. (opt_prob)
+ *   - quantum kinetic equation (6 comp.) . Sec. II.B, Eqs. (qke), (matrix)
+ *   - differential evolution ............. Sec. IV.B, DE/rand/1/bin steps 1-4
+ *
+ * Compile with -ffp-contract=off so that every product and sum is rounded as
+ * written.  Units: m = e = c = hbar = 1 (so e*E is written E).
+ */
+#define _GNU_SOURCE
+#include <complex.h>
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <unistd.h>
+
+typedef double complex cplx;
+
+#define ORC_OK 0
+#define ORC_ERR_ARG 1
+#define ORC_ERR_DEGENERATE 4
+
+/* ------------------------------------------------------------------------- */
+/* B-spline basis, Sec. III                                                  */
+/* ------------------------------------------------------------------------- */
+
+/* Clamped knot vector: `order` copies of w_min, equidistant interior
+ * breakpoints, `order` copies of w_max.  n = K - order + 2 breakpoints
+ * (including both ends), K + order knots in total (N_s = n + k - 2). */
+static int knot_vector(int K, int order, double wmin, double wmax, double *t)
+{
+    int n = K - order + 2;
+    if (n < 2)
+        return ORC_ERR_ARG;
+    for (int i = 0; i < order; i++)
+        t[i] = wmin;
+    for (int i = 1; i < n - 1; i++)
+        t[order - 1 + i] = wmin + (wmax - wmin) * (double)i / (double)(n - 1);
+    for (int i = 0; i < order; i++)
+        t[K + i] = wmax;
+    return ORC_OK;
+}
+
+/* B_i(w), i = 0..K-1, by the Cox-de Boor recursion of Sec. III.  The order-1
+ * functions are indicators of [t_i, t_{i+1}); reading: the last non-empty
+ * interval is closed on the right so that the basis does not vanish at w_max.
+ * Terms with a zero-length denominator are zero. */
+int orc_bspline_basis(int K, int order, double wmin, double wmax, double w, double *B)
+{
+    if (K < 1 || order < 1 || K < order || !(wmax > wmin) || !B)
+        return ORC_ERR_ARG;
+    int nk = K + order;
+    double *t = malloc(sizeof(double) * nk);
+    double *b = malloc(sizeof(double) * nk);
+    knot_vector(K, order, wmin, wmax, t);
+    int last = -1; /* index of the last non-empty interval */
+    for (int i = 0; i < nk - 1; i++)
+        if (t[i] < t[i + 1])
+            last = i;
+    for (int i = 0; i < nk - 1; i++) {
+        int inside = (t[i] <= w && w < t[i + 1]);
+        if (i == last && w == t[i + 1])
+            inside = 1;
+        b[i] = inside ? 1.0 : 0.0;
+    }
+    for (int r = 2; r <= order; r++) {
+        for (int i = 0; i < nk - r; i++) {
+            double left = 0.0, right = 0.0;
+            double d1 = t[i + r - 1] - t[i];
+            double d2 = t[i + r] - t[i + 1];
+            if (d1 > 0.0)
+                left = (w - t[i]) / d1 * b[i];
+            if (d2 > 0.0)
+                right = (t[i + r] - w) / d2 * b[i + 1];
+            b[i] = left + right;
+        }
+    }
+    for (int i = 0; i < K; i++)
+        B[i] = b[i];
+    free(t);
+    free(b);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Spectral sampling and field synthesis, Sec. III                           */
+/* ------------------------------------------------------------------------- */
+
+/* Modes Omega_j = j * dOmega, dOmega = 2 pi / T, for every integer j >= 1 with
+ * w_min <= Omega_j <= w_max (the j = 0 DC term is removed).  Returns the number
+ * of modes and the first j. */
+int orc_mode_range(double wmin, double wmax, double T, int *j_first)
+{
+    double dw = 2.0 * M_PI / T;
+    int j0 = (int)ceil(wmin / dw - 1e-12);
+    if (j0 < 1)
+        j0 = 1;
+    int j1 = (int)floor(wmax / dw + 1e-12);
+    if (j_first)
+        *j_first = j0;
+    return j1 >= j0 ? j1 - j0 + 1 : 0;
+}
+
+/* Parameter layout of one candidate: [a^E_x (K), a^phi_x (K), a^E_y (K), a^phi_y (K)].
+ * Fills Omega[M], amp[2][M] = E~_l(Omega_j), phase[2][M] = phi_l(Omega_j). */
+int orc_spectrum(const double *params, int K, int order, double wmin, double wmax, double T,
+                 double *Omega, double *amp, double *phase)
+{
+    int j0;
+    int M = orc_mode_range(wmin, wmax, T, &j0);
+    if (M <= 0)
+        return -ORC_ERR_ARG;
+    double dw = 2.0 * M_PI / T;
+    double *B = malloc(sizeof(double) * K);
+    for (int m = 0; m < M; m++) {
+        double W = (double)(j0 + m) * dw;
+        Omega[m] = W;
+        int rc = orc_bspline_basis(K, order, wmin, wmax, W, B);
+        if (rc) {
+            free(B);
+            return -rc;
+        }
+        for (int l = 0; l < 2; l++) {
+            const double *aE = params + (2 * l) * K;
+            const double *aP = params + (2 * l + 1) * K;
+            double e = 0.0, p = 0.0;
+            for (int i = 0; i < K; i++) {
+                e += aE[i] * B[i];
+                p += aP[i] * B[i];
+            }
+            amp[l * M + m] = e;
+            phase[l * M + m] = p;
+        }
+    }
+    free(B);
+    return M;
+}
+
+/* Field of Eq. (field) with g = 1 over one period t in [-T/2, T/2], the
+ * potential A_l(t) = -int_{-T/2}^t E_l, and the global renormalisation of the
+ * DE update (Sec. IV.B) to the fluence U of Eq. (energy).  Without the DC term
+ * the potential is periodic, so A(-T/2) = A(T/2) = 0.  The fluence of the
+ * unscaled field over one period is (T/2) sum_{l,j} E~_{l,j}^2 (orthogonality
+ * of the modes); the field is scaled by s = sqrt(U / U_raw).
+ *
+ * Output: A[c][2][ld] (row 0 = A_x, row 1 = A_y) on the half-step grid
+ * t_k = -T/2 + k*T/(2 n_steps), k = 0..2 n_steps; E likewise (may be NULL);
+ * scale[c] = s (may be NULL).  A zero-fluence candidate gets A = E = 0,
+ * scale = 0 and makes the call return ORC_ERR_DEGENERATE. */
+int orc_synth_field(const double *params, int ncand, int K, int order, double wmin, double wmax,
+                    double T, double U, int n_steps, int ld, double *A, double *E, double *scale)
+{
+    if (ncand < 0 || n_steps < 1 || ld < 2 * n_steps + 1 || !(T > 0) || !(U > 0))
+        return ORC_ERR_ARG;
+    int M = orc_mode_range(wmin, wmax, T, NULL);
+    if (M <= 0)
+        return ORC_ERR_ARG;
+    double *Om = malloc(sizeof(double) * M);
+    double *amp = malloc(sizeof(double) * 2 * M);
+    double *ph = malloc(sizeof(double) * 2 * M);
+    int status = ORC_OK;
+    int nsamp = 2 * n_steps + 1;
+    double h = T / (2.0 * n_steps);
+    double ti = -0.5 * T;
+    for (int c = 0; c < ncand; c++) {
+        int rc = orc_spectrum(params + (size_t)c * 4 * K, K, order, wmin, wmax, T, Om, amp, ph);
+        if (rc < 0) {
+            status = -rc;
+            break;
+        }
+        double Uraw = 0.0;
+        for (int q = 0; q < 2 * M; q++)
+            Uraw += amp[q] * amp[q];
+        Uraw *= 0.5 * T;
+        double s = Uraw > 0.0 ? sqrt(U / Uraw) : 0.0;
+        if (!(Uraw > 0.0))
+            status = ORC_ERR_DEGENERATE;
+        if (scale)
+            scale[c] = s;
+        for (int l = 0; l < 2; l++) {
+            double *Arow = A + ((size_t)c * 2 + l) * ld;
+            double *Erow = E ? E + ((size_t)c * 2 + l) * ld : NULL;
+            for (int k = 0; k < nsamp; k++) {
+                double t = ti + (double)k * h;
+                double a = 0.0, e = 0.0;
+                for (int m = 0; m < M; m++) {
+                    double Ej = amp[l * M + m], Pj = ph[l * M + m], W = Om[m];
+                    e += Ej * cos(W * t - Pj);
+                    a += Ej * (sin(W * t - Pj) - sin(W * ti - Pj)) / W;
+                }
+                Arow[k] = -s * a;
+                if (Erow)
+                    Erow[k] = s * e;
+            }
+        }
+    }
+    free(Om);
+    free(amp);
+    free(ph);
+    return status;
+}
+
+/* ------------------------------------------------------------------------- */
+/* A test field: E(t) = E0 exp(-t^2/tau^2) (cos w t, sin w t, 0), A(t0) = 0,  */
+/* A(t) = -int_{t0}^t E.  The integral has no elementary closed form; it is  */
+/* accumulated interval by interval with 10-point Gauss-Legendre quadrature. */
+/* ------------------------------------------------------------------------- */
+
+/* Gauss-Legendre nodes/weights on [-1,1] by Newton iteration on P_n. */
+static void gauss_legendre(int n, double *x, double *w)
+{
+    for (int i = 0; i < n; i++) {
+        double z = cos(M_PI * (i + 0.75) / (n + 0.5));
+        double dp = 0.0;
+        for (int it = 0; it < 100; it++) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; k++) {
+                double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-16)
+                break;
+        }
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+static void gauss_rot_E(double E0, double w, double tau, double t, double *ex, double *ey)
+{
+    double g = E0 * exp(-(t * t) / (tau * tau));
+    *ex = g * cos(w * t);
+    *ey = g * sin(w * t);
+}
+
+/* Samples k = 0..nsamp-1 at t = t0 + k h.  A[2][nsamp]; E, Edot likewise or NULL. */
+void orc_gaussian_rotating_field(double E0, double w, double tau, double t0, double h, int nsamp,
+                                 double *A, double *E, double *Edot)
+{
+    double gx[10], gw[10];
+    gauss_legendre(10, gx, gw);
+    double ax = 0.0, ay = 0.0;
+    for (int k = 0; k < nsamp; k++) {
+        double t = t0 + (double)k * h;
+        if (k > 0) {
+            double a = t0 + (double)(k - 1) * h, mid = a + 0.5 * h;
+            double sx = 0.0, sy = 0.0;
+            for (int q = 0; q < 10; q++) {
+                double ex, ey;
+                gauss_rot_E(E0, w, tau, mid + 0.5 * h * gx[q], &ex, &ey);
+                sx += gw[q] * ex;
+                sy += gw[q] * ey;
+            }
+            ax -= 0.5 * h * sx;
+            ay -= 0.5 * h * sy;
+        }
+        A[k] = ax;
+        A[nsamp + k] = ay;
+        double ex, ey;
+        gauss_rot_E(E0, w, tau, t, &ex, &ey);
+        if (E) {
+            E[k] = ex;
+            E[nsamp + k] = ey;
+        }
+        if (Edot) {
+            double dg = -2.0 * t / (tau * tau);
+            Edot[k] = dg * ex - w * ey;
+            Edot[nsamp + k] = dg * ey + w * ex;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Momentum-space Dirac equation, Sec. II.A                                  */
+/* ------------------------------------------------------------------------- */
+
+/* Dirac representation: alpha_i = sigma_x (x) sigma_i, beta = sigma_z (x) 1. */
+static void kron2(const cplx a[2][2], const cplx b[2][2], cplx out[4][4])
+{
+    for (int i = 0; i < 2; i++)
+        for (int j = 0; j < 2; j++)
+            for (int k = 0; k < 2; k++)
+                for (int l = 0; l < 2; l++)
+                    out[2 * i + k][2 * j + l] = a[i][j] * b[k][l];
+}
+
+typedef struct {
+    cplx alpha[3][4][4];
+    cplx beta[4][4];
+} dirac_mats;
+
+static void make_dirac_mats(dirac_mats *D)
+{
+    const cplx s0[2][2] = {{1, 0}, {0, 1}};
+    const cplx sx[2][2] = {{0, 1}, {1, 0}};
+    const cplx sy[2][2] = {{0, -I}, {I, 0}};
+    const cplx sz[2][2] = {{1, 0}, {0, -1}};
+    kron2(sx, sx, D->alpha[0]);
+    kron2(sx, sy, D->alpha[1]);
+    kron2(sx, sz, D->alpha[2]);
+    kron2(sz, s0, D->beta);
+}
+
+/* H(P) = alpha . P + beta m, Eq. (dirac_eq_mom) with P = p - A(t), Eq. (kin_mom). */
+static void hamiltonian(const dirac_mats *D, const double P[3], cplx H[4][4])
+{
+    for (int i = 0; i < 4; i++)
+        for (int j = 0; j < 4; j++)
+            H[i][j] = D->alpha[0][i][j] * P[0] + D->alpha[1][i][j] * P[1] +
+                      D->alpha[2][i][j] * P[2] + D->beta[i][j];
+}
+
+/* dpsi/dt = -i H psi */
+static void dirac_rhs(const cplx H[4][4], const cplx psi[4], cplx out[4])
+{
+    for (int i = 0; i < 4; i++) {
+        cplx acc = 0;
+        for (int j = 0; j < 4; j++)
+            acc += H[i][j] * psi[j];
+        out[i] = -I * acc;
+    }
+}
+
+/* sigma . P as a 2x2 matrix */
+static void sigma_dot(const double P[3], cplx S[2][2])
+{
+    S[0][0] = P[2];
+    S[0][1] = P[0] - I * P[1];
+    S[1][0] = P[0] + I * P[1];
+    S[1][1] = -P[2];
+}
+
+/* Adiabatic free spinors of Eq. (free_spin1) at kinetic momentum P:
+ * u_s = [(w+m) xi_s ; (sigma.P) xi_s] / sqrt(w+m),
+ * v_s = [-(sigma.P) eta_s ; (w+m) eta_s] / sqrt(w+m),
+ * xi_1 = eta_2 = (1,0), xi_2 = eta_1 = (0,1); s = 0,1 here for s = 1,2. */
+void orc_spinors(const double P[3], double _Complex u[2][4], double _Complex v[2][4])
+{
+    double w = sqrt(P[0] * P[0] + P[1] * P[1] + P[2] * P[2] + 1.0);
+    double nrm = 1.0 / sqrt(w + 1.0);
+    cplx S[2][2];
+    sigma_dot(P, S);
+    const cplx xi[2][2] = {{1, 0}, {0, 1}};
+    const cplx eta[2][2] = {{0, 1}, {1, 0}};
+    for (int s = 0; s < 2; s++) {
+        for (int a = 0; a < 2; a++) {
+            cplx sx = S[a][0] * xi[s][0] + S[a][1] * xi[s][1];
+            cplx se = S[a][0] * eta[s][0] + S[a][1] * eta[s][1];
+            u[s][a] = (w + 1.0) * xi[s][a] * nrm;
+            u[s][2 + a] = sx * nrm;
+            v[s][a] = -se * nrm;
+            v[s][2 + a] = (w + 1.0) * eta[s][a] * nrm;
+        }
+    }
+}
+
+static double pdot2(const double P[3])
+{
+    return P[0] * P[0] + P[1] * P[1] + P[2] * P[2];
+}
+
+/* One momentum mode, both spins.  A[0][k], A[1][k] (row stride ld) are the
+ * potential samples at t_i + k dt/2.  Classical RK4 on Eq. (dirac_eq_mom)
+ * over n_steps steps of size dt; the stage times t_n, t_n + dt/2, t_n + dt use
+ * samples 2n, 2n+1, 2n+2.  Initial state psi_s = v_s(P_in), Eq. (wf_init).
+ * Returns f(t_f, p) of Eq. (pair_prod_homo):
+ *   spin_sum = 0: sum_s sum_s' |u_s'^out+ psi_s|^2 / (2 w_out 2 w_in)   (full trace)
+ *   spin_sum = 1: sum_s        |u_s^out+  psi_s|^2 / (2 w_out 2 w_in)   (same-s only)
+ * If psi_out is given it receives psi_s(t_f) (s-major, 8 complex). */
+double orc_dirac_mode(const double *A, int ld, int n_steps, double dt, const double p[3],
+                      int spin_sum, double _Complex *psi_out)
+{
+    dirac_mats D;
+    make_dirac_mats(&D);
+    const double *Ax = A, *Ay = A + ld;
+    double Pin[3] = {p[0] - Ax[0], p[1] - Ay[0], p[2]};
+    double Pout[3] = {p[0] - Ax[2 * n_steps], p[1] - Ay[2 * n_steps], p[2]};
+    double win = sqrt(pdot2(Pin) + 1.0), wout = sqrt(pdot2(Pout) + 1.0);
+    cplx uin[2][4], vin[2][4], uout[2][4], vout[2][4];
+    orc_spinors(Pin, uin, vin);
+    orc_spinors(Pout, uout, vout);
+    double f = 0.0;
+    for (int s = 0; s < 2; s++) {
+        cplx psi[4];
+        for (int a = 0; a < 4; a++)
+            psi[a] = vin[s][a];
+        for (int n = 0; n < n_steps; n++) {
+            double P0[3] = {p[0] - Ax[2 * n], p[1] - Ay[2 * n], p[2]};
+            double P1[3] = {p[0] - Ax[2 * n + 1], p[1] - Ay[2 * n + 1], p[2]};
+            double P2[3] = {p[0] - Ax[2 * n + 2], p[1] - Ay[2 * n + 2], p[2]};
+            cplx H0[4][4], H1[4][4], H2[4][4];
+            hamiltonian(&D, P0, H0);
+            hamiltonian(&D, P1, H1);
+            hamiltonian(&D, P2, H2);
+            cplx k1[4], k2[4], k3[4], k4[4], tmp[4];
+            dirac_rhs(H0, psi, k1);
+            for (int a = 0; a < 4; a++)
+                tmp[a] = psi[a] + 0.5 * dt * k1[a];
+            dirac_rhs(H1, tmp, k2);
+            for (int a = 0; a < 4; a++)
+                tmp[a] = psi[a] + 0.5 * dt * k2[a];
+            dirac_rhs(H1, tmp, k3);
+            for (int a = 0; a < 4; a++)
+                tmp[a] = psi[a] + dt * k3[a];
+            dirac_rhs(H2, tmp, k4);
+            for (int a = 0; a < 4; a++)
+                psi[a] = psi[a] + dt / 6.0 * (k1[a] + 2.0 * k2[a] + 2.0 * k3[a] + k4[a]);
+        }
+        if (psi_out)
+            for (int a = 0; a < 4; a++)
+                psi_out[4 * s + a] = psi[a];
+        for (int s2 = 0; s2 < 2; s2++) {
+            if (spin_sum == 1 && s2 != s)
+                continue;
+            cplx amp = 0;
+            for (int a = 0; a < 4; a++)
+                amp += conj(uout[s2][a]) * psi[a];
+            f += creal(amp * conj(amp)) / (2.0 * wout * 2.0 * win);
+        }
+    }
+    return f;
+}
+
+/* ------------------------------------------------------------------------- */
+/* 6-component quantum kinetic equation, Sec. II.B, Eqs. (qke), (matrix)      */
+/* The paper's field plane (e2,e3) with out-of-plane axis e1 maps onto this   */
+/* file's (x,y) plane with out-of-plane z (a cyclic relabelling).             */
+/* ------------------------------------------------------------------------- */
+
+static void qke_matrix(const double P[3], const double E[2], const double Ed[2], double N[6][6])
+{
+    double w2 = pdot2(P) + 1.0, w = sqrt(w2);
+    double EE = E[0] * E[0] + E[1] * E[1];
+    double EP = E[0] * P[0] + E[1] * P[1];
+    double X = w2 * EE - EP * EP;
+    double eperp = sqrt(1.0 + P[2] * P[2]);
+    double cross = E[0] * Ed[1] - E[1] * Ed[0];
+    double Q = sqrt(X) / w2;
+    double R = X > 0.0 ? eperp * w * cross / X : 0.0;
+    memset(N, 0, sizeof(double) * 36);
+    N[0][1] = -Q;
+    N[1][0] = Q;
+    N[1][2] = -2.0 * w;
+    N[1][3] = R;
+    N[2][1] = 2.0 * w;
+    N[2][4] = -R;
+    N[3][1] = -R;
+    N[3][4] = 2.0 * w;
+    N[4][2] = R;
+    N[4][3] = -2.0 * w;
+    N[4][5] = Q;
+    N[5][4] = -Q;
+}
+
+static void mat6_vec(const double N[6][6], const double x[6], double y[6])
+{
+    for (int i = 0; i < 6; i++) {
+        double acc = 0.0;
+        for (int j = 0; j < 6; j++)
+            acc += N[i][j] * x[j];
+        y[i] = acc;
+    }
+}
+
+/* f = 1 - chi_1(t_f) by classical RK4 with chi(t_i) = (1,0,0,0,0,0).  A, E,
+ * Edot are [2][ld] half-step samples as in orc_dirac_mode. */
+double orc_qke6_mode(const double *A, const double *E, const double *Edot, int ld, int n_steps,
+                     double dt, const double p[3])
+{
+    double chi[6] = {1, 0, 0, 0, 0, 0};
+    for (int n = 0; n < n_steps; n++) {
+        double Nm[3][6][6];
+        for (int q = 0; q < 3; q++) {
+            int k = 2 * n + q;
+            double P[3] = {p[0] - A[k], p[1] - A[ld + k], p[2]};
+            double Ek[2] = {E[k], E[ld + k]};
+            double Edk[2] = {Edot[k], Edot[ld + k]};
+            qke_matrix(P, Ek, Edk, Nm[q]);
+        }
+        double k1[6], k2[6], k3[6], k4[6], tmp[6];
+        mat6_vec(Nm[0], chi, k1);
+        for (int i = 0; i < 6; i++)
+            tmp[i] = chi[i] + 0.5 * dt * k1[i];
+        mat6_vec(Nm[1], tmp, k2);
+        for (int i = 0; i < 6; i++)
+            tmp[i] = chi[i] + 0.5 * dt * k2[i];
+        mat6_vec(Nm[1], tmp, k3);
+        for (int i = 0; i < 6; i++)
+            tmp[i] = chi[i] + dt * k3[i];
+        mat6_vec(Nm[2], tmp, k4);
+        for (int i = 0; i < 6; i++)
+            chi[i] = chi[i] + dt / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+    }
+    return 1.0 - chi[0];
+}
+
+/* ------------------------------------------------------------------------- */
+/* Many modes in parallel (std threads over the mode list)                   */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    const double *A, *E, *Edot;
+    int ld, n_steps, spin_sum, kind;
+    double dt;
+    const double *p;
+    int nm, stride;
+    int first;
+    double *out;
+} mode_job;
+
+static void *mode_worker(void *arg)
+{
+    mode_job *J = arg;
+    for (int m = J->first; m < J->nm; m += J->stride) {
+        if (J->kind == 0)
+            J->out[m] = orc_dirac_mode(J->A, J->ld, J->n_steps, J->dt, J->p + 3 * m, J->spin_sum, NULL);
+        else
+            J->out[m] = orc_qke6_mode(J->A, J->E, J->Edot, J->ld, J->n_steps, J->dt, J->p + 3 * m);
+    }
+    return NULL;
+}
+
+static int resolve_threads(int nthreads)
+{
+    if (nthreads <= 0) {
+        long c = sysconf(_SC_NPROCESSORS_ONLN);
+        nthreads = c > 0 ? (int)c : 1;
+    }
+    return nthreads;
+}
+
+int orc_num_threads(int nthreads)
+{
+    return resolve_threads(nthreads);
+}
+
+static void run_modes(mode_job *tmpl, int nthreads)
+{
+    nthreads = resolve_threads(nthreads);
+    if (nthreads > tmpl->nm)
+        nthreads = tmpl->nm > 0 ? tmpl->nm : 1;
+    pthread_t *th = malloc(sizeof(pthread_t) * nthreads);
+    mode_job *jobs = malloc(sizeof(mode_job) * nthreads);
+    for (int i = 0; i < nthreads; i++) {
+        jobs[i] = *tmpl;
+        jobs[i].first = i;
+        jobs[i].stride = nthreads;
+        pthread_create(&th[i], NULL, mode_worker, &jobs[i]);
+    }
+    for (int i = 0; i < nthreads; i++)
+        pthread_join(th[i], NULL);
+    free(th);
+    free(jobs);
+}
+
+/* f(p) for a list of momenta p[nm][3] (Dirac, Eq. pair_prod_homo). */
+int orc_dirac_modes(const double *A, int ld, int n_steps, double dt, const double *p, int nm,
+                    int spin_sum, double *n_out, int nthreads)
+{
+    if (!A || !p || !n_out || nm < 0 || n_steps < 1 || ld < 2 * n_steps + 1)
+        return ORC_ERR_ARG;
+    mode_job J = {A, NULL, NULL, ld, n_steps, spin_sum, 0, dt, p, nm, 1, 0, n_out};
+    run_modes(&J, nthreads);
+    return ORC_OK;
+}
+
+/* f(p) = 1 - chi_1 for a list of momenta (quantum kinetic equation). */
+int orc_qke6_modes(const double *A, const double *E, const double *Edot, int ld, int n_steps,
+                   double dt, const double *p, int nm, double *f_out, int nthreads)
+{
+    if (!A || !E || !Edot || !p || !f_out || nm < 0 || n_steps < 1 || ld < 2 * n_steps + 1)
+        return ORC_ERR_ARG;
+    mode_job J = {A, E, Edot, ld, n_steps, 0, 1, dt, p, nm, 1, 0, f_out};
+    run_modes(&J, nthreads);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Momentum integral, Eq. (opt_prob): N = int_D d^3p f                        */
+/* ------------------------------------------------------------------------- */
+
+/* Trapezoid weights of a linspace(a, b, n) axis (endpoints included).  With
+ * mirror = 1 the axis is the non-negative half [0, b] of the symmetric axis
+ * [-b, b] and the weights are those of the trapezoid rule on the full axis:
+ * a point p > 0 stands for +p and -p (twice its half-axis weight) and p = 0 is
+ * an interior point of the full axis (weight d = twice its half-axis d/2).
+ * Both cases double the half-axis weight.  A single-point axis has weight 1. */
+void orc_trapz_weights(int n, double a, double b, int mirror, double *w)
+{
+    if (n == 1) {
+        w[0] = 1.0;
+        return;
+    }
+    double d = (b - a) / (double)(n - 1);
+    for (int i = 0; i < n; i++) {
+        w[i] = (i == 0 || i == n - 1) ? 0.5 * d : d;
+        if (mirror)
+            w[i] = 2.0 * w[i];
+    }
+}
+
+static double axis_point(int i, int n, double a, double b)
+{
+    return n == 1 ? a : a + (b - a) * (double)i / (double)(n - 1);
+}
+
+/* Pair number N[c] = sum_p w(p) f_c(p) over the grid p = (x_i, y_j, z_k),
+ * x fastest (n_p[c][k][j][i]).  Candidate c uses n_steps[c] steps and the
+ * potential rows A + c*2*ld.  n_out may be NULL.  The sum is taken serially
+ * in grid order, so the result does not depend on the thread count. */
+int orc_pair_number(const double *A, int ncand, int ld, const int *n_steps, double dt, int nx,
+                    int ny, int nz, double x0, double x1, double y0, double y1, double z0,
+                    double z1, int mirror_z, int spin_sum, double *n_out, double *N_out,
+                    int nthreads)
+{
+    if (!A || !n_steps || !N_out || ncand < 0 || nx < 1 || ny < 1 || nz < 1)
+        return ORC_ERR_ARG;
+    int nm = nx * ny * nz;
+    double *p = malloc(sizeof(double) * 3 * nm);
+    double *wgt = malloc(sizeof(double) * nm);
+    double *wx = malloc(sizeof(double) * nx), *wy = malloc(sizeof(double) * ny),
+           *wz = malloc(sizeof(double) * nz);
+    orc_trapz_weights(nx, x0, x1, 0, wx);
+    orc_trapz_weights(ny, y0, y1, 0, wy);
+    orc_trapz_weights(nz, z0, z1, mirror_z, wz);
+    for (int k = 0; k < nz; k++)
+        for (int j = 0; j < ny; j++)
+            for (int i = 0; i < nx; i++) {
+                int m = (k * ny + j) * nx + i;
+                p[3 * m + 0] = axis_point(i, nx, x0, x1);
+                p[3 * m + 1] = axis_point(j, ny, y0, y1);
+                p[3 * m + 2] = axis_point(k, nz, z0, z1);
+                wgt[m] = wx[i] * wy[j] * wz[k];
+            }
+    double *nbuf = malloc(sizeof(double) * nm);
+    int status = ORC_OK;
+    for (int c = 0; c < ncand; c++) {
+        if (n_steps[c] < 1 || ld < 2 * n_steps[c] + 1) {
+            status = ORC_ERR_ARG;
+            break;
+        }
+        orc_dirac_modes(A + (size_t)c * 2 * ld, ld, n_steps[c], dt, p, nm, spin_sum, nbuf, nthreads);
+        double N = 0.0;
+        for (int m = 0; m < nm; m++)
+            N += wgt[m] * nbuf[m];
+        N_out[c] = N;
+        if (n_out)
+            memcpy(n_out + (size_t)c * nm, nbuf, sizeof(double) * nm);
+    }
+    free(p);
+    free(wgt);
+    free(wx);
+    free(wy);
+    free(wz);
+    free(nbuf);
+    return status;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Differential evolution, DE/rand/1/bin, Sec. IV.B                          */
+/* ------------------------------------------------------------------------- */
+
+/* SplitMix64 (Steele, Lea, Flood, OOPSLA 2014): the k-th output (k = 0,1,..)
+ * of the generator seeded with `seed` is mix(seed + (k+1) * gamma). */
+uint64_t orc_splitmix64_at(uint64_t seed, uint64_t k)
+{
+    uint64_t z = seed + (k + 1) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* Random-number slots of individual i in generation g: the stream key is
+ * splitmix64_at(splitmix64_at(seed, g), i); slots 0..61 feed the rejection
+ * draws of the three donors, slot 62 the forced index R, slot 64 + j the
+ * crossover number of coordinate j. */
+#define DE_SLOT_R 62
+#define DE_SLOT_CROSS 64
+#define DE_MAX_DRAWS 62
+
+static double u01(uint64_t x)
+{
+    return (double)(x >> 11) * 0x1.0p-53;
+}
+
+static int below(uint64_t x, int n)
+{
+    return (int)(((x >> 32) * (uint64_t)n) >> 32);
+}
+
+/* Steps 1-3 of DE/rand/1/bin for every individual i:
+ *  1. three distinct donors a, b, c, all different from i;
+ *  2. mutation u = a + F (b - c);
+ *  3. binomial crossover: y_j = u_j if r_j <= CR or j == R, else x_ij.
+ * Coordinates taken from u are brought back into bounds: periodic ones
+ * (phases) are wrapped into [lo, hi), the others clipped to [lo, hi].
+ * pop[NP][D] -> trial[NP][D].  Returns ORC_ERR_ARG when NP < 4. */
+int orc_de_propose(const double *pop, int NP, int D, const double *lo, const double *hi,
+                   const uint8_t *periodic, double F, double CR, uint64_t seed, uint64_t gen,
+                   double *trial)
+{
+    if (NP < 4 || D < 1 || D > 4096 || !pop || !trial || !lo || !hi)
+        return ORC_ERR_ARG;
+    uint64_t gkey = orc_splitmix64_at(seed, gen);
+    for (int i = 0; i < NP; i++) {
+        uint64_t key = orc_splitmix64_at(gkey, (uint64_t)i);
+        int r[3];
+        int slot = 0;
+        for (int q = 0; q < 3; q++) {
+            for (;;) {
+                if (slot >= DE_MAX_DRAWS)
+                    return ORC_ERR_ARG;
+                int cand = below(orc_splitmix64_at(key, (uint64_t)slot++), NP);
+                int clash = (cand == i);
+                for (int z = 0; z < q; z++)
+                    clash |= (cand == r[z]);
+                if (!clash) {
+                    r[q] = cand;
+                    break;
+                }
+            }
+        }
+        int R = below(orc_splitmix64_at(key, DE_SLOT_R), D);
+        const double *xa = pop + (size_t)r[0] * D, *xb = pop + (size_t)r[1] * D,
+                     *xc = pop + (size_t)r[2] * D, *xi = pop + (size_t)i * D;
+        double *y = trial + (size_t)i * D;
+        for (int j = 0; j < D; j++) {
+            double rj = u01(orc_splitmix64_at(key, (uint64_t)(DE_SLOT_CROSS + j)));
+            if (rj <= CR || j == R) {
+                double diff = xb[j] - xc[j];
+                double step = F * diff;
+                double u = xa[j] + step;
+                if (periodic && periodic[j]) {
+                    double period = hi[j] - lo[j];
+                    double off = fmod(u - lo[j], period);
+                    if (off < 0.0)
+                        off = off + period;
+                    u = lo[j] + off;
+                    if (u >= hi[j])
+                        u = lo[j];
+                } else {
+                    if (u < lo[j])
+                        u = lo[j];
+                    if (u > hi[j])
+                        u = hi[j];
+                }
+                y[j] = u;
+            } else {
+                y[j] = xi[j];
+            }
+        }
+    }
+    return ORC_OK;
+}
+
+/* Step 4, read for maximisation of N: x is replaced by y when N(y) >= N(x)
+ * (ties go to the trial).  A NaN trial fitness never replaces. */
+int orc_de_select(double *pop, double *fit, const double *trial, const double *trial_fit, int NP,
+                  int D)
+{
+    if (NP < 1 || D < 1 || !pop || !fit || !trial || !trial_fit)
+        return ORC_ERR_ARG;
+    for (int i = 0; i < NP; i++) {
+        if (trial_fit[i] >= fit[i]) {
+            memcpy(pop + (size_t)i * D, trial + (size_t)i * D, sizeof(double) * D);
+            fit[i] = trial_fit[i];
+        }
+    }
+    return ORC_OK;
+}

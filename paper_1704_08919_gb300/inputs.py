@@ -1,0 +1,93 @@
+"""Seeded synthetic inputs shared by the tests, the bench and the smoke check.
+
+This module holds workload descriptions and random draws only -- none of the
+method's arithmetic -- so that the CUDA path and the CPU oracle can be fed the
+same inputs without sharing any code.  Numbers are drawn with numpy's PCG64
+(`numpy.random.default_rng(seed)`).
+
+Workloads (sizes follow the paper's pulse model, Sec. III, and momentum
+windows, Sec. V, scaled to the configurations below):
+
+* ``ROTATING_GAUSSIAN``: one rotating field
+  E(t) = E0 exp(-t^2/tau^2) (cos w t, sin w t, 0), E0 = 0.1, w = 0.7, tau = 10,
+  t in [-40, 40], dt = 0.02 (4000 RK4 steps), A(-40) = 0; grid 32 x 32 x 16 on
+  [-1.5, 1.5]^2 x [0, 1.5] with the p_z mirror.
+* ``DE_BATCH``: a population of 64 B-spline pulses (K = 8 control points per
+  amplitude and phase per polarisation, cubic splines on [0, 2], T = 200,
+  8192 RK4 steps, fluence 2.0) on a 64 x 64 x 32 grid over [-2, 2]^2 x [0, 2]
+  with the p_z mirror; DE with F = 0.8, CR = 0.9.
+"""
+import math
+
+import numpy as np
+
+ROTATING_GAUSSIAN = dict(
+    name="rotating-gaussian E0=0.1 w=0.7 tau=10 t=[-40,40] dt=0.02 grid 32x32x16",
+    E0=0.1, w=0.7, tau=10.0, t0=-40.0, t1=40.0, n_steps=4000,
+    grid=dict(nx=32, ny=32, nz=16, x0=-1.5, x1=1.5, y0=-1.5, y1=1.5, z0=0.0, z1=1.5, mirror_z=1),
+)
+
+DE_BATCH = dict(
+    name="de-batch 64 B-spline pulses K=8 T=200 8192 steps grid 64x64x32",
+    NP=64, K=8, order=4, w_min=0.0, w_max=2.0, T=200.0, fluence=2.0, n_steps=8192,
+    F=0.8, CR=0.9,
+    grid=dict(nx=64, ny=64, nz=32, x0=-2.0, x1=2.0, y0=-2.0, y1=2.0, z0=0.0, z1=2.0, mirror_z=1),
+)
+
+
+def field_spec(cfg):
+    """The pulse-model settings of a workload as a plain dict."""
+    return dict(K=cfg["K"], order=cfg["order"], w_min=cfg["w_min"], w_max=cfg["w_max"],
+                T=cfg["T"], fluence=cfg["fluence"], n_steps=cfg["n_steps"])
+
+
+def param_bounds(K):
+    """(lo, hi, periodic) for the 4K parameters [a^E_x, a^phi_x, a^E_y, a^phi_y].
+
+    Amplitude weights lie in [0, 1]; phase weights in [0, 2 pi) and wrap.
+    """
+    lo = np.zeros(4 * K)
+    hi = np.empty(4 * K)
+    per = np.zeros(4 * K, dtype=np.uint8)
+    for blk in range(4):
+        sl = slice(blk * K, (blk + 1) * K)
+        if blk % 2 == 0:
+            hi[sl] = 1.0
+        else:
+            hi[sl] = 2.0 * math.pi
+            per[sl] = 1
+    return lo, hi, per
+
+
+def random_population(NP, K, seed):
+    """NP parameter vectors drawn uniformly inside param_bounds(K)."""
+    lo, hi, _ = param_bounds(K)
+    rng = np.random.default_rng(seed)
+    return lo + rng.random((NP, 4 * K)) * (hi - lo)
+
+
+def grid_axes(grid):
+    """(x, y, z) node coordinates of a momentum grid (linspace, end points included)."""
+    def ax(n, a, b):
+        return np.array([a]) if n == 1 else np.linspace(a, b, n)
+    return (ax(grid["nx"], grid["x0"], grid["x1"]), ax(grid["ny"], grid["y0"], grid["y1"]),
+            ax(grid["nz"], grid["z0"], grid["z1"]))
+
+
+def grid_points(grid):
+    """All grid momenta as an array [nz*ny*nx, 3], x fastest."""
+    x, y, z = grid_axes(grid)
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    return np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+
+
+def strided_modes(grid, count, seed):
+    """`count` distinct flat mode indices spread over the grid (sorted)."""
+    nm = grid["nx"] * grid["ny"] * grid["nz"]
+    rng = np.random.default_rng(seed)
+    return np.sort(rng.choice(nm, size=min(count, nm), replace=False))
+
+
+def small_grid(nx, ny, nz, ext=2.0, mirror_z=1):
+    return dict(nx=nx, ny=ny, nz=nz, x0=-ext, x1=ext, y0=-ext, y1=ext, z0=0.0, z1=ext,
+                mirror_z=mirror_z)
