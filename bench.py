@@ -1,0 +1,353 @@
+"""Throughput of candidate-pulse scoring inside the DE loop (arXiv 1704.08919).
+
+Workload (one "step" = one DE generation of the whole hot path): a population
+of 64 B-spline pulses (K = 8, cubic, band [0, 2], T = 200, 8192 RK4 steps,
+fluence 2.0), momentum grid 64 x 64 x 32 over [-2, 2]^2 x [0, 2] with the p_z
+mirror; per generation: DE/rand/1/bin proposal (F = 0.8, CR = 0.9), synthesis
+of the 64 trial pulses, their pair numbers (FP32 propagation, FP64 projection
+and momentum sum), greedy selection -- all through pp_de_step.
+
+Prints one JSON line.  `value` is candidate pulses scored per second over all
+ranks (64 per rank per step); mode-steps/s, the live roofline of the
+propagation kernel, the FP32-vs-FP64 N error, clocks, an end-to-end figure
+with host buffers and a CPU-oracle baseline are added.  `--impl reference`
+times the FP64 CPU oracle instead (rank 0 only under torchrun).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1704_08919_gb300 import inputs  # noqa: E402
+
+CFG = inputs.DE_BATCH
+# FP32 operation count of one mode-step of the propagation kernel (both spin
+# channels, RK4 increment form, compensated accumulation), FMA = 2.
+FLOP_PER_MODE_STEP_FP32 = 268
+FLOP_PER_MODE_STEP_FP64 = 244
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--cpu-modes", type=int, default=8192,
+                    help="modes of one candidate in the CPU-oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload_config(precision):
+    g = CFG["grid"]
+    return {
+        "workload": CFG["name"],
+        "NP": CFG["NP"], "K": CFG["K"], "order": CFG["order"], "T": CFG["T"],
+        "n_steps": CFG["n_steps"], "fluence": CFG["fluence"],
+        "grid": "%dx%dx%d px,py in [%g,%g], pz in [%g,%g] mirrored" % (
+            g["nx"], g["ny"], g["nz"], g["x0"], g["x1"], g["z0"], g["z1"]),
+        "F": CFG["F"], "CR": CFG["CR"], "precision": precision,
+        "l2": "flushed between timed steps (256 MiB write)",
+    }
+
+
+def units_per_candidate():
+    g = CFG["grid"]
+    return g["nx"] * g["ny"] * g["nz"] * CFG["n_steps"]
+
+
+# ----------------------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_median": statistics.median(power)}
+
+
+# ----------------------------------------------------------------------------- oracle legs
+
+
+def oracle_sample(A_host, cand, nmodes, seed=0):
+    """The FP64 CPU oracle on `nmodes` strided modes of one candidate: (seconds, n, idx, cores)."""
+    import oracle
+    idx = inputs.strided_modes(CFG["grid"], nmodes, seed=seed)
+    pts = inputs.grid_points(CFG["grid"])[idx]
+    dt = CFG["T"] / CFG["n_steps"]
+    t0 = time.perf_counter()
+    n = oracle.dirac_modes(A_host[cand], CFG["n_steps"], dt, pts)
+    el = time.perf_counter() - t0
+    return el, n, idx, oracle.num_threads(0)
+
+
+def reference_main(args):
+    """--impl reference: the FP64 CPU oracle, as it stands, on the host cores."""
+    import oracle
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    params = inputs.random_population(CFG["NP"], CFG["K"], seed=1)
+    nm = max(256, args.cpu_modes // 4)
+    A, _, _, rc = oracle.synth_field(params[:1], CFG["K"], CFG["order"], CFG["w_min"], CFG["w_max"],
+                                     CFG["T"], CFG["fluence"], CFG["n_steps"], want_E=False)
+    for _ in range(args.warmup):
+        oracle_sample(A, 0, 64)
+    times = []
+    for s in range(args.steps):
+        el, _, _, cores = oracle_sample(A, 0, nm, seed=s)
+        times.append(el)
+    per_mode_step = sum(times) / (args.steps * nm * CFG["n_steps"])
+    cand_per_s = 1.0 / (per_mode_step * units_per_candidate())
+    sample = ("%d strided modes of one candidate x %d RK4 steps per step; the oracle's synthesis "
+              "is excluded; candidates/s extrapolated by mode-steps" % (nm, CFG["n_steps"]))
+    line = {
+        "metric": "candidate pulses scored/s (DE batch, rel. N err <= 1e-4 vs FP64 oracle)",
+        "value": cand_per_s, "unit": "candidates/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000.0 * CFG["NP"] / cand_per_s,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded B-spline pulses)", "config": workload_config("fp64"),
+        "impl": "reference", "mode_steps_per_s": 1.0 / per_mode_step,
+        "cpu_baseline": {"value": cand_per_s, "unit": "candidates/s", "cores": cores,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": cand_per_s, "unit": "candidates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU leg
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_main(args)
+    import torch
+    import paper_1704_08919_gb300 as pp
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    pp.lib()
+    stream = torch.cuda.current_stream()
+
+    NP, K = CFG["NP"], CFG["K"]
+    spec = inputs.field_spec(CFG)
+    grid = CFG["grid"]
+    dt = CFG["T"] / CFG["n_steps"]
+    lo, hi, per = inputs.param_bounds(K)
+    seed = 1000 + rank
+    pop0 = inputs.random_population(NP, K, seed=1 + rank)
+    lo_t, hi_t = torch.tensor(lo, device=dev), torch.tensor(hi, device=dev)
+    per_t = torch.tensor(per, device=dev)
+    pop = torch.tensor(pop0, device=dev)
+    A, _, _ = pp.synth_field(pop, spec)
+    fit, _ = pp.pair_number(A, dt, grid, precision=args.precision)
+    trial = torch.empty_like(pop)
+    tfit = torch.empty_like(fit)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    if pp.sync_status() != pp.PP_OK:
+        raise RuntimeError("initial scoring failed: %s" % pp.lib().pp_last_error().decode())
+
+    gen = 0
+    for _ in range(max(args.warmup, 0)):
+        pp.de_step(pop, fit, spec, grid, lo_t, hi_t, per_t, CFG["F"], CFG["CR"], seed, gen,
+                   precision=args.precision, trial_out=trial, trial_fit_out=tfit)
+        gen += 1
+    torch.cuda.synchronize()
+
+    # ---- timed region: K generations, each bracketed by CUDA events, L2 flushed between
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    pp.profile_begin()
+    t_wall = time.perf_counter()
+    for s in range(args.steps):
+        flush.zero_()
+        starts[s].record(stream)
+        pp.de_step(pop, fit, spec, grid, lo_t, hi_t, per_t, CFG["F"], CFG["CR"], seed, gen,
+                   precision=args.precision, trial_out=trial, trial_fit_out=tfit)
+        ends[s].record(stream)
+        gen += 1
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    kern_ms, kern_launches = pp.profile_end()
+    clk = clocks.stop()
+    st = pp.sync_status()
+    if st != pp.PP_OK:
+        raise RuntimeError("device status %d after the timed region" % st)
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = t.item()
+    ms_per_step = total_ms / args.steps
+    cand_per_s = ws * NP * args.steps / (total_ms / 1000.0)
+    mode_steps_per_s = cand_per_s * units_per_candidate()
+
+    # ---- live roofline of the propagation kernel
+    per_launch_ms = kern_ms / max(kern_launches, 1)
+    flop = FLOP_PER_MODE_STEP_FP32 if args.precision == "fp32" else FLOP_PER_MODE_STEP_FP64
+    achieved = flop * NP * units_per_candidate() / (per_launch_ms / 1000.0) / 1e12
+    peak_fp32 = SM_COUNT * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
+    roofline = {"bound": "alu", "kernel": "propagate_kernel<%s>" % (
+        "float, compensated" if args.precision == "fp32" else "double"),
+        "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
+        "frac": achieved / peak_fp32,
+        "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)",
+        "flop_per_mode_step": flop, "launch_ms": per_launch_ms,
+        "kernel_share_of_step": kern_ms / total_ms if ws == 1 else None,
+        "traffic": None}
+
+    # ---- accuracy at the bench config: FP32 N vs FP64 N on 4 candidates of the final population
+    Acheck, _, _ = pp.synth_field(pop[:4].contiguous(), spec)
+    N32, _ = pp.pair_number(Acheck, dt, grid, precision="fp32")
+    N64, n64 = pp.pair_number(Acheck, dt, grid, precision="fp64", want_n=True)
+    pp.sync_status()
+    rel_err = (N32 / N64 - 1).abs().max().item()
+
+    # ---- end to end through the public API with host buffers
+    pop_h = torch.tensor(pop0, dtype=torch.float64).pin_memory()
+    fit_h = fit.cpu().pin_memory()
+    e2e_times = []
+    for s in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pop.copy_(pop_h, non_blocking=True)
+        fit.copy_(fit_h, non_blocking=True)
+        pp.de_step(pop, fit, spec, grid, lo_t, hi_t, per_t, CFG["F"], CFG["CR"], seed, gen,
+                   precision=args.precision, trial_out=trial, trial_fit_out=tfit)
+        pop_h.copy_(pop, non_blocking=True)
+        fit_h.copy_(fit, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+        gen += 1
+    e2e_total = sum(e2e_times)
+    if dist is not None:
+        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = t.item()
+    e2e_value = ws * NP * args.steps / e2e_total
+    h2d = pop_h.numel() * 8 + fit_h.numel() * 8
+
+    # ---- CPU-oracle baseline (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        A_host = Acheck.cpu().numpy()
+        el, n_or, idx, cores = oracle_sample(A_host, 0, args.cpu_modes)
+        cpu_mode_steps = args.cpu_modes * CFG["n_steps"] / el
+        n_gpu = n64[0].reshape(-1).cpu().numpy()[idx]
+        big = n_or >= 1e-6 * n64[0].max().item()
+        cpu = {"value": cpu_mode_steps / units_per_candidate(), "unit": "candidates/s",
+               "cores": cores, "kind": "oracle",
+               "sample": "%d strided modes of one candidate x %d RK4 steps (%.1f s), "
+                         "extrapolated to a full candidate by mode-steps" % (
+                             args.cpu_modes, CFG["n_steps"], el),
+               "mode_steps_per_s": cpu_mode_steps,
+               "gpu_fp64_vs_oracle_max_rel_n": float(np.abs(n_gpu[big] / n_or[big] - 1).max())}
+
+    if rank == 0:
+        line = {
+            "metric": "candidate pulses scored/s (DE batch, rel. N err <= 1e-4 vs FP64 oracle)",
+            "value": cand_per_s, "unit": "candidates/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else "f64",
+            "data": "synthetic (seeded B-spline pulses, uniform in bounds)",
+            "config": workload_config(args.precision),
+            "mode_steps_per_s": mode_steps_per_s,
+            "n_rel_err_fp32_vs_fp64_max": rel_err,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "candidates/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": h2d},
+            "gpu_launches": 7 * args.steps,
+            "clocks": clk,
+            "wall_s_timed": t_wall,
+            "step_ms": step_ms,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,191 @@
+/*
+ * pp.h -- C ABI of libpp: GPU scoring of candidate laser pulses by the
+ * electron-positron pair number they produce, after
+ * F. Fillion-Gourdeau, F. Hebenstreit, D. Gagnon, S. MacLean,
+ * "Pulse shape optimization for electron-positron production in rotating
+ * fields", arXiv 1704.08919.
+ *
+ * Units: m = e = c = hbar = 1 (so e*E is written E; E = 1 is the Schwinger field).
+ *
+ * Conventions shared by every entry point:
+ *  - Array arguments marked (device) are caller-owned device pointers in the
+ *    current CUDA context; (host) pointers are read before the call returns.
+ *    Nothing is retained after a call returns.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  All GPU work
+ *    is enqueued on it asynchronously; a PP_OK return means "validated and
+ *    launched", not "finished".
+ *  - Argument errors are detected on the host before anything is launched and
+ *    return PP_ERR_INVALID_ARG; pp_last_error() then describes the problem.
+ *  - Errors that only the device can see (a bounded wait that gave up, a
+ *    non-finite result, a zero-fluence pulse) are recorded in a device status
+ *    word and returned by pp_sync_status().
+ *  - The library keeps a private per-device scratch area (the per-step field
+ *    table of pp_pair_number and the per-block partial sums).  It grows on
+ *    demand with cudaMalloc after a device synchronisation; call an entry point
+ *    once with the largest sizes before capturing it in a CUDA graph.
+ *  - Calls are thread-compatible: concurrent calls on different host threads
+ *    must use different devices.
+ */
+#ifndef PP_H
+#define PP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PP_OK = 0,
+    PP_ERR_INVALID_ARG = 1,      /* bad size, null pointer, bad option: nothing launched */
+    PP_ERR_CUDA = 2,             /* a CUDA runtime call failed (message in pp_last_error) */
+    PP_ERR_NONFINITE = 3,        /* a NaN or Inf reached N (device-detected) */
+    PP_ERR_DEGENERATE_FIELD = 4, /* a candidate had zero fluence and was set to A = 0 */
+    PP_ERR_TIMEOUT = 5,          /* a bounded device wait gave up (the kernel returned early) */
+    PP_ERR_NOT_IMPLEMENTED = 6
+} pp_status;
+
+typedef enum {
+    PP_FP64 = 0, /* FP64 throughout (the parity path) */
+    PP_FP32 = 1  /* FP32 propagation with compensated (two-float) state accumulation;
+                    FP64 initial state, projection and momentum sum */
+} pp_precision;
+
+/* Pulse model of Sec. III of the paper.
+ *  K        B-spline coefficients per amplitude and per phase and polarisation (N_s).
+ *  order    B-spline order k (k = 4: cubic; the paper's tables use k = 3).
+ *  w_min, w_max  spectral band [omega_min, omega_max] (angular frequency).
+ *  T        pulse length = period 2 pi / dOmega; t runs over [-T/2, T/2].
+ *  fluence  U_const of Eq. (energy): every pulse is rescaled to int E^2 dt = U_const.
+ *  n_steps  RK4 steps over [-T/2, T/2] (dt = T / n_steps); the potential is
+ *           sampled on the half-step grid, 2 n_steps + 1 samples.
+ *  envelope 0 only (g(t) = 1, DC removed so A(-T/2) = A(T/2) = 0).            */
+typedef struct {
+    int32_t K;
+    int32_t order;
+    double w_min;
+    double w_max;
+    double T;
+    double fluence;
+    int32_t n_steps;
+    int32_t envelope;
+} pp_field_spec;
+
+/* Uniform momentum grid: nx x ny x nz linspace nodes (end points included) over
+ * [x0,x1] x [y0,y1] x [z0,z1].  mirror_z = 1 declares [z0,z1] = [0, zmax] to be
+ * the non-negative half of the symmetric window [-zmax, zmax]: the pair density
+ * is even in p_z for fields in the x-y plane, and the p_z weights are doubled. */
+typedef struct {
+    int32_t nx, ny, nz;
+    double x0, x1, y0, y1, z0, z1;
+    int32_t mirror_z;
+} pp_grid;
+
+/* Field synthesis: parameters -> vector potential (Sec. III, Eqs. (coeff_basis_E),
+ * (coeff_basis_phi), (field), (energy); renormalisation to U_const at every
+ * update, Sec. IV.B).
+ *  params (device) [ncand][4K] FP64, per candidate [a^E_x(K), a^phi_x(K), a^E_y(K), a^phi_y(K)].
+ *  spec   (host)   pulse model.
+ *  A      (device) [ncand][2][ld] FP64 output, row 0 = A_x, row 1 = A_y, sample k at
+ *                  t_k = -T/2 + k T / (2 n_steps), k = 0 .. 2 n_steps; ld >= 2 n_steps + 1.
+ *  E      (device) same layout for E = -dA/dt, or NULL.
+ *  scale  (device) [ncand] the factor s applied to the unit-weight spectrum, or NULL.
+ * A zero-fluence candidate produces A = E = 0, s = 0 and sets PP_ERR_DEGENERATE_FIELD
+ * in the status word.  Errors: INVALID_ARG (K < order, order < 1 or > 8, K > 64,
+ * empty band or more than 1536 modes in it, T <= 0, fluence <= 0, n_steps < 1, ld too
+ * small, null A or params). */
+int pp_synth_field(const double *params, int32_t ncand, const pp_field_spec *spec, double *A,
+                   int32_t ld, double *E, double *scale, void *stream);
+
+/* Pair number of each candidate field (Sec. II.A, Eqs. (kin_mom), (free_spin1),
+ * (wf_init), (dirac_eq_mom), (pair_prod_homo); Eq. (opt_prob)).
+ * For every momentum p of the grid and both spin states, the momentum-space
+ * Dirac equation i d/dt psi = [alpha.(p - A(t)) + beta] psi is integrated with
+ * classical RK4 (step dt, stage times t_n, t_n + dt/2, t_n + dt taken from
+ * samples 2n, 2n+1, 2n+2 of A) from the negative-energy state at p - A(t_0);
+ * f(p) = sum over both spins of the squared projections onto the positive-
+ * energy states at p - A(t_end) (the full spin trace); N = sum_p w(p) f(p)
+ * with trapezoid weights per axis.
+ *  A       (device) [ncand][2][ld] FP64 potential samples as written by pp_synth_field.
+ *  n_steps (host)   [ncand] steps per candidate (each 2 n_steps[c] + 1 <= ld), or
+ *                   NULL: every candidate takes (ld - 1) / 2 steps.
+ *  dt      step size (> 0).
+ *  grid    (host)   momentum grid shared by all candidates.
+ *  precision PP_FP64 or PP_FP32.
+ *  N       (device) [ncand] FP64 output.
+ *  n_p     (device) [ncand][nz][ny][nx] FP64 output (x fastest), or NULL.
+ * The sum over p is taken in a fixed order: results are bitwise reproducible
+ * run to run.  Errors: INVALID_ARG (sizes, null pointers, dt <= 0, bad precision). */
+int pp_pair_number(const double *A, int32_t ncand, int32_t ld, const int32_t *n_steps, double dt,
+                   const pp_grid *grid, int32_t precision, double *N, double *n_p, void *stream);
+
+/* DE/rand/1/bin trial vectors (Sec. IV.B, steps 1-3).  For each individual i:
+ * three distinct donors r1, r2, r3 != i; u = x_r1 + F (x_r2 - x_r3); binomial
+ * crossover with a forced index R.  Coordinates taken from u are wrapped into
+ * [lo, hi) where periodic[j] = 1 (phases) and clipped to [lo, hi] elsewhere.
+ * Random numbers come from SplitMix64 (Steele, Lea, Flood 2014): the key of
+ * individual i in generation `generation` is out(out(seed, generation), i)
+ * with out(s, k) the k-th output of the generator seeded with s; slots 0..61
+ * of that key serve the donor draws (rejection), slot 62 the index R and slot
+ * 64 + j the crossover number of coordinate j.  The result is bit-identical to
+ * the sequential definition.
+ *  pop (device) [NP][D]; lo, hi (device) [D]; periodic (device) [D] or NULL;
+ *  trial (device) [NP][D] output.  NP >= 4, 1 <= D <= 4096, 0 <= CR <= 1. */
+int pp_de_propose(const double *pop, int32_t NP, int32_t D, const double *lo, const double *hi,
+                  const uint8_t *periodic, double F, double CR, uint64_t seed, uint64_t generation,
+                  double *trial, void *stream);
+
+/* Greedy selection for maximisation (Sec. IV.B, step 4): row i of pop and fit[i]
+ * are replaced by the trial when trial_fit[i] >= fit[i] (ties go to the trial;
+ * a NaN trial never replaces).  All pointers (device). */
+int pp_de_select(double *pop, double *fit, const double *trial, const double *trial_fit,
+                 int32_t NP, int32_t D, void *stream);
+
+/* One DE generation on the device: propose (pp_de_propose) -> synthesise the
+ * trial pulses (pp_synth_field) -> score them (pp_pair_number) -> select
+ * (pp_de_select).  pop [NP][4 spec->K] and fit [NP] (device) are updated in
+ * place; lo, hi, periodic as in pp_de_propose (device); trial_out (device,
+ * [NP][4K]) and trial_fit_out (device, [NP]) receive the scored trials or may
+ * be NULL.  The potential buffer and the trials live in library scratch. */
+int pp_de_step(double *pop, double *fit, int32_t NP, const pp_field_spec *spec,
+               const pp_grid *grid, int32_t precision, const double *lo, const double *hi,
+               const uint8_t *periodic, double F, double CR, uint64_t seed, uint64_t generation,
+               double *trial_out, double *trial_fit_out, void *stream);
+
+/* Waits for `stream`, returns and clears the device status word:
+ * PP_OK, PP_ERR_TIMEOUT, PP_ERR_NONFINITE or PP_ERR_DEGENERATE_FIELD (the most
+ * severe one seen since the last call), or PP_ERR_CUDA if the wait failed. */
+int pp_sync_status(void *stream);
+
+/* Test hooks for the bounded device waits (failure detection without a GPU fault).
+ * pp_set_wait_limit: iteration limit of every mbarrier wait in the propagation
+ *   kernel's main loop (default 1 << 26 polls; 0 restores the default).  Returns
+ *   the previous limit.
+ * pp_set_skip_copies: when nonzero, the propagation kernel issues none of its
+ *   tile copies, so its first wait is on a barrier that nothing completes; the
+ *   wait runs out after the limit, the kernel records PP_ERR_TIMEOUT, writes NaN
+ *   for the affected candidates and returns.  No copy is ever in flight on that
+ *   path.  Returns the previous setting. */
+int64_t pp_set_wait_limit(int64_t limit);
+int pp_set_skip_copies(int skip);
+
+/* Kernel timing for the propagation kernel (the hot loop of pp_pair_number and
+ * pp_de_step).  pp_profile_begin() makes every later launch of that kernel, on
+ * the calling host thread's device, bracket itself with a pair of CUDA events
+ * recorded on its own stream.  pp_profile_end() waits for the recorded events,
+ * writes the summed kernel time in milliseconds and the number of launches, and
+ * stops the recording.  Both return PP_OK or PP_ERR_CUDA. */
+int pp_profile_begin(void);
+int pp_profile_end(double *total_ms, int64_t *launches);
+
+/* Message of the last error on the calling host thread ("" if none). */
+const char *pp_last_error(void);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int pp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PP_H */

@@ -1,0 +1,209 @@
+"""GPU scoring of candidate laser pulses by the electron-positron pair number
+(arXiv 1704.08919): a thin ctypes binding over the C ABI of libpp
+(include/pp.h).  The functions take and return torch CUDA tensors and only
+marshal arguments; every step of the computation runs in the library's CUDA
+kernels.  There is no CPU fallback: calling any function without the built
+library raises.
+
+    A, E, s = synth_field(params, spec)                  # Sec. III pulse model
+    N, n    = pair_number(A, dt, grid, precision="fp32")  # Sec. II.A + Eq. (opt_prob)
+    trial   = de_propose(pop, lo, hi, periodic, F, CR, seed, gen)   # Sec. IV.B
+    de_select(pop, fit, trial, trial_fit)
+    de_step(pop, fit, spec, grid, lo, hi, periodic, F, CR, seed, gen)
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libpp.so")
+
+PP_OK = 0
+PP_ERR_INVALID_ARG = 1
+PP_ERR_CUDA = 2
+PP_ERR_NONFINITE = 3
+PP_ERR_DEGENERATE_FIELD = 4
+PP_ERR_TIMEOUT = 5
+PP_ERR_NOT_IMPLEMENTED = 6
+
+PP_FP64 = 0
+PP_FP32 = 1
+PRECISIONS = {"fp64": PP_FP64, "fp32": PP_FP32, PP_FP64: PP_FP64, PP_FP32: PP_FP32}
+
+EXPORTS = ("pp_synth_field", "pp_pair_number", "pp_de_propose", "pp_de_select", "pp_de_step",
+           "pp_sync_status", "pp_set_wait_limit", "pp_set_skip_copies", "pp_last_error",
+           "pp_version", "pp_profile_begin", "pp_profile_end")
+
+
+class PPError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("libpp error %d: %s" % (code, msg))
+        self.code = code
+
+
+class FieldSpec(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int32), ("order", ctypes.c_int32), ("w_min", ctypes.c_double),
+                ("w_max", ctypes.c_double), ("T", ctypes.c_double), ("fluence", ctypes.c_double),
+                ("n_steps", ctypes.c_int32), ("envelope", ctypes.c_int32)]
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("x0", ctypes.c_double), ("x1", ctypes.c_double), ("y0", ctypes.c_double),
+                ("y1", ctypes.c_double), ("z0", ctypes.c_double), ("z1", ctypes.c_double),
+                ("mirror_z", ctypes.c_int32)]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_d = ctypes.c_double
+_u64 = ctypes.c_uint64
+
+
+def lib():
+    """The loaded libpp.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libpp.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        L.pp_synth_field.argtypes = [_vp, _i32, ctypes.POINTER(FieldSpec), _vp, _i32, _vp, _vp, _vp]
+        L.pp_pair_number.argtypes = [_vp, _i32, _i32, _vp, _d, ctypes.POINTER(Grid), _i32, _vp, _vp,
+                                     _vp]
+        L.pp_de_propose.argtypes = [_vp, _i32, _i32, _vp, _vp, _vp, _d, _d, _u64, _u64, _vp, _vp]
+        L.pp_de_select.argtypes = [_vp, _vp, _vp, _vp, _i32, _i32, _vp]
+        L.pp_de_step.argtypes = [_vp, _vp, _i32, ctypes.POINTER(FieldSpec), ctypes.POINTER(Grid),
+                                 _i32, _vp, _vp, _vp, _d, _d, _u64, _u64, _vp, _vp, _vp]
+        L.pp_sync_status.argtypes = [_vp]
+        L.pp_set_wait_limit.argtypes = [ctypes.c_int64]
+        L.pp_set_wait_limit.restype = ctypes.c_int64
+        L.pp_set_skip_copies.argtypes = [ctypes.c_int]
+        L.pp_last_error.restype = ctypes.c_char_p
+        L.pp_profile_end.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != PP_OK:
+        raise PPError(rc, lib().pp_last_error().decode())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def field_spec(K, order, w_min, w_max, T, fluence, n_steps, envelope=0):
+    return FieldSpec(K, order, w_min, w_max, T, fluence, n_steps, envelope)
+
+
+def _spec(spec):
+    if isinstance(spec, FieldSpec):
+        return spec
+    return FieldSpec(spec["K"], spec["order"], spec["w_min"], spec["w_max"], spec["T"],
+                     spec["fluence"], spec["n_steps"], spec.get("envelope", 0))
+
+
+def _grid(grid):
+    if isinstance(grid, Grid):
+        return grid
+    return Grid(grid["nx"], grid["ny"], grid["nz"], grid["x0"], grid["x1"], grid["y0"], grid["y1"],
+                grid["z0"], grid["z1"], int(grid.get("mirror_z", 0)))
+
+
+def synth_field(params, spec, want_E=False, want_scale=False, stream=None, out=None):
+    """pp_synth_field: params [ncand, 4K] float64 CUDA -> A [ncand, 2, 2n+1] (and E, scale)."""
+    import torch
+    sp = _spec(spec)
+    ncand = params.shape[0]
+    ld = 2 * sp.n_steps + 1
+    dev = params.device
+    A = out if out is not None else torch.empty((ncand, 2, ld), dtype=torch.float64, device=dev)
+    E = torch.empty_like(A) if want_E else None
+    s = torch.empty(ncand, dtype=torch.float64, device=dev) if want_scale else None
+    _check(lib().pp_synth_field(_ptr(params), ncand, ctypes.byref(sp), _ptr(A), A.shape[-1],
+                                _ptr(E), _ptr(s), _stream(stream)))
+    return A, E, s
+
+
+def pair_number(A, dt, grid, precision="fp32", n_steps=None, want_n=False, stream=None, N_out=None):
+    """pp_pair_number: A [ncand, 2, ld] float64 CUDA -> N [ncand] (and n [ncand, nz, ny, nx])."""
+    import torch
+    g = _grid(grid)
+    ncand, _, ld = A.shape
+    N = N_out if N_out is not None else torch.empty(ncand, dtype=torch.float64, device=A.device)
+    n = (torch.empty((ncand, g.nz, g.ny, g.nx), dtype=torch.float64, device=A.device)
+         if want_n else None)
+    ns = None
+    if n_steps is not None:
+        arr = (ctypes.c_int32 * ncand)(*[int(x) for x in n_steps])
+        ns = ctypes.cast(arr, ctypes.c_void_p)
+    _check(lib().pp_pair_number(_ptr(A), ncand, ld, ns, float(dt), ctypes.byref(g),
+                                PRECISIONS[precision], _ptr(N), _ptr(n), _stream(stream)))
+    return N, n
+
+
+def de_propose(pop, lo, hi, periodic, F, CR, seed, generation, stream=None, out=None):
+    """pp_de_propose: DE/rand/1/bin trial vectors."""
+    import torch
+    NP, D = pop.shape
+    trial = out if out is not None else torch.empty_like(pop)
+    _check(lib().pp_de_propose(_ptr(pop), NP, D, _ptr(lo), _ptr(hi), _ptr(periodic), float(F),
+                               float(CR), int(seed), int(generation), _ptr(trial), _stream(stream)))
+    return trial
+
+
+def de_select(pop, fit, trial, trial_fit, stream=None):
+    """pp_de_select: greedy selection (maximisation), in place."""
+    NP, D = pop.shape
+    _check(lib().pp_de_select(_ptr(pop), _ptr(fit), _ptr(trial), _ptr(trial_fit), NP, D,
+                              _stream(stream)))
+
+
+def de_step(pop, fit, spec, grid, lo, hi, periodic, F, CR, seed, generation, precision="fp32",
+            trial_out=None, trial_fit_out=None, stream=None):
+    """pp_de_step: one DE generation (propose, synthesise, score, select) in place."""
+    sp, g = _spec(spec), _grid(grid)
+    NP = pop.shape[0]
+    _check(lib().pp_de_step(_ptr(pop), _ptr(fit), NP, ctypes.byref(sp), ctypes.byref(g),
+                            PRECISIONS[precision], _ptr(lo), _ptr(hi), _ptr(periodic), float(F),
+                            float(CR), int(seed), int(generation), _ptr(trial_out),
+                            _ptr(trial_fit_out), _stream(stream)))
+
+
+def sync_status(stream=None):
+    """pp_sync_status: wait for the stream; return (and clear) the device status code."""
+    return lib().pp_sync_status(_stream(stream))
+
+
+def profile_begin():
+    """pp_profile_begin: start timing every propagation-kernel launch with CUDA events."""
+    _check(lib().pp_profile_begin())
+
+
+def profile_end():
+    """pp_profile_end: (total kernel milliseconds, launches) since profile_begin()."""
+    ms = ctypes.c_double(0.0)
+    n = ctypes.c_int64(0)
+    _check(lib().pp_profile_end(ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
+
+
+def set_wait_limit(limit):
+    return lib().pp_set_wait_limit(int(limit))
+
+
+def set_skip_copies(skip):
+    return lib().pp_set_skip_copies(int(skip))

@@ -1,0 +1,190 @@
+// pp_field.cu -- pulse synthesis: B-spline spectral parameters -> A(t), E(t)
+// (Sec. III of arXiv 1704.08919, Eqs. (coeff_basis_E), (coeff_basis_phi),
+// (field), (energy); global renormalisation to U_const at every DE update,
+// Sec. IV.B).
+//
+// With g(t) = 1 and the DC term removed, on the half-step grid
+//     t_k = -T/2 + k h,  h = T / (2 n),  Omega_j = j 2 pi / T,
+// the phases are Omega_j t_k = -j pi + pi j k / n, so with z_k = exp(i pi k / n)
+//     E_l(t_k) = Re sum_j C_j z_k^j,         C_j = s E~_j e^{-i Phi_j} (-1)^j
+//     A_l(t_k) = -Im sum_j D_j (z_k^j - 1),  D_j = C_j / Omega_j
+// (A = -int_{-T/2}^t E, so A(-T/2) = 0 and, by periodicity, A(T/2) = 0).
+// Each sum is evaluated by Horner's rule in z_k after factoring z_k^{j_first};
+// z_k comes from sincospi of an exactly reduced argument.  The fluence of the
+// unit-scale field over one period is (T/2) sum_{l,j} E~_{l,j}^2, and
+// s = sqrt(U_const / that).
+#include <math.h>
+
+#include "pp_internal.cuh"
+
+namespace {
+
+constexpr int kMaxK = 64;
+constexpr int kMaxOrder = 8;
+
+// Cox-de Boor recursion on the clamped knot vector (order copies of w_min,
+// equidistant interior breakpoints, order copies of w_max); order-1 indicators
+// of [t_i, t_{i+1}) with the last non-empty interval closed on the right.
+__device__ void bspline_basis(int K, int order, double wmin, double wmax, double w, double *B)
+{
+    double t[kMaxK + kMaxOrder];
+    double b[kMaxK + kMaxOrder];
+    const int nk = K + order;
+    const int nbrk = K - order + 2;
+    for (int i = 0; i < order; ++i) {
+        t[i] = wmin;
+        t[K + i] = wmax;
+    }
+    for (int i = 1; i < nbrk - 1; ++i)
+        t[order - 1 + i] = wmin + (wmax - wmin) * (double)i / (double)(nbrk - 1);
+    int last = -1;
+    for (int i = 0; i < nk - 1; ++i)
+        if (t[i] < t[i + 1])
+            last = i;
+    for (int i = 0; i < nk - 1; ++i) {
+        bool inside = (t[i] <= w && w < t[i + 1]) || (i == last && w == t[i + 1]);
+        b[i] = inside ? 1.0 : 0.0;
+    }
+    for (int r = 2; r <= order; ++r) {
+        for (int i = 0; i < nk - r; ++i) {
+            double d1 = t[i + r - 1] - t[i], d2 = t[i + r] - t[i + 1];
+            double left = d1 > 0.0 ? (w - t[i]) / d1 * b[i] : 0.0;
+            double right = d2 > 0.0 ? (t[i + r] - w) / d2 * b[i + 1] : 0.0;
+            b[i] = left + right;
+        }
+    }
+    for (int i = 0; i < K; ++i)
+        B[i] = b[i];
+}
+
+// One block per candidate: spectrum at every mode, fluence, scale, and the
+// Horner coefficients coef[c][l][m] = (C, D) for mode j = j0 + m.
+__global__ void spectrum_kernel(const double *__restrict__ params, int K, int order, double wmin,
+                                double wmax, double T, double U, int j0, int M,
+                                double2 *__restrict__ coef, double *__restrict__ scale_out,
+                                unsigned int *__restrict__ status)
+{
+    __shared__ double red[256];
+    const int c = blockIdx.x;
+    const double *prm = params + (size_t)c * 4 * K;
+    const double dw = 2.0 * M_PI / T;
+    double ssq = 0.0;
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+        const int j = j0 + m;
+        const double W = (double)j * dw;
+        double B[kMaxK];
+        bspline_basis(K, order, wmin, wmax, W, B);
+        for (int l = 0; l < 2; ++l) {
+            double e = 0.0, ph = 0.0;
+            for (int i = 0; i < K; ++i) {
+                e += prm[(2 * l) * K + i] * B[i];
+                ph += prm[(2 * l + 1) * K + i] * B[i];
+            }
+            ssq += e * e;
+            double sn, cs;
+            sincos(ph, &sn, &cs);
+            const double sg = (j & 1) ? -1.0 : 1.0;
+            // unit-scale C_j = E~ e^{-i Phi} (-1)^j ; the scale is applied below
+            coef[((size_t)c * 2 + l) * 2 * M + m] = make_double2(sg * e * cs, -sg * e * sn);
+            coef[((size_t)c * 2 + l) * 2 * M + M + m] = make_double2(sg * e * cs / W, -sg * e * sn / W);
+        }
+    }
+    red[threadIdx.x] = ssq;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    const double Uraw = 0.5 * T * red[0];
+    const double s = Uraw > 0.0 ? sqrt(U / Uraw) : 0.0;
+    if (threadIdx.x == 0) {
+        if (!(Uraw > 0.0))
+            pp_flag(status, PP_FLAG_DEGENERATE);
+        if (scale_out)
+            scale_out[c] = s;
+    }
+    for (int q = threadIdx.x; q < 4 * M; q += blockDim.x) {
+        double2 v = coef[(size_t)c * 4 * M + q];
+        coef[(size_t)c * 4 * M + q] = make_double2(s * v.x, s * v.y);
+    }
+}
+
+// Samples: grid (ceil(nsamp / 256), ncand, 2 polarisations).
+__global__ void samples_kernel(const double2 *__restrict__ coef, int M, int j0, int n_steps,
+                               int ld, double *__restrict__ A, double *__restrict__ E)
+{
+    extern __shared__ double2 sc[];  // [2M]: C then D
+    const int c = blockIdx.y, l = blockIdx.z;
+    const double2 *cf = coef + ((size_t)c * 2 + l) * 2 * M;
+    for (int q = threadIdx.x; q < 2 * M; q += blockDim.x)
+        sc[q] = cf[q];
+    __syncthreads();
+    const int nsamp = 2 * n_steps + 1;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nsamp)
+        return;
+    // z = exp(i pi k / n), zj0 = z^{j0}; arguments reduced exactly modulo 2n
+    const long long two_n = 2ll * n_steps;
+    double zs, zc, js, jc;
+    sincospi((double)(k % two_n) / (double)n_steps, &zs, &zc);
+    sincospi((double)(((long long)k * j0) % two_n) / (double)n_steps, &js, &jc);
+    // Horner: sum_{m=0}^{M-1} X_m z^m
+    double cr = 0.0, ci = 0.0, dr = 0.0, di = 0.0;
+    double d0r = 0.0, d0i = 0.0;  // sum of D_j (the z = 1 value)
+    for (int m = M - 1; m >= 0; --m) {
+        const double2 C = sc[m], D = sc[M + m];
+        double tr = cr * zc - ci * zs + C.x;
+        ci = cr * zs + ci * zc + C.y;
+        cr = tr;
+        tr = dr * zc - di * zs + D.x;
+        di = dr * zs + di * zc + D.y;
+        dr = tr;
+        d0r += D.x;
+        d0i += D.y;
+    }
+    // multiply by z^{j0}
+    const double Cr = cr * jc - ci * js;
+    const double Di = dr * js + di * jc;
+    double *Arow = A + ((size_t)c * 2 + l) * ld;
+    Arow[k] = -(Di - d0i);
+    if (E)
+        E[((size_t)c * 2 + l) * ld + k] = Cr;
+    (void)d0r;
+}
+
+}  // namespace
+
+namespace pp {
+
+int launch_synth_field(const double *params, int ncand, const pp_field_spec *spec, double *A, int ld,
+                       double *E, double *scale, cudaStream_t stream)
+{
+    const double dw = 2.0 * M_PI / spec->T;
+    int j0 = (int)ceil(spec->w_min / dw - 1e-12);
+    if (j0 < 1)
+        j0 = 1;
+    const int j1 = (int)floor(spec->w_max / dw + 1e-12);
+    const int M = j1 - j0 + 1;
+    void *coef = nullptr;
+    int rc = scratch(SCR_COEF, (size_t)ncand * 4 * M * sizeof(double2), &coef);
+    if (rc)
+        return rc;
+    if (ncand == 0)
+        return PP_OK;
+    unsigned int *status = status_word();
+    if (!status)
+        return fail(PP_ERR_CUDA, "status word unavailable");
+    spectrum_kernel<<<ncand, 128, 0, stream>>>(params, spec->K, spec->order, spec->w_min, spec->w_max,
+                                               spec->T, spec->fluence, j0, M, (double2 *)coef, scale, status);
+    const int nsamp = 2 * spec->n_steps + 1;
+    dim3 g((nsamp + 255) / 256, ncand, 2);
+    samples_kernel<<<g, 256, 2 * M * sizeof(double2), stream>>>((const double2 *)coef, M, j0,
+                                                                spec->n_steps, ld, A, E);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return cuda_fail(e, "synthesis kernel launch");
+    return PP_OK;
+}
+
+}  // namespace pp

@@ -1,0 +1,124 @@
+// pp_internal.cuh -- private declarations shared by the libpp translation units
+// (status word, scratch, launch helpers, inline-PTX wrappers for mbarriers and
+// 1-D bulk copies on sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pp.h"
+
+// ---------------------------------------------------------------- device status word
+// Bits set by kernels with atomicOr on the word whose device address
+// pp::status_word() returns; collected and cleared by pp_sync_status.
+#define PP_FLAG_TIMEOUT 1u
+#define PP_FLAG_NONFINITE 2u
+#define PP_FLAG_DEGENERATE 4u
+
+__device__ __forceinline__ void pp_flag(unsigned int *status, unsigned int bit) { atomicOr(status, bit); }
+
+// ---------------------------------------------------------------- host helpers
+namespace pp {
+
+// Thread-local error message; returns `code` for convenient `return fail(...)`.
+int fail(int code, const char *fmt, ...);
+int cuda_fail(cudaError_t e, const char *what);
+void clear_error();
+
+// Per-device grow-only scratch buffers (slot index -> pointer).  Growth
+// synchronises the device, frees the old buffer and allocates a new one.
+enum ScratchSlot { SCR_TABLE = 0, SCR_PARTIAL, SCR_A, SCR_TRIAL, SCR_TFIT, SCR_COEF, SCR_NSLOTS };
+int scratch(int slot, size_t bytes, void **ptr);
+
+// Device address of the status word of the current device (nullptr on failure).
+unsigned int *status_word();
+
+// Kernel-timing hooks around the propagation kernel (no-ops unless profiling).
+void profile_mark_start(cudaStream_t stream);
+void profile_mark_stop(cudaStream_t stream);
+
+int64_t wait_limit();
+int skip_copies();
+
+// Launch the propagation for one precision (pp_propagate.cu).
+int launch_pair_number(const double *A, int ncand, int ld, const int32_t *n_steps_host, double dt,
+                       const pp_grid *grid, int precision, double *N, double *n_p,
+                       cudaStream_t stream);
+
+// Field synthesis launch without argument re-validation (pp_field.cu).
+int launch_synth_field(const double *params, int ncand, const pp_field_spec *spec, double *A,
+                       int ld, double *E, double *scale, cudaStream_t stream);
+
+// DE launches (pp_de.cu).
+int launch_de_propose(const double *pop, int NP, int D, const double *lo, const double *hi,
+                      const uint8_t *periodic, double F, double CR, uint64_t seed, uint64_t gen,
+                      double *trial, cudaStream_t stream);
+int launch_de_select(double *pop, double *fit, const double *trial, const double *trial_fit,
+                     int NP, int D, cudaStream_t stream);
+
+}  // namespace pp
+
+// ---------------------------------------------------------------- inline PTX (sm_90+)
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+// Make barrier initialisation visible to the asynchronous (bulk-copy) proxy.
+__device__ __forceinline__ void mbar_fence_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\t"
+        "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_u32(bar)),
+        "r"(bytes)
+        : "memory");
+}
+
+// Non-blocking test of phase `parity`; true once that phase has completed.
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: polls at most `limit` times; false if the phase never completed.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int64_t limit)
+{
+    for (int64_t it = 0; it < limit; ++it) {
+        if (mbar_test_wait(bar, parity))
+            return true;
+        if (it > 64)
+            __nanosleep(32);
+    }
+    return false;
+}
+
+// 1-D bulk copy global -> shared (TMA engine), completion counted on `bar`.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes,
+                                              uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}

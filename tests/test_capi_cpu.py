@@ -1,0 +1,96 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every entry point that include/pp.h declares, and rejects bad arguments on the
+host before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def pp():
+    from paper_1704_08919_gb300 import build
+    build.build()
+    import paper_1704_08919_gb300 as pp
+    pp.lib()
+    return pp
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "pp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pp_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_the_entry_points():
+    names = declared_symbols()
+    for n in ("pp_synth_field", "pp_pair_number", "pp_de_propose", "pp_de_select", "pp_de_step",
+              "pp_sync_status", "pp_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(pp):
+    L = pp.lib()
+    for name in declared_symbols():
+        assert hasattr(L, name), name
+    assert set(pp.EXPORTS) <= set(declared_symbols())
+    assert L.pp_version() >= 100
+
+
+def test_host_validation_rejects_bad_arguments(pp):
+    L = pp.lib()
+    g = pp.Grid(0, 4, 4, -1, 1, -1, 1, 0, 1, 1)
+    rc = L.pp_pair_number(ctypes.c_void_p(8), 1, 101, None, 0.1, ctypes.byref(g), 0,
+                          ctypes.c_void_p(8), None, None)
+    assert rc == pp.PP_ERR_INVALID_ARG
+    assert b"grid sizes" in L.pp_last_error()
+    g = pp.Grid(4, 4, 4, -1, 1, -1, 1, 0.5, 1, 1)
+    rc = L.pp_pair_number(ctypes.c_void_p(8), 1, 101, None, 0.1, ctypes.byref(g), 0,
+                          ctypes.c_void_p(8), None, None)
+    assert rc == pp.PP_ERR_INVALID_ARG and b"mirror_z" in L.pp_last_error()
+    g = pp.Grid(4, 4, 4, -1, 1, -1, 1, 0, 1, 1)
+    rc = L.pp_pair_number(ctypes.c_void_p(8), 1, 101, None, -0.1, ctypes.byref(g), 0,
+                          ctypes.c_void_p(8), None, None)
+    assert rc == pp.PP_ERR_INVALID_ARG and b"dt" in L.pp_last_error()
+    rc = L.pp_pair_number(ctypes.c_void_p(8), 1, 101, None, 0.1, ctypes.byref(g), 7,
+                          ctypes.c_void_p(8), None, None)
+    assert rc == pp.PP_ERR_INVALID_ARG and b"precision" in L.pp_last_error()
+    ns = (ctypes.c_int32 * 1)(60)
+    rc = L.pp_pair_number(ctypes.c_void_p(8), 1, 101, ctypes.cast(ns, ctypes.c_void_p), 0.1,
+                          ctypes.byref(g), 0, ctypes.c_void_p(8), None, None)
+    assert rc == pp.PP_ERR_INVALID_ARG and b"n_steps" in L.pp_last_error()
+    rc = L.pp_de_propose(ctypes.c_void_p(8), 3, 4, ctypes.c_void_p(8), ctypes.c_void_p(8), None,
+                         0.5, 0.9, 1, 0, ctypes.c_void_p(8), None)
+    assert rc == pp.PP_ERR_INVALID_ARG and b"NP" in L.pp_last_error()
+    rc = L.pp_de_propose(ctypes.c_void_p(8), 8, 4, ctypes.c_void_p(8), ctypes.c_void_p(8), None,
+                         0.5, 1.5, 1, 0, ctypes.c_void_p(8), None)
+    assert rc == pp.PP_ERR_INVALID_ARG and b"CR" in L.pp_last_error()
+    spec = pp.FieldSpec(8, 9, 0.0, 2.0, 200.0, 2.0, 100, 0)
+    rc = L.pp_synth_field(ctypes.c_void_p(8), 1, ctypes.byref(spec), ctypes.c_void_p(8), 201, None,
+                          None, None)
+    assert rc == pp.PP_ERR_INVALID_ARG and b"order" in L.pp_last_error()
+    spec = pp.FieldSpec(8, 4, 0.0, 0.01, 200.0, 2.0, 100, 0)
+    rc = L.pp_synth_field(ctypes.c_void_p(8), 1, ctypes.byref(spec), ctypes.c_void_p(8), 201, None,
+                          None, None)
+    assert rc == pp.PP_ERR_INVALID_ARG and b"no mode" in L.pp_last_error()
+    spec = pp.FieldSpec(8, 4, 0.0, 2.0, 200.0, 2.0, 100, 0)
+    rc = L.pp_synth_field(ctypes.c_void_p(8), 1, ctypes.byref(spec), ctypes.c_void_p(8), 200, None,
+                          None, None)
+    assert rc == pp.PP_ERR_INVALID_ARG and b"ld" in L.pp_last_error()
+    spec = pp.FieldSpec(8, 4, 0.0, 2.0, 200.0, 2.0, 100, 1)
+    rc = L.pp_synth_field(ctypes.c_void_p(8), 1, ctypes.byref(spec), ctypes.c_void_p(8), 201, None,
+                          None, None)
+    assert rc == pp.PP_ERR_NOT_IMPLEMENTED
+
+
+def test_product_package_does_not_import_the_oracle():
+    pkg = os.path.join(ROOT, "paper_1704_08919_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle\b", txt, re.M), f
+                assert "pp_oracle" not in txt and "liboracle" not in txt, f

