@@ -717,6 +717,9 @@ static int below(uint64_t x, int n)
  *  3. binomial crossover: y_j = u_j if r_j <= CR or j == R, else x_ij.
  * Coordinates taken from u are brought back into bounds: periodic ones
  * (phases) are wrapped into [lo, hi), the others clipped to [lo, hi].
+ * The paper does not say how the donors are drawn; here each is drawn by
+ * rejection from at most 62 random slots, and if the slots run out (possible
+ * only for tiny populations) the trial is a copy of the parent.
  * pop[NP][D] -> trial[NP][D].  Returns ORC_ERR_ARG when NP < 4. */
 int orc_de_propose(const double *pop, int NP, int D, const double *lo, const double *hi,
                    const uint8_t *periodic, double F, double CR, uint64_t seed, uint64_t gen,
@@ -727,21 +730,26 @@ int orc_de_propose(const double *pop, int NP, int D, const double *lo, const dou
     uint64_t gkey = orc_splitmix64_at(seed, gen);
     for (int i = 0; i < NP; i++) {
         uint64_t key = orc_splitmix64_at(gkey, (uint64_t)i);
-        int r[3];
-        int slot = 0;
-        for (int q = 0; q < 3; q++) {
-            for (;;) {
-                if (slot >= DE_MAX_DRAWS)
-                    return ORC_ERR_ARG;
+        int r[3] = {-1, -1, -1};
+        int slot = 0, found_all = 1;
+        for (int q = 0; q < 3 && found_all; q++) {
+            found_all = 0;
+            while (slot < DE_MAX_DRAWS) {
                 int cand = below(orc_splitmix64_at(key, (uint64_t)slot++), NP);
                 int clash = (cand == i);
                 for (int z = 0; z < q; z++)
                     clash |= (cand == r[z]);
                 if (!clash) {
                     r[q] = cand;
+                    found_all = 1;
                     break;
                 }
             }
+        }
+        if (!found_all) {
+            /* the donor draws ran out of random slots: the trial is the parent */
+            memcpy(trial + (size_t)i * D, pop + (size_t)i * D, sizeof(double) * D);
+            continue;
         }
         int R = below(orc_splitmix64_at(key, DE_SLOT_R), D);
         const double *xa = pop + (size_t)r[0] * D, *xb = pop + (size_t)r[1] * D,
