@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--cpu-modes", type=int, default=8192,
                     help="modes of one candidate in the CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ncand", type=int, default=CFG["NP"],
+                    help="population size (smaller values only for profiling runs)")
     return ap.parse_args()
 
 
@@ -60,11 +63,31 @@ def dist_env():
     return ws, rank, local
 
 
-def workload_config(precision):
+def rank_seeds(rank):
+    """(population seed, DE seed) of a rank: every rank evolves its own population."""
+    return 1 + rank, 1000 + rank
+
+
+def max_over_ranks(x, dist=None, device=None):
+    """The maximum of a per-rank scalar over all ranks (x itself without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def throughput(world_size, NP, steps, total_ms):
+    """Candidates scored per second by the whole job (weak scaling: NP per rank per step)."""
+    return world_size * NP * steps / (total_ms / 1000.0)
+
+
+def workload_config(precision, NP=None):
     g = CFG["grid"]
     return {
         "workload": CFG["name"],
-        "NP": CFG["NP"], "K": CFG["K"], "order": CFG["order"], "T": CFG["T"],
+        "NP": NP or CFG["NP"], "K": CFG["K"], "order": CFG["order"], "T": CFG["T"],
         "n_steps": CFG["n_steps"], "fluence": CFG["fluence"],
         "grid": "%dx%dx%d px,py in [%g,%g], pz in [%g,%g] mirrored" % (
             g["nx"], g["ny"], g["nz"], g["x0"], g["x1"], g["z0"], g["z1"]),
@@ -201,13 +224,13 @@ def main():
     pp.lib()
     stream = torch.cuda.current_stream()
 
-    NP, K = CFG["NP"], CFG["K"]
+    NP, K = args.ncand, CFG["K"]
     spec = inputs.field_spec(CFG)
     grid = CFG["grid"]
     dt = CFG["T"] / CFG["n_steps"]
     lo, hi, per = inputs.param_bounds(K)
-    seed = 1000 + rank
-    pop0 = inputs.random_population(NP, K, seed=1 + rank)
+    pop_seed, seed = rank_seeds(rank)
+    pop0 = inputs.random_population(NP, K, seed=pop_seed)
     lo_t, hi_t = torch.tensor(lo, device=dev), torch.tensor(hi, device=dev)
     per_t = torch.tensor(per, device=dev)
     pop = torch.tensor(pop0, device=dev)
@@ -252,13 +275,9 @@ def main():
     if st != pp.PP_OK:
         raise RuntimeError("device status %d after the timed region" % st)
     step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
-    total_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = t.item()
+    total_ms = max_over_ranks(sum(step_ms), dist, dev)
     ms_per_step = total_ms / args.steps
-    cand_per_s = ws * NP * args.steps / (total_ms / 1000.0)
+    cand_per_s = throughput(ws, NP, args.steps, total_ms)
     mode_steps_per_s = cand_per_s * units_per_candidate()
 
     # ---- live roofline of the propagation kernel
@@ -286,7 +305,7 @@ def main():
     pop_h = torch.tensor(pop0, dtype=torch.float64).pin_memory()
     fit_h = fit.cpu().pin_memory()
     e2e_times = []
-    for s in range(args.steps):
+    for s in range(0 if args.no_e2e else args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         pop.copy_(pop_h, non_blocking=True)
@@ -298,12 +317,8 @@ def main():
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t0)
         gen += 1
-    e2e_total = sum(e2e_times)
-    if dist is not None:
-        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = t.item()
-    e2e_value = ws * NP * args.steps / e2e_total
+    e2e_total = max_over_ranks(sum(e2e_times) if e2e_times else float("nan"), dist, dev)
+    e2e_value = throughput(ws, NP, args.steps, 1000.0 * e2e_total)
     h2d = pop_h.numel() * 8 + fit_h.numel() * 8
 
     # ---- CPU-oracle baseline (rank 0, N = 1 only)
@@ -330,7 +345,7 @@ def main():
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.precision == "fp32" else "f64",
             "data": "synthetic (seeded B-spline pulses, uniform in bounds)",
-            "config": workload_config(args.precision),
+            "config": workload_config(args.precision, NP),
             "mode_steps_per_s": mode_steps_per_s,
             "n_rel_err_fp32_vs_fp64_max": rel_err,
             "roofline": roofline,

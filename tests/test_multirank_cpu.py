@@ -1,0 +1,57 @@
+"""The N > 1 launch path of bench.py on CPU: two gloo ranks exchange only the
+timing maximum; each rank evolves its own population (weak scaling)."""
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ws, r, local = bench.dist_env()
+    local_ms = 100.0 + 50.0 * rank
+    m = bench.max_over_ranks(local_ms, dist, "cpu")
+    seeds = bench.rank_seeds(r)
+    dist.barrier()
+    dist.destroy_process_group()
+    q.put((rank, ws, m, seeds, bench.throughput(ws, 64, 5, m)))
+
+
+def test_two_gloo_ranks_share_only_the_timing_maximum():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    (r0, ws0, m0, s0, v0), (r1, ws1, m1, s1, v1) = res
+    assert ws0 == ws1 == 2
+    assert m0 == m1 == 150.0
+    assert s0 != s1 and s0[0] != s1[0] and s0[1] != s1[1]
+    # weak scaling: 2 ranks x 64 candidates x 5 steps in the slowest rank's time
+    assert abs(v0 - 2 * 64 * 5 / 0.150) < 1e-9 and v0 == v1
+
+
+def test_single_process_needs_no_process_group():
+    import bench
+    assert bench.max_over_ranks(3.5) == 3.5
+    assert bench.dist_env()[0] >= 1
