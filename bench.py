@@ -31,10 +31,14 @@ if ROOT not in sys.path:
 from paper_1704_08919_gb300 import inputs  # noqa: E402
 
 CFG = inputs.DE_BATCH
-# FP32 operation count of one mode-step of the propagation kernel (both spin
-# channels, RK4 increment form, compensated accumulation), FMA = 2.
-FLOP_PER_MODE_STEP_FP32 = 268
-FLOP_PER_MODE_STEP_FP64 = 244
+# Arithmetic of one mode-step (one momentum mode, both spin channels, one
+# step) of the propagation kernel, counted from its source: (flop with
+# FMA = 2, FP32/FP64 instructions).  FP32 paths use compensated accumulation.
+#  rk4:     4 matrix applications, 3 stage updates, increment sum, Fast2Sum
+#  magnus4: dt h_eff, |.|^2, cos-1 and sinc polynomials, scaled vector, increment, Fast2Sum
+#  split2:  coupling factor, stage, free factor, Fast2Sum
+WORK = {("fp32", "rk4"): (268, 184), ("fp32", "magnus4"): (136, 98), ("fp32", "split2"): (144, 96),
+        ("fp64", "rk4"): (244, 148), ("fp64", "magnus4"): (112, 74), ("fp64", "split2"): (120, 72)}
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 L2_FLUSH_BYTES = 256 << 20
@@ -47,6 +51,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--scheme", default="magnus4", choices=["magnus4", "rk4", "split2"])
     ap.add_argument("--cpu-modes", type=int, default=8192,
                     help="modes of one candidate in the CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -83,10 +88,10 @@ def throughput(world_size, NP, steps, total_ms):
     return world_size * NP * steps / (total_ms / 1000.0)
 
 
-def workload_config(precision, NP=None):
+def workload_config(precision, NP=None, scheme="rk4"):
     g = CFG["grid"]
     return {
-        "workload": CFG["name"],
+        "workload": CFG["name"], "scheme": scheme,
         "NP": NP or CFG["NP"], "K": CFG["K"], "order": CFG["order"], "T": CFG["T"],
         "n_steps": CFG["n_steps"], "fluence": CFG["fluence"],
         "grid": "%dx%dx%d px,py in [%g,%g], pz in [%g,%g] mirrored" % (
@@ -193,7 +198,7 @@ def reference_main(args):
         "value": cand_per_s, "unit": "candidates/s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000.0 * CFG["NP"] / cand_per_s,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (seeded B-spline pulses)", "config": workload_config("fp64"),
+        "data": "synthetic (seeded B-spline pulses)", "config": workload_config("fp64", None, "rk4"),
         "impl": "reference", "mode_steps_per_s": 1.0 / per_mode_step,
         "cpu_baseline": {"value": cand_per_s, "unit": "candidates/s", "cores": cores,
                          "kind": "oracle", "sample": sample},
@@ -235,7 +240,7 @@ def main():
     per_t = torch.tensor(per, device=dev)
     pop = torch.tensor(pop0, device=dev)
     A, _, _ = pp.synth_field(pop, spec)
-    fit, _ = pp.pair_number(A, dt, grid, precision=args.precision)
+    fit, _ = pp.pair_number(A, dt, grid, precision=args.precision, scheme=args.scheme)
     trial = torch.empty_like(pop)
     tfit = torch.empty_like(fit)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -245,7 +250,8 @@ def main():
     gen = 0
     for _ in range(max(args.warmup, 0)):
         pp.de_step(pop, fit, spec, grid, lo_t, hi_t, per_t, CFG["F"], CFG["CR"], seed, gen,
-                   precision=args.precision, trial_out=trial, trial_fit_out=tfit)
+                   precision=args.precision, trial_out=trial, trial_fit_out=tfit,
+                   scheme=args.scheme)
         gen += 1
     torch.cuda.synchronize()
 
@@ -264,7 +270,8 @@ def main():
         flush.zero_()
         starts[s].record(stream)
         pp.de_step(pop, fit, spec, grid, lo_t, hi_t, per_t, CFG["F"], CFG["CR"], seed, gen,
-                   precision=args.precision, trial_out=trial, trial_fit_out=tfit)
+                   precision=args.precision, trial_out=trial, trial_fit_out=tfit,
+                   scheme=args.scheme)
         ends[s].record(stream)
         gen += 1
     torch.cuda.synchronize()
@@ -282,22 +289,32 @@ def main():
 
     # ---- live roofline of the propagation kernel
     per_launch_ms = kern_ms / max(kern_launches, 1)
-    flop = FLOP_PER_MODE_STEP_FP32 if args.precision == "fp32" else FLOP_PER_MODE_STEP_FP64
-    achieved = flop * NP * units_per_candidate() / (per_launch_ms / 1000.0) / 1e12
-    peak_fp32 = SM_COUNT * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
-    roofline = {"bound": "alu", "kernel": "propagate_kernel<%s>" % (
-        "float, compensated" if args.precision == "fp32" else "double"),
-        "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
-        "frac": achieved / peak_fp32,
-        "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)",
-        "flop_per_mode_step": flop, "launch_ms": per_launch_ms,
+    flop, inst = WORK[(args.precision, args.scheme)]
+    units = NP * units_per_candidate()
+    achieved = flop * units / (per_launch_ms / 1000.0) / 1e12
+    if args.precision == "fp32":
+        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
+        peak_src = "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)"
+        lanes = SM_COUNT * FP32_LANES_PER_SM * 2070e6
+    else:
+        peak = 1.25
+        peak_src = "nominal GB300 FP64 (no measured FP64 peak available)"
+        lanes = peak * 1e12 / 2
+    roofline = {"bound": "alu", "kernel": "propagate_kernel<%s, %s>" % (args.scheme, (
+        "float, compensated" if args.precision == "fp32" else "double")),
+        "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+        "frac": achieved / peak, "peak_source": peak_src,
+        "flop_per_mode_step": flop, "inst_per_mode_step": inst,
+        "pipe_frac": inst * units / (per_launch_ms / 1000.0) / lanes,
+        "launch_ms": per_launch_ms,
         "kernel_share_of_step": kern_ms / total_ms if ws == 1 else None,
         "traffic": None}
 
-    # ---- accuracy at the bench config: FP32 N vs FP64 N on 4 candidates of the final population
+    # ---- accuracy at the bench config: N of the timed path vs FP64 RK4 (the oracle's
+    # algorithm, parity-tested against it) on 4 candidates of the final population
     Acheck, _, _ = pp.synth_field(pop[:4].contiguous(), spec)
-    N32, _ = pp.pair_number(Acheck, dt, grid, precision="fp32")
-    N64, n64 = pp.pair_number(Acheck, dt, grid, precision="fp64", want_n=True)
+    N32, _ = pp.pair_number(Acheck, dt, grid, precision=args.precision, scheme=args.scheme)
+    N64, n64 = pp.pair_number(Acheck, dt, grid, precision="fp64", scheme="rk4", want_n=True)
     pp.sync_status()
     rel_err = (N32 / N64 - 1).abs().max().item()
 
@@ -311,7 +328,8 @@ def main():
         pop.copy_(pop_h, non_blocking=True)
         fit.copy_(fit_h, non_blocking=True)
         pp.de_step(pop, fit, spec, grid, lo_t, hi_t, per_t, CFG["F"], CFG["CR"], seed, gen,
-                   precision=args.precision, trial_out=trial, trial_fit_out=tfit)
+                   precision=args.precision, trial_out=trial, trial_fit_out=tfit,
+                   scheme=args.scheme)
         pop_h.copy_(pop, non_blocking=True)
         fit_h.copy_(fit, non_blocking=True)
         torch.cuda.synchronize()
@@ -344,10 +362,11 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.precision == "fp32" else "f64",
+            "scheme": args.scheme,
             "data": "synthetic (seeded B-spline pulses, uniform in bounds)",
-            "config": workload_config(args.precision, NP),
+            "config": workload_config(args.precision, NP, args.scheme),
             "mode_steps_per_s": mode_steps_per_s,
-            "n_rel_err_fp32_vs_fp64_max": rel_err,
+            "n_rel_err_vs_fp64_rk4_max": rel_err,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "candidates/s", "h2d_bytes_per_step": h2d,

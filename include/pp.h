@@ -51,6 +51,19 @@ typedef enum {
                     FP64 initial state, projection and momentum sum */
 } pp_precision;
 
+/* Time integrator of the momentum-space Dirac equation (all on the same grid:
+ * step dt, potential samples at t_n, t_n + dt/2, t_n + dt).
+ *  PP_RK4     classical fourth-order Runge-Kutta (the integrator of the paper's
+ *             kinetic equation, Sec. II.B, applied to the Dirac equation); the
+ *             parity path against the CPU oracle.
+ *  PP_MAGNUS4 fourth-order Magnus step exp(Omega), Omega = -i dt/6 (H_0 + 4 H_h +
+ *             H_1) + dt^2/12 [H_0, H_1]: unitary; the fourth-order scheme the
+ *             paper's outlook (Sec. V.C.2) calls for.
+ *  PP_SPLIT2  second-order Strang split operator, the paper's own integrator
+ *             (Sec. II.A): constant part beta + alpha_z p_z, field part
+ *             alpha_x P_x + alpha_y P_y at t_n + dt/2; unitary. */
+typedef enum { PP_RK4 = 0, PP_MAGNUS4 = 1, PP_SPLIT2 = 2 } pp_scheme;
+
 /* Pulse model of Sec. III of the paper.
  *  K        B-spline coefficients per amplitude and per phase and polarisation (N_s).
  *  order    B-spline order k (k = 4: cubic; the paper's tables use k = 3).
@@ -101,8 +114,8 @@ int pp_synth_field(const double *params, int32_t ncand, const pp_field_spec *spe
  * (wf_init), (dirac_eq_mom), (pair_prod_homo); Eq. (opt_prob)).
  * For every momentum p of the grid and both spin states, the momentum-space
  * Dirac equation i d/dt psi = [alpha.(p - A(t)) + beta] psi is integrated with
- * classical RK4 (step dt, stage times t_n, t_n + dt/2, t_n + dt taken from
- * samples 2n, 2n+1, 2n+2 of A) from the negative-energy state at p - A(t_0);
+ * the chosen scheme (step dt; times t_n, t_n + dt/2, t_n + dt take samples
+ * 2n, 2n+1, 2n+2 of A) from the negative-energy state at p - A(t_0);
  * f(p) = sum over both spins of the squared projections onto the positive-
  * energy states at p - A(t_end) (the full spin trace); N = sum_p w(p) f(p)
  * with trapezoid weights per axis.
@@ -112,12 +125,15 @@ int pp_synth_field(const double *params, int32_t ncand, const pp_field_spec *spe
  *  dt      step size (> 0).
  *  grid    (host)   momentum grid shared by all candidates.
  *  precision PP_FP64 or PP_FP32.
+ *  scheme  PP_RK4, PP_MAGNUS4 or PP_SPLIT2.
  *  N       (device) [ncand] FP64 output.
  *  n_p     (device) [ncand][nz][ny][nx] FP64 output (x fastest), or NULL.
  * The sum over p is taken in a fixed order: results are bitwise reproducible
- * run to run.  Errors: INVALID_ARG (sizes, null pointers, dt <= 0, bad precision). */
+ * run to run.  Errors: INVALID_ARG (sizes, null pointers, dt <= 0, bad precision
+ * or scheme). */
 int pp_pair_number(const double *A, int32_t ncand, int32_t ld, const int32_t *n_steps, double dt,
-                   const pp_grid *grid, int32_t precision, double *N, double *n_p, void *stream);
+                   const pp_grid *grid, int32_t precision, int32_t scheme, double *N, double *n_p,
+                   void *stream);
 
 /* DE/rand/1/bin trial vectors (Sec. IV.B, steps 1-3).  For each individual i:
  * three distinct donors r1, r2, r3 != i; u = x_r1 + F (x_r2 - x_r3); binomial
@@ -148,7 +164,7 @@ int pp_de_select(double *pop, double *fit, const double *trial, const double *tr
  * [NP][4K]) and trial_fit_out (device, [NP]) receive the scored trials or may
  * be NULL.  The potential buffer and the trials live in library scratch. */
 int pp_de_step(double *pop, double *fit, int32_t NP, const pp_field_spec *spec,
-               const pp_grid *grid, int32_t precision, const double *lo, const double *hi,
+               const pp_grid *grid, int32_t precision, int32_t scheme, const double *lo, const double *hi,
                const uint8_t *periodic, double F, double CR, uint64_t seed, uint64_t generation,
                double *trial_out, double *trial_fit_out, void *stream);
 

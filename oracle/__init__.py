@@ -41,6 +41,8 @@ def lib():
         L.orc_dirac_mode.argtypes = [_pd, _i, _i, _d, _pd, _i, ctypes.c_void_p]
         L.orc_dirac_mode.restype = _d
         L.orc_dirac_modes.argtypes = [_pd, _i, _i, _d, _pd, _i, _i, _pd, _i]
+        L.orc_dirac_split_modes.argtypes = [_pd, _i, _i, _d, _pd, _i, _pd, _pd, _i]
+        L.orc_dirac_magnus_modes.argtypes = [_pd, _i, _i, _d, _pd, _i, _pd, _pd, _i]
         L.orc_qke6_modes.argtypes = [_pd, _pd, _pd, _i, _i, _d, _pd, _i, _pd, _i]
         L.orc_trapz_weights.argtypes = [_i, _d, _d, _i, _pd]
         L.orc_trapz_weights.restype = None
@@ -142,6 +144,32 @@ def dirac_modes(A, n_steps, dt, p, spin_sum=0, nthreads=0):
     if rc:
         raise ValueError("orc_dirac_modes rc=%d" % rc)
     return out
+
+
+def dirac_split_modes(A, n_steps, dt, p, nthreads=0):
+    """(f, norm deviation) per momentum with the second-order split operator (Sec. II.A)."""
+    A = _f64(A).reshape(2, -1)
+    p = _f64(p).reshape(-1, 3)
+    out = np.zeros(p.shape[0])
+    dev = np.zeros(p.shape[0])
+    rc = lib().orc_dirac_split_modes(_p(A), A.shape[1], n_steps, dt, _p(p), p.shape[0], _p(out),
+                                     _p(dev), nthreads)
+    if rc:
+        raise ValueError("orc_dirac_split_modes rc=%d" % rc)
+    return out, dev
+
+
+def dirac_magnus_modes(A, n_steps, dt, p, nthreads=0):
+    """(f, norm deviation) per momentum with the fourth-order Magnus step."""
+    A = _f64(A).reshape(2, -1)
+    p = _f64(p).reshape(-1, 3)
+    out = np.zeros(p.shape[0])
+    dev = np.zeros(p.shape[0])
+    rc = lib().orc_dirac_magnus_modes(_p(A), A.shape[1], n_steps, dt, _p(p), p.shape[0],
+                                      _p(out), _p(dev), nthreads)
+    if rc:
+        raise ValueError("orc_dirac_magnus_modes rc=%d" % rc)
+    return out, dev
 
 
 def qke6_modes(A, E, Edot, n_steps, dt, p, nthreads=0):

@@ -445,6 +445,201 @@ double orc_dirac_mode(const double *A, int ld, int n_steps, double dt, const dou
 }
 
 /* ------------------------------------------------------------------------- */
+/* Second-order split operator (Sec. II.A: the paper propagates the Dirac    */
+/* equation with "a simple split-operator method with a second order         */
+/* convergence"; the splitting is not given).  Reading: Strang splitting of  */
+/* H(t) = H_0 + V(t) into the free Hamiltonian H_0 = alpha.p + beta and the  */
+/* coupling to the field V(t) = -alpha.A(t), the latter at t_n + dt/2:        */
+/*   psi_{n+1} = e^{-i H_0 dt/2} e^{-i V(t_n + dt/2) dt} e^{-i H_0 dt/2} psi_n */
+/* Both parts square to multiples of the identity (H_0^2 = (p^2 + 1) 1,      */
+/* V^2 = |A|^2 1 for A in the x-y plane), so each factor is exactly          */
+/* cos(k tau) - i sin(k tau) K / k, and free propagation (A = 0) is exact.   */
+/* ------------------------------------------------------------------------- */
+
+/* U = exp(-i K tau) for Hermitian K with K^2 = k2 * 1. */
+static void expm_squared_scalar(cplx K[4][4], double k2, double tau, cplx U[4][4])
+{
+    double k = sqrt(k2);
+    double c = cos(k * tau);
+    double sk = k > 0.0 ? sin(k * tau) / k : tau;
+    for (int i = 0; i < 4; i++)
+        for (int j = 0; j < 4; j++)
+            U[i][j] = (i == j ? c : 0.0) - I * sk * K[i][j];
+}
+
+static void matvec4(cplx U[4][4], const cplx x[4], cplx y[4])
+{
+    for (int i = 0; i < 4; i++) {
+        cplx acc = 0;
+        for (int j = 0; j < 4; j++)
+            acc += U[i][j] * x[j];
+        y[i] = acc;
+    }
+}
+
+/* f(t_f, p) as orc_dirac_mode (full spin trace), propagated with the split
+ * operator; *norm_dev receives max_s | |psi_s(t_f)|^2 / |psi_s(t_0)|^2 - 1 |. */
+double orc_dirac_split_mode(const double *A, int ld, int n_steps, double dt, const double p[3],
+                            double *norm_dev)
+{
+    dirac_mats D;
+    make_dirac_mats(&D);
+    const double *Ax = A, *Ay = A + ld;
+    double Pin[3] = {p[0] - Ax[0], p[1] - Ay[0], p[2]};
+    double Pout[3] = {p[0] - Ax[2 * n_steps], p[1] - Ay[2 * n_steps], p[2]};
+    double win = sqrt(pdot2(Pin) + 1.0), wout = sqrt(pdot2(Pout) + 1.0);
+    cplx uin[2][4], vin[2][4], uout[2][4], vout[2][4];
+    orc_spinors(Pin, uin, vin);
+    orc_spinors(Pout, uout, vout);
+    cplx H0[4][4], UB[4][4];
+    hamiltonian(&D, p, H0);
+    expm_squared_scalar(H0, pdot2(p) + 1.0, 0.5 * dt, UB);
+    double f = 0.0, dev = 0.0;
+    for (int s = 0; s < 2; s++) {
+        cplx psi[4], tmp[4];
+        for (int a = 0; a < 4; a++)
+            psi[a] = vin[s][a];
+        double n0 = 0.0;
+        for (int a = 0; a < 4; a++)
+            n0 += creal(psi[a] * conj(psi[a]));
+        for (int n = 0; n < n_steps; n++) {
+            double ax = Ax[2 * n + 1], ay = Ay[2 * n + 1];
+            cplx V[4][4], UA[4][4];
+            for (int i = 0; i < 4; i++)
+                for (int j = 0; j < 4; j++)
+                    V[i][j] = -(D.alpha[0][i][j] * ax + D.alpha[1][i][j] * ay);
+            expm_squared_scalar(V, ax * ax + ay * ay, dt, UA);
+            matvec4(UB, psi, tmp);
+            matvec4(UA, tmp, psi);
+            matvec4(UB, psi, tmp);
+            for (int a = 0; a < 4; a++)
+                psi[a] = tmp[a];
+        }
+        double n1 = 0.0;
+        for (int a = 0; a < 4; a++)
+            n1 += creal(psi[a] * conj(psi[a]));
+        if (fabs(n1 / n0 - 1.0) > dev)
+            dev = fabs(n1 / n0 - 1.0);
+        for (int s2 = 0; s2 < 2; s2++) {
+            cplx amp = 0;
+            for (int a = 0; a < 4; a++)
+                amp += conj(uout[s2][a]) * psi[a];
+            f += creal(amp * conj(amp)) / (2.0 * wout * 2.0 * win);
+        }
+    }
+    if (norm_dev)
+        *norm_dev = dev;
+    return f;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Fourth-order Magnus integrator (the paper's outlook, Sec. V.C.2, names a   */
+/* fourth-order scheme for the Dirac equation as the next step).  With the    */
+/* samples H_0 = H(t_n), H_h = H(t_n + dt/2), H_1 = H(t_n + dt):               */
+/*   Omega = -i dt/6 (H_0 + 4 H_h + H_1) + dt^2/12 [H_0, H_1],                */
+/*   psi_{n+1} = exp(Omega) psi_n,                                            */
+/* the two-term Magnus expansion with Simpson's rule for the first integral   */
+/* and the endpoint form of the commutator term (fourth order, unitary).      */
+/* ------------------------------------------------------------------------- */
+
+static void matmul4(cplx X[4][4], cplx Y[4][4], cplx Z[4][4])
+{
+    for (int i = 0; i < 4; i++)
+        for (int j = 0; j < 4; j++) {
+            cplx acc = 0;
+            for (int k = 0; k < 4; k++)
+                acc += X[i][k] * Y[k][j];
+            Z[i][j] = acc;
+        }
+}
+
+/* exp(X) by its Taylor series, summed until the terms stop changing the sum
+ * (|X| < 1 here, so at most ~25 terms). */
+static void expm_taylor(cplx X[4][4], cplx E[4][4])
+{
+    cplx term[4][4], next[4][4];
+    for (int i = 0; i < 4; i++)
+        for (int j = 0; j < 4; j++) {
+            E[i][j] = (i == j) ? 1.0 : 0.0;
+            term[i][j] = E[i][j];
+        }
+    for (int k = 1; k < 60; k++) {
+        matmul4(term, X, next);
+        double mx = 0.0;
+        for (int i = 0; i < 4; i++)
+            for (int j = 0; j < 4; j++) {
+                term[i][j] = next[i][j] / (double)k;
+                E[i][j] += term[i][j];
+                if (cabs(term[i][j]) > mx)
+                    mx = cabs(term[i][j]);
+            }
+        if (mx < 1e-30)
+            break;
+    }
+}
+
+/* f(t_f, p) as orc_dirac_mode (full spin trace), propagated with the
+ * fourth-order Magnus step; *norm_dev as in orc_dirac_split_mode. */
+double orc_dirac_magnus_mode(const double *A, int ld, int n_steps, double dt, const double p[3],
+                             double *norm_dev)
+{
+    dirac_mats D;
+    make_dirac_mats(&D);
+    const double *Ax = A, *Ay = A + ld;
+    double Pin[3] = {p[0] - Ax[0], p[1] - Ay[0], p[2]};
+    double Pout[3] = {p[0] - Ax[2 * n_steps], p[1] - Ay[2 * n_steps], p[2]};
+    double win = sqrt(pdot2(Pin) + 1.0), wout = sqrt(pdot2(Pout) + 1.0);
+    cplx uin[2][4], vin[2][4], uout[2][4], vout[2][4];
+    orc_spinors(Pin, uin, vin);
+    orc_spinors(Pout, uout, vout);
+    cplx psi[2][4];
+    for (int s = 0; s < 2; s++)
+        for (int a = 0; a < 4; a++)
+            psi[s][a] = vin[s][a];
+    for (int n = 0; n < n_steps; n++) {
+        double P0[3] = {p[0] - Ax[2 * n], p[1] - Ay[2 * n], p[2]};
+        double Ph[3] = {p[0] - Ax[2 * n + 1], p[1] - Ay[2 * n + 1], p[2]};
+        double P1[3] = {p[0] - Ax[2 * n + 2], p[1] - Ay[2 * n + 2], p[2]};
+        cplx H0[4][4], Hh[4][4], H1[4][4], C01[4][4], C10[4][4], Om[4][4], U[4][4];
+        hamiltonian(&D, P0, H0);
+        hamiltonian(&D, Ph, Hh);
+        hamiltonian(&D, P1, H1);
+        matmul4(H0, H1, C01);
+        matmul4(H1, H0, C10);
+        for (int i = 0; i < 4; i++)
+            for (int j = 0; j < 4; j++)
+                Om[i][j] = -I * dt / 6.0 * (H0[i][j] + 4.0 * Hh[i][j] + H1[i][j]) +
+                           dt * dt / 12.0 * (C01[i][j] - C10[i][j]);
+        expm_taylor(Om, U);
+        for (int s = 0; s < 2; s++) {
+            cplx tmp[4];
+            matvec4(U, psi[s], tmp);
+            for (int a = 0; a < 4; a++)
+                psi[s][a] = tmp[a];
+        }
+    }
+    double f = 0.0, dev = 0.0;
+    for (int s = 0; s < 2; s++) {
+        double n0 = 0.0, n1 = 0.0;
+        for (int a = 0; a < 4; a++) {
+            n0 += creal(vin[s][a] * conj(vin[s][a]));
+            n1 += creal(psi[s][a] * conj(psi[s][a]));
+        }
+        if (fabs(n1 / n0 - 1.0) > dev)
+            dev = fabs(n1 / n0 - 1.0);
+        for (int s2 = 0; s2 < 2; s2++) {
+            cplx amp = 0;
+            for (int a = 0; a < 4; a++)
+                amp += conj(uout[s2][a]) * psi[s][a];
+            f += creal(amp * conj(amp)) / (2.0 * wout * 2.0 * win);
+        }
+    }
+    if (norm_dev)
+        *norm_dev = dev;
+    return f;
+}
+
+/* ------------------------------------------------------------------------- */
 /* 6-component quantum kinetic equation, Sec. II.B, Eqs. (qke), (matrix)      */
 /* The paper's field plane (e2,e3) with out-of-plane axis e1 maps onto this   */
 /* file's (x,y) plane with out-of-plane z (a cyclic relabelling).             */
@@ -529,6 +724,7 @@ typedef struct {
     int nm, stride;
     int first;
     double *out;
+    double *aux;
 } mode_job;
 
 static void *mode_worker(void *arg)
@@ -537,6 +733,12 @@ static void *mode_worker(void *arg)
     for (int m = J->first; m < J->nm; m += J->stride) {
         if (J->kind == 0)
             J->out[m] = orc_dirac_mode(J->A, J->ld, J->n_steps, J->dt, J->p + 3 * m, J->spin_sum, NULL);
+        else if (J->kind == 2)
+            J->out[m] = orc_dirac_split_mode(J->A, J->ld, J->n_steps, J->dt, J->p + 3 * m,
+                                             J->aux ? J->aux + m : NULL);
+        else if (J->kind == 3)
+            J->out[m] = orc_dirac_magnus_mode(J->A, J->ld, J->n_steps, J->dt, J->p + 3 * m,
+                                              J->aux ? J->aux + m : NULL);
         else
             J->out[m] = orc_qke6_mode(J->A, J->E, J->Edot, J->ld, J->n_steps, J->dt, J->p + 3 * m);
     }
@@ -582,7 +784,29 @@ int orc_dirac_modes(const double *A, int ld, int n_steps, double dt, const doubl
 {
     if (!A || !p || !n_out || nm < 0 || n_steps < 1 || ld < 2 * n_steps + 1)
         return ORC_ERR_ARG;
-    mode_job J = {A, NULL, NULL, ld, n_steps, spin_sum, 0, dt, p, nm, 1, 0, n_out};
+    mode_job J = {A, NULL, NULL, ld, n_steps, spin_sum, 0, dt, p, nm, 1, 0, n_out, NULL};
+    run_modes(&J, nthreads);
+    return ORC_OK;
+}
+
+/* f(p) for a list of momenta with the fourth-order Magnus step. */
+int orc_dirac_magnus_modes(const double *A, int ld, int n_steps, double dt, const double *p, int nm,
+                           double *n_out, double *norm_dev, int nthreads)
+{
+    if (!A || !p || !n_out || nm < 0 || n_steps < 1 || ld < 2 * n_steps + 1)
+        return ORC_ERR_ARG;
+    mode_job J = {A, NULL, NULL, ld, n_steps, 0, 3, dt, p, nm, 1, 0, n_out, norm_dev};
+    run_modes(&J, nthreads);
+    return ORC_OK;
+}
+
+/* f(p) for a list of momenta with the split operator; norm_dev[m] may be NULL. */
+int orc_dirac_split_modes(const double *A, int ld, int n_steps, double dt, const double *p, int nm,
+                          double *n_out, double *norm_dev, int nthreads)
+{
+    if (!A || !p || !n_out || nm < 0 || n_steps < 1 || ld < 2 * n_steps + 1)
+        return ORC_ERR_ARG;
+    mode_job J = {A, NULL, NULL, ld, n_steps, 0, 2, dt, p, nm, 1, 0, n_out, norm_dev};
     run_modes(&J, nthreads);
     return ORC_OK;
 }
@@ -593,7 +817,7 @@ int orc_qke6_modes(const double *A, const double *E, const double *Edot, int ld,
 {
     if (!A || !E || !Edot || !p || !f_out || nm < 0 || n_steps < 1 || ld < 2 * n_steps + 1)
         return ORC_ERR_ARG;
-    mode_job J = {A, E, Edot, ld, n_steps, 0, 1, dt, p, nm, 1, 0, f_out};
+    mode_job J = {A, E, Edot, ld, n_steps, 0, 1, dt, p, nm, 1, 0, f_out, NULL};
     run_modes(&J, nthreads);
     return ORC_OK;
 }

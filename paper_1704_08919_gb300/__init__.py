@@ -29,6 +29,12 @@ PP_FP64 = 0
 PP_FP32 = 1
 PRECISIONS = {"fp64": PP_FP64, "fp32": PP_FP32, PP_FP64: PP_FP64, PP_FP32: PP_FP32}
 
+PP_RK4 = 0
+PP_MAGNUS4 = 1
+PP_SPLIT2 = 2
+SCHEMES = {"rk4": PP_RK4, "magnus4": PP_MAGNUS4, "split2": PP_SPLIT2,
+           PP_RK4: PP_RK4, PP_MAGNUS4: PP_MAGNUS4, PP_SPLIT2: PP_SPLIT2}
+
 EXPORTS = ("pp_synth_field", "pp_pair_number", "pp_de_propose", "pp_de_select", "pp_de_step",
            "pp_sync_status", "pp_set_wait_limit", "pp_set_skip_copies", "pp_last_error",
            "pp_version", "pp_profile_begin", "pp_profile_end")
@@ -68,12 +74,12 @@ def lib():
             raise RuntimeError("libpp.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
         L = ctypes.CDLL(LIB_PATH)
         L.pp_synth_field.argtypes = [_vp, _i32, ctypes.POINTER(FieldSpec), _vp, _i32, _vp, _vp, _vp]
-        L.pp_pair_number.argtypes = [_vp, _i32, _i32, _vp, _d, ctypes.POINTER(Grid), _i32, _vp, _vp,
-                                     _vp]
+        L.pp_pair_number.argtypes = [_vp, _i32, _i32, _vp, _d, ctypes.POINTER(Grid), _i32, _i32,
+                                     _vp, _vp, _vp]
         L.pp_de_propose.argtypes = [_vp, _i32, _i32, _vp, _vp, _vp, _d, _d, _u64, _u64, _vp, _vp]
         L.pp_de_select.argtypes = [_vp, _vp, _vp, _vp, _i32, _i32, _vp]
         L.pp_de_step.argtypes = [_vp, _vp, _i32, ctypes.POINTER(FieldSpec), ctypes.POINTER(Grid),
-                                 _i32, _vp, _vp, _vp, _d, _d, _u64, _u64, _vp, _vp, _vp]
+                                 _i32, _i32, _vp, _vp, _vp, _d, _d, _u64, _u64, _vp, _vp, _vp]
         L.pp_sync_status.argtypes = [_vp]
         L.pp_set_wait_limit.argtypes = [ctypes.c_int64]
         L.pp_set_wait_limit.restype = ctypes.c_int64
@@ -138,7 +144,8 @@ def synth_field(params, spec, want_E=False, want_scale=False, stream=None, out=N
     return A, E, s
 
 
-def pair_number(A, dt, grid, precision="fp32", n_steps=None, want_n=False, stream=None, N_out=None):
+def pair_number(A, dt, grid, precision="fp32", n_steps=None, want_n=False, stream=None, N_out=None,
+                scheme="rk4"):
     """pp_pair_number: A [ncand, 2, ld] float64 CUDA -> N [ncand] (and n [ncand, nz, ny, nx])."""
     import torch
     g = _grid(grid)
@@ -151,7 +158,8 @@ def pair_number(A, dt, grid, precision="fp32", n_steps=None, want_n=False, strea
         arr = (ctypes.c_int32 * ncand)(*[int(x) for x in n_steps])
         ns = ctypes.cast(arr, ctypes.c_void_p)
     _check(lib().pp_pair_number(_ptr(A), ncand, ld, ns, float(dt), ctypes.byref(g),
-                                PRECISIONS[precision], _ptr(N), _ptr(n), _stream(stream)))
+                                PRECISIONS[precision], SCHEMES[scheme], _ptr(N), _ptr(n),
+                                _stream(stream)))
     return N, n
 
 
@@ -173,12 +181,13 @@ def de_select(pop, fit, trial, trial_fit, stream=None):
 
 
 def de_step(pop, fit, spec, grid, lo, hi, periodic, F, CR, seed, generation, precision="fp32",
-            trial_out=None, trial_fit_out=None, stream=None):
+            trial_out=None, trial_fit_out=None, stream=None, scheme="rk4"):
     """pp_de_step: one DE generation (propose, synthesise, score, select) in place."""
     sp, g = _spec(spec), _grid(grid)
     NP = pop.shape[0]
     _check(lib().pp_de_step(_ptr(pop), _ptr(fit), NP, ctypes.byref(sp), ctypes.byref(g),
-                            PRECISIONS[precision], _ptr(lo), _ptr(hi), _ptr(periodic), float(F),
+                            PRECISIONS[precision], SCHEMES[scheme], _ptr(lo), _ptr(hi),
+                            _ptr(periodic), float(F),
                             float(CR), int(seed), int(generation), _ptr(trial_out),
                             _ptr(trial_fit_out), _stream(stream)))
 

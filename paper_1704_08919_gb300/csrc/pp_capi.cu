@@ -284,7 +284,8 @@ int pp_synth_field(const double *params, int32_t ncand, const pp_field_spec *spe
 }
 
 int pp_pair_number(const double *A, int32_t ncand, int32_t ld, const int32_t *n_steps, double dt,
-                   const pp_grid *grid, int32_t precision, double *N, double *n_p, void *stream)
+                   const pp_grid *grid, int32_t precision, int32_t scheme, double *N, double *n_p,
+                   void *stream)
 {
     clear_error();
     int rc = check_grid(grid);
@@ -300,6 +301,8 @@ int pp_pair_number(const double *A, int32_t ncand, int32_t ld, const int32_t *n_
         return fail(PP_ERR_INVALID_ARG, "dt must be positive and finite");
     if (precision != PP_FP64 && precision != PP_FP32)
         return fail(PP_ERR_INVALID_ARG, "precision must be PP_FP64 or PP_FP32");
+    if (scheme != PP_RK4 && scheme != PP_MAGNUS4 && scheme != PP_SPLIT2)
+        return fail(PP_ERR_INVALID_ARG, "scheme must be PP_RK4, PP_MAGNUS4 or PP_SPLIT2");
     if (ld < 3)
         return fail(PP_ERR_INVALID_ARG, "ld must be >= 3");
     for (int c = 0; c < ncand; ++c) {
@@ -307,7 +310,8 @@ int pp_pair_number(const double *A, int32_t ncand, int32_t ld, const int32_t *n_
         if (ns < 1 || 2 * ns + 1 > ld)
             return fail(PP_ERR_INVALID_ARG, "candidate %d: n_steps %lld needs 2 n_steps + 1 <= ld (%d)", c, ns, ld);
     }
-    return launch_pair_number(A, ncand, ld, n_steps, dt, grid, precision, N, n_p, (cudaStream_t)stream);
+    return launch_pair_number(A, ncand, ld, n_steps, dt, grid, precision, scheme, N, n_p,
+                              (cudaStream_t)stream);
 }
 
 int pp_de_propose(const double *pop, int32_t NP, int32_t D, const double *lo, const double *hi,
@@ -339,7 +343,7 @@ int pp_de_select(double *pop, double *fit, const double *trial, const double *tr
 }
 
 int pp_de_step(double *pop, double *fit, int32_t NP, const pp_field_spec *spec, const pp_grid *grid,
-               int32_t precision, const double *lo, const double *hi, const uint8_t *periodic,
+               int32_t precision, int32_t scheme, const double *lo, const double *hi, const uint8_t *periodic,
                double F, double CR, uint64_t seed, uint64_t generation, double *trial_out,
                double *trial_fit_out, void *stream)
 {
@@ -355,6 +359,8 @@ int pp_de_step(double *pop, double *fit, int32_t NP, const pp_field_spec *spec, 
         return fail(PP_ERR_INVALID_ARG, "pop, fit, lo, hi must not be NULL");
     if (precision != PP_FP64 && precision != PP_FP32)
         return fail(PP_ERR_INVALID_ARG, "precision must be PP_FP64 or PP_FP32");
+    if (scheme != PP_RK4 && scheme != PP_MAGNUS4 && scheme != PP_SPLIT2)
+        return fail(PP_ERR_INVALID_ARG, "scheme must be PP_RK4, PP_MAGNUS4 or PP_SPLIT2");
     if (!(CR >= 0.0 && CR <= 1.0) || !isfinite(F))
         return fail(PP_ERR_INVALID_ARG, "CR must be in [0, 1] and F finite");
     cudaStream_t st = (cudaStream_t)stream;
@@ -379,8 +385,8 @@ int pp_de_step(double *pop, double *fit, int32_t NP, const pp_field_spec *spec, 
         return rc;
     if ((rc = launch_synth_field(trial, NP, spec, A, ld, nullptr, nullptr, st)))
         return rc;
-    if ((rc = launch_pair_number(A, NP, ld, nullptr, spec->T / spec->n_steps, grid, precision, tfit,
-                                 nullptr, st)))
+    if ((rc = launch_pair_number(A, NP, ld, nullptr, spec->T / spec->n_steps, grid, precision, scheme,
+                                 tfit, nullptr, st)))
         return rc;
     return launch_de_select(pop, fit, trial, tfit, NP, D, st);
 }

@@ -42,7 +42,7 @@ int skip_copies();
 
 // Launch the propagation for one precision (pp_propagate.cu).
 int launch_pair_number(const double *A, int ncand, int ld, const int32_t *n_steps_host, double dt,
-                       const pp_grid *grid, int precision, double *N, double *n_p,
+                       const pp_grid *grid, int precision, int scheme, double *N, double *n_p,
                        cudaStream_t stream);
 
 // Field synthesis launch without argument re-validation (pp_field.cu).

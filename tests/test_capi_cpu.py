@@ -43,24 +43,27 @@ def test_library_exports_every_declared_symbol(pp):
 def test_host_validation_rejects_bad_arguments(pp):
     L = pp.lib()
     g = pp.Grid(0, 4, 4, -1, 1, -1, 1, 0, 1, 1)
-    rc = L.pp_pair_number(ctypes.c_void_p(8), 1, 101, None, 0.1, ctypes.byref(g), 0,
+    rc = L.pp_pair_number(ctypes.c_void_p(8), 1, 101, None, 0.1, ctypes.byref(g), 0, 0,
                           ctypes.c_void_p(8), None, None)
     assert rc == pp.PP_ERR_INVALID_ARG
     assert b"grid sizes" in L.pp_last_error()
     g = pp.Grid(4, 4, 4, -1, 1, -1, 1, 0.5, 1, 1)
-    rc = L.pp_pair_number(ctypes.c_void_p(8), 1, 101, None, 0.1, ctypes.byref(g), 0,
+    rc = L.pp_pair_number(ctypes.c_void_p(8), 1, 101, None, 0.1, ctypes.byref(g), 0, 0,
                           ctypes.c_void_p(8), None, None)
     assert rc == pp.PP_ERR_INVALID_ARG and b"mirror_z" in L.pp_last_error()
     g = pp.Grid(4, 4, 4, -1, 1, -1, 1, 0, 1, 1)
-    rc = L.pp_pair_number(ctypes.c_void_p(8), 1, 101, None, -0.1, ctypes.byref(g), 0,
+    rc = L.pp_pair_number(ctypes.c_void_p(8), 1, 101, None, -0.1, ctypes.byref(g), 0, 0,
                           ctypes.c_void_p(8), None, None)
     assert rc == pp.PP_ERR_INVALID_ARG and b"dt" in L.pp_last_error()
-    rc = L.pp_pair_number(ctypes.c_void_p(8), 1, 101, None, 0.1, ctypes.byref(g), 7,
+    rc = L.pp_pair_number(ctypes.c_void_p(8), 1, 101, None, 0.1, ctypes.byref(g), 7, 0,
                           ctypes.c_void_p(8), None, None)
     assert rc == pp.PP_ERR_INVALID_ARG and b"precision" in L.pp_last_error()
+    rc = L.pp_pair_number(ctypes.c_void_p(8), 1, 101, None, 0.1, ctypes.byref(g), 0, 9,
+                          ctypes.c_void_p(8), None, None)
+    assert rc == pp.PP_ERR_INVALID_ARG and b"scheme" in L.pp_last_error()
     ns = (ctypes.c_int32 * 1)(60)
     rc = L.pp_pair_number(ctypes.c_void_p(8), 1, 101, ctypes.cast(ns, ctypes.c_void_p), 0.1,
-                          ctypes.byref(g), 0, ctypes.c_void_p(8), None, None)
+                          ctypes.byref(g), 0, 0, ctypes.c_void_p(8), None, None)
     assert rc == pp.PP_ERR_INVALID_ARG and b"n_steps" in L.pp_last_error()
     rc = L.pp_de_propose(ctypes.c_void_p(8), 3, 4, ctypes.c_void_p(8), ctypes.c_void_p(8), None,
                          0.5, 0.9, 1, 0, ctypes.c_void_p(8), None)

@@ -97,26 +97,50 @@ def test_rotating_gaussian_fp32(pp, gauss_ref):
     assert n_excess(n, no, ns, rel=1e-4, d=d32(ns, dt, pmax, np.abs(A).max())) <= 1.0
 
 
-@pytest.mark.parametrize("n_steps", [1, 7, 255, 256, 257, 511, 512, 513, 1100])
+def oracle_n(scheme, A, n_steps, dt, pts):
+    """The oracle twin of a scheme: f for the momenta pts."""
+    if scheme == "rk4":
+        return oracle.dirac_modes(A, n_steps, dt, pts)
+    if scheme == "magnus4":
+        return oracle.dirac_magnus_modes(A, n_steps, dt, pts)[0]
+    return oracle.dirac_split_modes(A, n_steps, dt, pts)[0]
+
+
+def weighted_N(grid, n):
+    x, y, z = inputs.grid_axes(grid)
+
+    def tw(a, mirror):
+        if a.size == 1:
+            return np.ones(1)
+        w = np.full(a.size, a[1] - a[0])
+        w[[0, -1]] /= 2
+        return w * (2 if mirror else 1)
+    W = (tw(z, grid["mirror_z"])[:, None, None] * tw(y, 0)[None, :, None]
+         * tw(x, 0)[None, None, :])
+    return float(np.sum(W.ravel() * np.asarray(n).ravel()))
+
+
+@pytest.mark.parametrize("n_steps", [1, 7, 127, 128, 129, 255, 256, 257, 511, 512, 513, 1100])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_ragged_steps_and_modes(pp, n_steps, precision):
-    # step counts around the shared-memory tile (256 FP64 / 512 FP32 steps) and a
-    # mode count (5*7*3 = 105) that fills no block
-    g = inputs.ROTATING_GAUSSIAN
+@pytest.mark.parametrize("scheme", ["rk4", "magnus4", "split2"])
+def test_ragged_steps_and_modes(pp, n_steps, precision, scheme):
+    # step counts around the shared-memory tiles (128..1024 steps depending on
+    # scheme and precision) and a mode count (5*7*3 = 105) that fills no block;
+    # each scheme against its own oracle twin
     dt = 0.05
     t0 = -0.5 * n_steps * dt
     A, _, _ = oracle.gaussian_rotating_field(0.3, 0.9, 3.0, t0, dt / 2, 2 * n_steps + 1)
     grid = inputs.small_grid(5, 7, 3, ext=1.3)
-    No, no = oracle.pair_number(A[None], n_steps, dt, grid)
+    no = oracle_n(scheme, A, n_steps, dt, inputs.grid_points(grid))
+    No = weighted_N(grid, no)
     N, n = pp.pair_number(torch.tensor(A[None], device=DEV), dt, grid, precision=precision,
-                          want_n=True)
+                          want_n=True, scheme=scheme)
     assert pp.sync_status() == pp.PP_OK
     N, n = N.cpu().numpy(), n.cpu().numpy()
     tol = 1e-9 if precision == "fp64" else 1e-4
-    assert abs(N[0] / No[0] - 1) < tol
+    assert abs(N[0] / No - 1) < tol
     if precision == "fp64":
         assert n_excess(n, no, n_steps) <= 1.0
-    del g
 
 
 def test_uneven_steps_batch_and_single_mode_axes(pp):
@@ -287,6 +311,43 @@ def test_de_batch_full_size_sampled_modes(pp):
         no = oracle.dirac_modes(Ah[c], cfg["n_steps"], dt, pts[idx])
         ng = n64[c].ravel()[idx]
         assert n_excess(ng, no, cfg["n_steps"]) <= 1.0
+
+
+@pytest.mark.parametrize("scheme", ["magnus4", "split2"])
+def test_unitary_schemes_on_the_rotating_gaussian(pp, gauss_ref, scheme):
+    g, ns, dt, A, No_rk4, _ = gauss_ref
+    pts = inputs.grid_points(g["grid"])
+    sub = inputs.strided_modes(g["grid"], 600, seed=5)
+    no_sub = oracle_n(scheme, A, ns, dt, pts[sub])
+    At = torch.tensor(A[None], device=DEV)
+    N64, n64 = pp.pair_number(At, dt, g["grid"], precision="fp64", want_n=True, scheme=scheme)
+    N32, _ = pp.pair_number(At, dt, g["grid"], precision="fp32", scheme=scheme)
+    assert pp.sync_status() == pp.PP_OK
+    assert n_excess(n64.cpu().numpy().ravel()[sub], no_sub, ns) <= 1.0
+    assert abs(N32.item() / N64.item() - 1) < 1e-4
+    # against the RK4 oracle: the fourth-order scheme agrees far inside 1e-4 at this dt
+    if scheme == "magnus4":
+        assert abs(N64.item() / No_rk4[0] - 1) < 1e-6
+
+
+def test_magnus_fp32_at_full_de_batch_size(pp):
+    cfg = inputs.DE_BATCH
+    spec = inputs.field_spec(cfg)
+    params = inputs.random_population(4, cfg["K"], seed=2)
+    A, _, _ = pp.synth_field(torch.tensor(params, device=DEV), spec)
+    dt = cfg["T"] / cfg["n_steps"]
+    N_rk4, _ = pp.pair_number(A, dt, cfg["grid"], precision="fp64", scheme="rk4")
+    N_m64, n_m64 = pp.pair_number(A, dt, cfg["grid"], precision="fp64", scheme="magnus4",
+                                  want_n=True)
+    N_m32, _ = pp.pair_number(A, dt, cfg["grid"], precision="fp32", scheme="magnus4")
+    assert pp.sync_status() == pp.PP_OK
+    assert (N_m32 / N_rk4 - 1).abs().max().item() < 1e-4
+    assert (N_m32 / N_m64 - 1).abs().max().item() < 1e-5
+    Ah = A.cpu().numpy()
+    pts = inputs.grid_points(cfg["grid"])
+    idx = inputs.strided_modes(cfg["grid"], 24, seed=3)
+    no = oracle.dirac_magnus_modes(Ah[0], cfg["n_steps"], dt, pts[idx])[0]
+    assert n_excess(n_m64[0].cpu().numpy().ravel()[idx], no, cfg["n_steps"]) <= 1.0
 
 
 def test_results_are_bitwise_reproducible(pp):
