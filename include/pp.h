@@ -29,6 +29,7 @@
 #ifndef PP_H
 #define PP_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -134,6 +135,38 @@ int pp_synth_field(const double *params, int32_t ncand, const pp_field_spec *spe
 int pp_pair_number(const double *A, int32_t ncand, int32_t ld, const int32_t *n_steps, double dt,
                    const pp_grid *grid, int32_t precision, int32_t scheme, double *N, double *n_p,
                    void *stream);
+
+/* pp_pair_number without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory --
+ * for example a host application whose device memory is fully reserved by its
+ * own allocator, or that forbids allocation once it is running, or code called
+ * back from another runtime in which a cudaMalloc (with its implicit device
+ * synchronisation) is not allowed.  The caller still supplies A, N and n_p.
+ * Arguments, results and errors are those of pp_pair_number, computed by the
+ * same kernels; the scratch (the per-step field table, the per-block partial
+ * sums and, for uneven step counts, a copy of n_steps) lives in a fixed device
+ * array of pp_static_scratch_bytes() = 16 MiB inside the library, which every
+ * GPU that loads the library holds until the process exits.
+ *  - A call whose scratch would exceed that size returns PP_ERR_INVALID_ARG
+ *    with the required size in pp_last_error(); it needs about
+ *    ncand * (padded n_steps * 32 B + ceil(modes/256) * 8 B) for PP_MAGNUS4
+ *    (16 B per step for PP_RK4 in FP32 and PP_SPLIT2), e.g. 64 candidates of
+ *    4096 steps, or 16 candidates of 16384 steps.
+ *  - The first call on each device looks up the device address of the array
+ *    (a one-time set-up with that device current); make that first call before
+ *    any stream capture.
+ *  - Every call shares the array and leaves its contents behind; each call
+ *    writes all the scratch it reads, so nothing must be cleared, but calls
+ *    whose work overlaps on the GPU (other streams, other host threads) race on
+ *    it: serialise them.
+ *  - Nothing in this call allocates: no cudaMalloc, cudaFree or allocating
+ *    library routine.  It calls no kernel-timing hook. */
+int pp_pair_number_static(const double *A, int32_t ncand, int32_t ld, const int32_t *n_steps,
+                          double dt, const pp_grid *grid, int32_t precision, int32_t scheme,
+                          double *N, double *n_p, void *stream);
+
+/* Size in bytes of the fixed scratch array used by pp_pair_number_static. */
+size_t pp_static_scratch_bytes(void);
 
 /* DE/rand/1/bin trial vectors (Sec. IV.B, steps 1-3).  For each individual i:
  * three distinct donors r1, r2, r3 != i; u = x_r1 + F (x_r2 - x_r3); binomial

@@ -314,6 +314,39 @@ int pp_pair_number(const double *A, int32_t ncand, int32_t ld, const int32_t *n_
                               (cudaStream_t)stream);
 }
 
+int pp_pair_number_static(const double *A, int32_t ncand, int32_t ld, const int32_t *n_steps,
+                          double dt, const pp_grid *grid, int32_t precision, int32_t scheme,
+                          double *N, double *n_p, void *stream)
+{
+    clear_error();
+    int rc = check_grid(grid);
+    if (rc)
+        return rc;
+    if (ncand < 0 || ncand > 65535)
+        return fail(PP_ERR_INVALID_ARG, "ncand must be in [0, 65535]");
+    if (ncand == 0)
+        return PP_OK;
+    if (!A || !N)
+        return fail(PP_ERR_INVALID_ARG, "A and N must not be NULL");
+    if (!(dt > 0.0) || !isfinite(dt))
+        return fail(PP_ERR_INVALID_ARG, "dt must be positive and finite");
+    if (precision != PP_FP64 && precision != PP_FP32)
+        return fail(PP_ERR_INVALID_ARG, "precision must be PP_FP64 or PP_FP32");
+    if (scheme != PP_RK4 && scheme != PP_MAGNUS4 && scheme != PP_SPLIT2)
+        return fail(PP_ERR_INVALID_ARG, "scheme must be PP_RK4, PP_MAGNUS4 or PP_SPLIT2");
+    if (ld < 3)
+        return fail(PP_ERR_INVALID_ARG, "ld must be >= 3");
+    for (int c = 0; c < ncand; ++c) {
+        long long ns = n_steps ? n_steps[c] : (ld - 1) / 2;
+        if (ns < 1 || 2 * ns + 1 > ld)
+            return fail(PP_ERR_INVALID_ARG, "candidate %d: n_steps %lld needs 2 n_steps + 1 <= ld (%d)", c, ns, ld);
+    }
+    return launch_pair_number_static(A, ncand, ld, n_steps, dt, grid, precision, scheme, N, n_p,
+                                     (cudaStream_t)stream);
+}
+
+size_t pp_static_scratch_bytes(void) { return static_scratch_bytes(); }
+
 int pp_de_propose(const double *pop, int32_t NP, int32_t D, const double *lo, const double *hi,
                   const uint8_t *periodic, double F, double CR, uint64_t seed, uint64_t generation,
                   double *trial, void *stream)

@@ -45,6 +45,13 @@ int launch_pair_number(const double *A, int ncand, int ld, const int32_t *n_step
                        const pp_grid *grid, int precision, int scheme, double *N, double *n_p,
                        cudaStream_t stream);
 
+// The same with the fixed static scratch of pp_propagate.cu instead of
+// allocated scratch (pp_pair_number_static); static_scratch_bytes() is its size.
+int launch_pair_number_static(const double *A, int ncand, int ld, const int32_t *n_steps_host,
+                              double dt, const pp_grid *grid, int precision, int scheme, double *N,
+                              double *n_p, cudaStream_t stream);
+size_t static_scratch_bytes();
+
 // Field synthesis launch without argument re-validation (pp_field.cu).
 int launch_synth_field(const double *params, int ncand, const pp_field_spec *spec, double *A,
                        int ld, double *E, double *scale, cudaStream_t stream);

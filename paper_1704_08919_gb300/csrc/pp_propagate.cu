@@ -30,6 +30,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "pp_internal.cuh"
 
 namespace {
@@ -913,6 +915,92 @@ int run(const double *A, int ncand, int ld, const int32_t *ns_host, double dt, c
     return PP_OK;
 }
 
+// ---------------------------------------------------------------- no-allocation variant
+// Scratch of pp_pair_number_static: a fixed device array in this file, held by
+// every GPU that loads the library until the process exits.  It holds, in
+// order, the per-step table, the per-block partial sums and (for uneven step
+// counts) a copy of n_steps; each call writes every byte it later reads, so
+// nothing needs clearing, and calls that overlap on the GPU race on it.
+constexpr size_t kStaticScratchBytes = (size_t)16 << 20;
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Device address of g_static_scratch on the current device, looked up once per
+// device (host code must not use the symbol itself as a device address).
+unsigned char *static_scratch_address()
+{
+    constexpr int kMaxDev = 64;
+    static unsigned char *addr[kMaxDev] = {};
+    static std::mutex mu;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev)
+        return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess)
+            return nullptr;
+        addr[dev] = (unsigned char *)p;
+    }
+    return addr[dev];
+}
+
+template <class P>
+int run_static(const double *A, int ncand, int ld, const int32_t *ns_host, double dt,
+               const pp_grid *grid, double *N, double *n_p, cudaStream_t stream)
+{
+    using V = typename P::Entry;
+    constexpr int TILE = P::TILE;
+    int max_ns = 0;
+    bool uniform = true;
+    const int ns0 = ns_host ? ns_host[0] : (ld - 1) / 2;
+    for (int c = 0; c < ncand; ++c) {
+        const int ns = ns_host ? ns_host[c] : ns0;
+        max_ns = ns > max_ns ? ns : max_ns;
+        uniform &= (ns == ns0);
+    }
+    const int padded = ((max_ns + TILE - 1) / TILE) * TILE;
+    const int nmodes = grid->nx * grid->ny * grid->nz;
+    const int nblk = (nmodes + kThreads - 1) / kThreads;
+    const size_t table_bytes = align256((size_t)ncand * padded * sizeof(V));
+    const size_t part_bytes = align256((size_t)ncand * nblk * sizeof(double));
+    const size_t ns_bytes = uniform ? 0 : align256((size_t)ncand * sizeof(int));
+    const size_t need = table_bytes + part_bytes + ns_bytes;
+    if (need > kStaticScratchBytes)
+        return pp::fail(PP_ERR_INVALID_ARG,
+                        "this call needs %zu bytes of scratch; the static scratch holds %zu "
+                        "(use fewer candidates, steps or modes, or pp_pair_number)",
+                        need, kStaticScratchBytes);
+    unsigned char *base = static_scratch_address();
+    if (!base)
+        return pp::fail(PP_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed");
+    unsigned int *status = pp::status_word();
+    if (!status)
+        return pp::fail(PP_ERR_CUDA, "status word unavailable");
+    V *table = (V *)base;
+    double *partial = (double *)(base + table_bytes);
+    const int *ns_array = nullptr;
+    if (!uniform) {
+        int *nsdev = (int *)(base + table_bytes + part_bytes);
+        cudaError_t e = cudaMemcpyAsync(nsdev, ns_host, sizeof(int) * ncand, cudaMemcpyHostToDevice, stream);
+        if (e != cudaSuccess)
+            return pp::cuda_fail(e, "copy of n_steps");
+        ns_array = nsdev;
+    }
+    dim3 tg((padded + 255) / 256, ncand);
+    build_table_kernel<P><<<tg, 256, 0, stream>>>(A, ld, ns0, ns_array, padded, dt, table);
+    dim3 pg(nblk, ncand);
+    propagate_kernel<P><<<pg, kThreads, 0, stream>>>(A, ld, ns0, ns_array, table, padded, dt, *grid,
+                                                     n_p, partial, (long long)pp::wait_limit(),
+                                                     pp::skip_copies(), status);
+    finalize_kernel<<<ncand, 256, 0, stream>>>(partial, nblk, N, status);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return pp::cuda_fail(e, "pair-number kernel launch");
+    return PP_OK;
+}
+
 }  // namespace
 
 namespace pp {
@@ -934,5 +1022,25 @@ int launch_pair_number(const double *A, int ncand, int ld, const int32_t *n_step
         return run<SplitPolicy<float, true>>(A, ncand, ld, n_steps_host, dt, grid, N, n_p, stream);
     return run<PackedPolicy>(A, ncand, ld, n_steps_host, dt, grid, N, n_p, stream);
 }
+
+int launch_pair_number_static(const double *A, int ncand, int ld, const int32_t *n_steps_host,
+                              double dt, const pp_grid *grid, int precision, int scheme, double *N,
+                              double *n_p, cudaStream_t stream)
+{
+    if (precision == PP_FP64) {
+        if (scheme == PP_MAGNUS4)
+            return run_static<MagnusPolicy<double, false>>(A, ncand, ld, n_steps_host, dt, grid, N, n_p, stream);
+        if (scheme == PP_SPLIT2)
+            return run_static<SplitPolicy<double, false>>(A, ncand, ld, n_steps_host, dt, grid, N, n_p, stream);
+        return run_static<ScalarPolicy<double, false>>(A, ncand, ld, n_steps_host, dt, grid, N, n_p, stream);
+    }
+    if (scheme == PP_MAGNUS4)
+        return run_static<MagnusPolicy<float, true>>(A, ncand, ld, n_steps_host, dt, grid, N, n_p, stream);
+    if (scheme == PP_SPLIT2)
+        return run_static<SplitPolicy<float, true>>(A, ncand, ld, n_steps_host, dt, grid, N, n_p, stream);
+    return run_static<PackedPolicy>(A, ncand, ld, n_steps_host, dt, grid, N, n_p, stream);
+}
+
+size_t static_scratch_bytes() { return kStaticScratchBytes; }
 
 }  // namespace pp
