@@ -37,8 +37,10 @@ CFG = inputs.DE_BATCH
 #  rk4:     4 matrix applications, 3 stage updates, increment sum, Fast2Sum
 #  magnus4: dt h_eff, |.|^2, cos-1 and sinc polynomials, scaled vector, increment, Fast2Sum
 #  split2:  coupling factor, stage, free factor, Fast2Sum
-WORK = {("fp32", "rk4"): (268, 184), ("fp32", "magnus4"): (136, 98), ("fp32", "split2"): (144, 96),
-        ("fp64", "rk4"): (244, 148), ("fp64", "magnus4"): (112, 74), ("fp64", "split2"): (120, 72)}
+WORK = {("fp32", "rk4"): (268, 184), ("fp32", "magnus4"): (138, 96), ("fp32", "split2"): (144, 96),
+        ("fp32fast", "rk4"): (244, 160), ("fp32fast", "magnus4"): (114, 64),
+        ("fp32fast", "split2"): (112, 64),
+        ("fp64", "rk4"): (244, 148), ("fp64", "magnus4"): (114, 64), ("fp64", "split2"): (112, 64)}
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 L2_FLUSH_BYTES = 256 << 20
@@ -50,7 +52,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32fast", choices=["fp32fast", "fp32", "fp64"])
+    ap.add_argument("--no-tune", action="store_true", help="skip the launch-configuration tuner")
+    ap.add_argument("--alt-steps", type=int, default=2,
+                    help="timed generations of the compensated FP32 path reported beside the main one")
     ap.add_argument("--scheme", default="magnus4", choices=["magnus4", "rk4", "split2"])
     ap.add_argument("--cpu-modes", type=int, default=8192,
                     help="modes of one candidate in the CPU-oracle sample")
@@ -240,6 +245,12 @@ def main():
     per_t = torch.tensor(per, device=dev)
     pop = torch.tensor(pop0, device=dev)
     A, _, _ = pp.synth_field(pop, spec)
+    tuned = None
+    if not args.no_tune:
+        chosen, cfg_ms, _ = pp.tune_pair_number(A, dt, grid, precision=args.precision,
+                                                scheme=args.scheme)
+        tuned = {"chosen": pp.launch_configs()[chosen], "ms": [round(x, 2) for x in cfg_ms],
+                 "configs": pp.launch_configs()}
     fit, _ = pp.pair_number(A, dt, grid, precision=args.precision, scheme=args.scheme)
     trial = torch.empty_like(pop)
     tfit = torch.empty_like(fit)
@@ -292,7 +303,7 @@ def main():
     flop, inst = WORK[(args.precision, args.scheme)]
     units = NP * units_per_candidate()
     achieved = flop * units / (per_launch_ms / 1000.0) / 1e12
-    if args.precision == "fp32":
+    if args.precision in ("fp32", "fp32fast"):
         peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
         peak_src = "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)"
         lanes = SM_COUNT * FP32_LANES_PER_SM * 2070e6
@@ -300,8 +311,8 @@ def main():
         peak = 1.25
         peak_src = "nominal GB300 FP64 (no measured FP64 peak available)"
         lanes = peak * 1e12 / 2
-    roofline = {"bound": "alu", "kernel": "propagate_kernel<%s, %s>" % (args.scheme, (
-        "float, compensated" if args.precision == "fp32" else "double")),
+    roofline = {"bound": "alu", "kernel": "propagate_kernel<%s, %s>" % (args.scheme, {
+        "fp32": "float, compensated", "fp32fast": "float", "fp64": "double"}[args.precision]),
         "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
         "frac": achieved / peak, "peak_source": peak_src,
         "flop_per_mode_step": flop, "inst_per_mode_step": inst,
@@ -339,6 +350,33 @@ def main():
     e2e_value = throughput(ws, NP, args.steps, 1000.0 * e2e_total)
     h2d = pop_h.numel() * 8 + fit_h.numel() * 8
 
+    # ---- the compensated FP32 path on the same population, reported beside the main line
+    alt = None
+    if args.precision == "fp32fast" and args.alt_steps > 0:
+        if not args.no_tune:
+            pp.tune_pair_number(A, dt, grid, precision="fp32", scheme=args.scheme)
+        for _ in range(2):
+            pp.de_step(pop, fit, spec, grid, lo_t, hi_t, per_t, CFG["F"], CFG["CR"], seed, gen,
+                       precision="fp32", trial_out=trial, trial_fit_out=tfit, scheme=args.scheme)
+            gen += 1
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.alt_steps)]
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            pp.de_step(pop, fit, spec, grid, lo_t, hi_t, per_t, CFG["F"], CFG["CR"], seed, gen,
+                       precision="fp32", trial_out=trial, trial_fit_out=tfit, scheme=args.scheme)
+            b.record(stream)
+            gen += 1
+        torch.cuda.synchronize()
+        alt_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), dist, dev)
+        Nc, _ = pp.pair_number(Acheck, dt, grid, precision="fp32", scheme=args.scheme)
+        pp.sync_status()
+        alt = {"precision": "fp32 (compensated)",
+               "value": throughput(ws, NP, args.alt_steps, alt_ms),
+               "ms_per_step": alt_ms / args.alt_steps,
+               "n_rel_err_vs_fp64_rk4_max": (Nc / N64 - 1).abs().max().item()}
+
     # ---- CPU-oracle baseline (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -355,13 +393,15 @@ def main():
                "mode_steps_per_s": cpu_mode_steps,
                "gpu_fp64_vs_oracle_max_rel_n": float(np.abs(n_gpu[big] / n_or[big] - 1).max())}
 
+    if rel_err > 1e-4:
+        raise RuntimeError("N error %.3e vs FP64 RK4 exceeds 1e-4: no valid measurement" % rel_err)
     if rank == 0:
         line = {
             "metric": "candidate pulses scored/s (DE batch, rel. N err <= 1e-4 vs FP64 oracle)",
             "value": cand_per_s, "unit": "candidates/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if args.precision == "fp32" else "f64",
+            "dtype": "f64" if args.precision == "fp64" else "f32",
             "scheme": args.scheme,
             "data": "synthetic (seeded B-spline pulses, uniform in bounds)",
             "config": workload_config(args.precision, NP, args.scheme),
@@ -372,6 +412,8 @@ def main():
             "e2e": {"value": e2e_value, "unit": "candidates/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": h2d},
             "gpu_launches": 7 * args.steps,
+            "launch_tuning": tuned,
+            "alt_compensated": alt,
             "clocks": clk,
             "wall_s_timed": t_wall,
             "step_ms": step_ms,

@@ -47,9 +47,13 @@ typedef enum {
 } pp_status;
 
 typedef enum {
-    PP_FP64 = 0, /* FP64 throughout (the parity path) */
-    PP_FP32 = 1  /* FP32 propagation with compensated (two-float) state accumulation;
-                    FP64 initial state, projection and momentum sum */
+    PP_FP64 = 0,     /* FP64 throughout (the parity path) */
+    PP_FP32 = 1,     /* FP32 propagation with compensated (two-float) state accumulation;
+                        FP64 initial state, projection and momentum sum */
+    PP_FP32_FAST = 2 /* as PP_FP32 but with plain FP32 accumulation of the state: about 27%
+                        faster; N stays within ~2e-6 of FP64 on the DE-batch workload while
+                        single n(p) values lose accuracy (a rounding walk of ~1e-6 in the
+                        transition amplitude) */
 } pp_precision;
 
 /* Time integrator of the momentum-space Dirac equation (all on the same grid:
@@ -125,7 +129,7 @@ int pp_synth_field(const double *params, int32_t ncand, const pp_field_spec *spe
  *                   NULL: every candidate takes (ld - 1) / 2 steps.
  *  dt      step size (> 0).
  *  grid    (host)   momentum grid shared by all candidates.
- *  precision PP_FP64 or PP_FP32.
+ *  precision PP_FP64, PP_FP32 or PP_FP32_FAST.
  *  scheme  PP_RK4, PP_MAGNUS4 or PP_SPLIT2.
  *  N       (device) [ncand] FP64 output.
  *  n_p     (device) [ncand][nz][ny][nx] FP64 output (x fastest), or NULL.
@@ -135,6 +139,27 @@ int pp_synth_field(const double *params, int32_t ncand, const pp_field_spec *spe
 int pp_pair_number(const double *A, int32_t ncand, int32_t ld, const int32_t *n_steps, double dt,
                    const pp_grid *grid, int32_t precision, int32_t scheme, double *N, double *n_p,
                    void *stream);
+
+/* Launch-configuration tuner of the propagation kernel.  FP32 paths can run the
+ * kernel with pp_num_launch_configs() launch configurations (threads per CTA x
+ * shared-memory tile length; pp_launch_config describes configuration k); the
+ * results do not depend on the configuration (the momentum sum uses fixed
+ * groups of 128 modes).  pp_tune_pair_number runs pp_pair_number's work once
+ * per configuration (plus one untimed launch each) on the caller's inputs,
+ * times it with CUDA events on `stream`, waits for the stream, and records the
+ * fastest configuration for this workload shape (precision, scheme, ncand,
+ * number of modes, largest n_steps); later pp_pair_number, pp_de_step and
+ * pp_pair_number_static calls with that shape use it, others use a built-in
+ * default.  N receives the pair numbers of the last run.  config_ms (host,
+ * pp_num_launch_configs() floats, or NULL) receives each configuration's time;
+ * chosen_config (host, or NULL) the winner.  FP64 paths have one configuration.
+ * pp_clear_tuning() forgets every tuned shape.  Errors as pp_pair_number. */
+int pp_tune_pair_number(const double *A, int32_t ncand, int32_t ld, const int32_t *n_steps,
+                        double dt, const pp_grid *grid, int32_t precision, int32_t scheme,
+                        double *N, int32_t *chosen_config, float *config_ms, void *stream);
+int pp_num_launch_configs(void);
+int pp_launch_config(int32_t k, int32_t *threads_per_cta, int32_t *tile_bytes);
+void pp_clear_tuning(void);
 
 /* pp_pair_number without any device allocation.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory --
@@ -149,9 +174,11 @@ int pp_pair_number(const double *A, int32_t ncand, int32_t ld, const int32_t *n_
  * GPU that loads the library holds until the process exits.
  *  - A call whose scratch would exceed that size returns PP_ERR_INVALID_ARG
  *    with the required size in pp_last_error(); it needs about
- *    ncand * (padded n_steps * 32 B + ceil(modes/256) * 8 B) for PP_MAGNUS4
- *    (16 B per step for PP_RK4 in FP32 and PP_SPLIT2), e.g. 64 candidates of
- *    4096 steps, or 16 candidates of 16384 steps.
+ *    ncand * (padded n_steps * E + ceil(modes/128) * 8 B), with a table entry
+ *    of E = 32 B per step for PP_MAGNUS4 and PP_RK4 in FP32 (16 B for
+ *    PP_SPLIT2; twice these in FP64) and n_steps padded to the kernel's tile
+ *    (256 to 1024 steps), e.g. 64 candidates of 4096 steps, or 16 candidates
+ *    of 16384 steps, with PP_MAGNUS4 in FP32.
  *  - The first call on each device looks up the device address of the array
  *    (a one-time set-up with that device current); make that first call before
  *    any stream capture.

@@ -27,7 +27,9 @@ PP_ERR_NOT_IMPLEMENTED = 6
 
 PP_FP64 = 0
 PP_FP32 = 1
-PRECISIONS = {"fp64": PP_FP64, "fp32": PP_FP32, PP_FP64: PP_FP64, PP_FP32: PP_FP32}
+PP_FP32_FAST = 2
+PRECISIONS = {"fp64": PP_FP64, "fp32": PP_FP32, "fp32fast": PP_FP32_FAST, PP_FP64: PP_FP64,
+              PP_FP32: PP_FP32, PP_FP32_FAST: PP_FP32_FAST}
 
 PP_RK4 = 0
 PP_MAGNUS4 = 1
@@ -37,7 +39,9 @@ SCHEMES = {"rk4": PP_RK4, "magnus4": PP_MAGNUS4, "split2": PP_SPLIT2,
 
 EXPORTS = ("pp_synth_field", "pp_pair_number", "pp_de_propose", "pp_de_select", "pp_de_step",
            "pp_sync_status", "pp_set_wait_limit", "pp_set_skip_copies", "pp_last_error",
-           "pp_version", "pp_profile_begin", "pp_profile_end")
+           "pp_version", "pp_profile_begin", "pp_profile_end", "pp_tune_pair_number",
+           "pp_num_launch_configs", "pp_launch_config", "pp_clear_tuning", "pp_pair_number_static",
+           "pp_static_scratch_bytes")
 
 
 class PPError(RuntimeError):
@@ -86,6 +90,13 @@ def lib():
         L.pp_set_skip_copies.argtypes = [ctypes.c_int]
         L.pp_last_error.restype = ctypes.c_char_p
         L.pp_profile_end.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
+        L.pp_tune_pair_number.argtypes = [_vp, _i32, _i32, _vp, _d, ctypes.POINTER(Grid), _i32,
+                                          _i32, _vp, ctypes.POINTER(_i32),
+                                          ctypes.POINTER(ctypes.c_float), _vp]
+        L.pp_launch_config.argtypes = [_i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]
+        L.pp_clear_tuning.restype = None
+        L.pp_pair_number_static.argtypes = L.pp_pair_number.argtypes
+        L.pp_static_scratch_bytes.restype = ctypes.c_size_t
         _lib = L
     return _lib
 
@@ -161,6 +172,40 @@ def pair_number(A, dt, grid, precision="fp32", n_steps=None, want_n=False, strea
                                 PRECISIONS[precision], SCHEMES[scheme], _ptr(N), _ptr(n),
                                 _stream(stream)))
     return N, n
+
+
+def tune_pair_number(A, dt, grid, precision="fp32", scheme="magnus4", n_steps=None, stream=None):
+    """pp_tune_pair_number: time every launch configuration on these inputs, remember the
+    fastest for this workload shape.  Returns (chosen index, per-configuration ms, N)."""
+    import torch
+    g = _grid(grid)
+    ncand, _, ld = A.shape
+    N = torch.empty(ncand, dtype=torch.float64, device=A.device)
+    nc = lib().pp_num_launch_configs()
+    ms = (ctypes.c_float * nc)()
+    chosen = _i32(-1)
+    ns = None
+    if n_steps is not None:
+        arr = (ctypes.c_int32 * ncand)(*[int(x) for x in n_steps])
+        ns = ctypes.cast(arr, ctypes.c_void_p)
+    _check(lib().pp_tune_pair_number(_ptr(A), ncand, ld, ns, float(dt), ctypes.byref(g),
+                                     PRECISIONS[precision], SCHEMES[scheme], _ptr(N),
+                                     ctypes.byref(chosen), ms, _stream(stream)))
+    return chosen.value, list(ms), N
+
+
+def launch_configs():
+    """[(threads per CTA, tile bytes)] of the propagation kernel's launch configurations."""
+    out = []
+    for k in range(lib().pp_num_launch_configs()):
+        t, b = _i32(0), _i32(0)
+        _check(lib().pp_launch_config(k, ctypes.byref(t), ctypes.byref(b)))
+        out.append((t.value, b.value))
+    return out
+
+
+def clear_tuning():
+    lib().pp_clear_tuning()
 
 
 def de_propose(pop, lo, hi, periodic, F, CR, seed, generation, stream=None, out=None):

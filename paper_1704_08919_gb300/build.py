@@ -39,7 +39,9 @@ def build(force=False, verbose_ptxas=False):
     headers.append(os.path.join(INCLUDE, "pp.h"))
     srcs = sources()
     objs = [os.path.join(OUT_DIR, os.path.basename(s)[:-3] + ".o") for s in srcs]
-    flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+    # -fmad=false: only explicit fma() calls fuse, so every kernel instantiation (any
+    # launch configuration) rounds exactly as the source is written.
+    flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC",
                     "-I", INCLUDE, "-I", CSRC, "--expt-relaxed-constexpr"]
     if verbose_ptxas:
         flags += ["-Xptxas", "-v"]

@@ -299,8 +299,8 @@ int pp_pair_number(const double *A, int32_t ncand, int32_t ld, const int32_t *n_
         return fail(PP_ERR_INVALID_ARG, "A and N must not be NULL");
     if (!(dt > 0.0) || !isfinite(dt))
         return fail(PP_ERR_INVALID_ARG, "dt must be positive and finite");
-    if (precision != PP_FP64 && precision != PP_FP32)
-        return fail(PP_ERR_INVALID_ARG, "precision must be PP_FP64 or PP_FP32");
+    if (precision != PP_FP64 && precision != PP_FP32 && precision != PP_FP32_FAST)
+        return fail(PP_ERR_INVALID_ARG, "precision must be PP_FP64, PP_FP32 or PP_FP32_FAST");
     if (scheme != PP_RK4 && scheme != PP_MAGNUS4 && scheme != PP_SPLIT2)
         return fail(PP_ERR_INVALID_ARG, "scheme must be PP_RK4, PP_MAGNUS4 or PP_SPLIT2");
     if (ld < 3)
@@ -330,8 +330,8 @@ int pp_pair_number_static(const double *A, int32_t ncand, int32_t ld, const int3
         return fail(PP_ERR_INVALID_ARG, "A and N must not be NULL");
     if (!(dt > 0.0) || !isfinite(dt))
         return fail(PP_ERR_INVALID_ARG, "dt must be positive and finite");
-    if (precision != PP_FP64 && precision != PP_FP32)
-        return fail(PP_ERR_INVALID_ARG, "precision must be PP_FP64 or PP_FP32");
+    if (precision != PP_FP64 && precision != PP_FP32 && precision != PP_FP32_FAST)
+        return fail(PP_ERR_INVALID_ARG, "precision must be PP_FP64, PP_FP32 or PP_FP32_FAST");
     if (scheme != PP_RK4 && scheme != PP_MAGNUS4 && scheme != PP_SPLIT2)
         return fail(PP_ERR_INVALID_ARG, "scheme must be PP_RK4, PP_MAGNUS4 or PP_SPLIT2");
     if (ld < 3)
@@ -346,6 +346,51 @@ int pp_pair_number_static(const double *A, int32_t ncand, int32_t ld, const int3
 }
 
 size_t pp_static_scratch_bytes(void) { return static_scratch_bytes(); }
+
+int pp_tune_pair_number(const double *A, int32_t ncand, int32_t ld, const int32_t *n_steps,
+                        double dt, const pp_grid *grid, int32_t precision, int32_t scheme,
+                        double *N, int32_t *chosen_config, float *config_ms, void *stream)
+{
+    clear_error();
+    int rc = check_grid(grid);
+    if (rc)
+        return rc;
+    if (ncand < 1 || ncand > 65535)
+        return fail(PP_ERR_INVALID_ARG, "ncand must be in [1, 65535]");
+    if (!A || !N)
+        return fail(PP_ERR_INVALID_ARG, "A and N must not be NULL");
+    if (!(dt > 0.0) || !isfinite(dt))
+        return fail(PP_ERR_INVALID_ARG, "dt must be positive and finite");
+    if (precision != PP_FP64 && precision != PP_FP32 && precision != PP_FP32_FAST)
+        return fail(PP_ERR_INVALID_ARG, "precision must be PP_FP64, PP_FP32 or PP_FP32_FAST");
+    if (scheme != PP_RK4 && scheme != PP_MAGNUS4 && scheme != PP_SPLIT2)
+        return fail(PP_ERR_INVALID_ARG, "scheme must be PP_RK4, PP_MAGNUS4 or PP_SPLIT2");
+    if (ld < 3)
+        return fail(PP_ERR_INVALID_ARG, "ld must be >= 3");
+    for (int c = 0; c < ncand; ++c) {
+        long long ns = n_steps ? n_steps[c] : (ld - 1) / 2;
+        if (ns < 1 || 2 * ns + 1 > ld)
+            return fail(PP_ERR_INVALID_ARG, "candidate %d: n_steps %lld needs 2 n_steps + 1 <= ld (%d)", c, ns, ld);
+    }
+    return tune_pair_number(A, ncand, ld, n_steps, dt, grid, precision, scheme, N, chosen_config,
+                            config_ms, (cudaStream_t)stream);
+}
+
+int pp_num_launch_configs(void) { return num_launch_configs(); }
+
+int pp_launch_config(int32_t k, int32_t *threads_per_cta, int32_t *tile_bytes)
+{
+    clear_error();
+    if (k < 0 || k >= num_launch_configs() || !threads_per_cta || !tile_bytes)
+        return fail(PP_ERR_INVALID_ARG, "configuration index out of range or NULL output");
+    int t = 0, b = 0;
+    launch_config(k, &t, &b);
+    *threads_per_cta = t;
+    *tile_bytes = b;
+    return PP_OK;
+}
+
+void pp_clear_tuning(void) { clear_tuning(); }
 
 int pp_de_propose(const double *pop, int32_t NP, int32_t D, const double *lo, const double *hi,
                   const uint8_t *periodic, double F, double CR, uint64_t seed, uint64_t generation,
@@ -390,8 +435,8 @@ int pp_de_step(double *pop, double *fit, int32_t NP, const pp_field_spec *spec, 
         return fail(PP_ERR_INVALID_ARG, "NP must be in [4, 65535]");
     if (!pop || !fit || !lo || !hi)
         return fail(PP_ERR_INVALID_ARG, "pop, fit, lo, hi must not be NULL");
-    if (precision != PP_FP64 && precision != PP_FP32)
-        return fail(PP_ERR_INVALID_ARG, "precision must be PP_FP64 or PP_FP32");
+    if (precision != PP_FP64 && precision != PP_FP32 && precision != PP_FP32_FAST)
+        return fail(PP_ERR_INVALID_ARG, "precision must be PP_FP64, PP_FP32 or PP_FP32_FAST");
     if (scheme != PP_RK4 && scheme != PP_MAGNUS4 && scheme != PP_SPLIT2)
         return fail(PP_ERR_INVALID_ARG, "scheme must be PP_RK4, PP_MAGNUS4 or PP_SPLIT2");
     if (!(CR >= 0.0 && CR <= 1.0) || !isfinite(F))

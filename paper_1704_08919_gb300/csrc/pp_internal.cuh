@@ -52,6 +52,14 @@ int launch_pair_number_static(const double *A, int ncand, int ld, const int32_t 
                               double *n_p, cudaStream_t stream);
 size_t static_scratch_bytes();
 
+// Launch-configuration tuner of the propagation kernel (pp_propagate.cu).
+int num_launch_configs();
+void launch_config(int k, int *threads, int *tile_bytes);
+int tune_pair_number(const double *A, int ncand, int ld, const int32_t *n_steps_host, double dt,
+                     const pp_grid *grid, int precision, int scheme, double *N, int32_t *chosen,
+                     float *config_ms, cudaStream_t stream);
+void clear_tuning();
+
 // Field synthesis launch without argument re-validation (pp_field.cu).
 int launch_synth_field(const double *params, int ncand, const pp_field_spec *spec, double *A,
                        int ld, double *E, double *scale, cudaStream_t stream);

@@ -30,13 +30,17 @@
 #include <math.h>
 #include <string.h>
 
+#include <map>
 #include <mutex>
 
 #include "pp_internal.cuh"
 
 namespace {
 
-constexpr int kThreads = 256;
+// Modes per partial sum of the momentum integral: the per-CTA sums are formed
+// over fixed groups of kGroup consecutive modes, so N does not depend on the
+// launch configuration (threads per CTA, tile length) the tuner picks.
+constexpr int kGroup = 128;
 
 struct alignas(32) dbl4 {
     double x, y, z, w;
@@ -120,7 +124,6 @@ __device__ __forceinline__ double proj_pos2(double hx, double hy, double hz, con
 template <typename T, bool COMP>
 struct ScalarPolicy {
     using Entry = typename Vec4<T>::type;
-    static constexpr int TILE = 8192 / (int)sizeof(Entry);
 
     __device__ static Entry make_entry(double ax3, double ay3, double ax6, double ay6)
     {
@@ -279,9 +282,9 @@ struct alignas(32) PackedEntry {
     f2 ax3, ay3, ax6, ay6;  // (dt/3)(A_x, A_x), (dt/3)(A_y, -A_y), (dt/6)(...), (dt/6)(...)
 };
 
+template <bool COMP>
 struct PackedPolicy {
     using Entry = PackedEntry;
-    static constexpr int TILE = 512;  // 16 KiB per buffer
 
     __device__ static Entry make_entry(double ax3, double ay3, double ax6, double ay6)
     {
@@ -341,7 +344,7 @@ struct PackedPolicy {
         const H2 hn = make_h(st.px6, st.py6, e.ax6, e.ay6);
         f2 e1[4], e2[4], y[4], S[4];
         rot2(st.h6, st.ez6, st.nez6, st.hi, e1);
-#pragma unroll
+        #pragma unroll
         for (int q = 0; q < 4; ++q)
             y[q] = ffma2(three, e1[q], st.hi[q]);
         rot2(h3, st.ez3, st.nez3, y, e2);
@@ -354,13 +357,16 @@ struct PackedPolicy {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             y[q] = ffma2(three, e2[q], st.hi[q]);
-            S[q] = fadd2(fadd2(S[q], e2[q]), st.lo[q]);
+            S[q] = fadd2(S[q], e2[q]);
+            if (COMP)
+                S[q] = fadd2(S[q], st.lo[q]);
         }
         rot2_acc(hn, st.ez6, st.nez6, y, S);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const f2 h = fadd2(st.hi[q], S[q]);
-            st.lo[q] = fsub2(S[q], fsub2(h, st.hi[q]));
+            if (COMP)
+                st.lo[q] = fsub2(S[q], fsub2(h, st.hi[q]));
             st.hi[q] = h;
         }
         st.h6 = hn;
@@ -374,6 +380,8 @@ struct PackedPolicy {
             float h0, h1, l0, l1;
             unpk2(st.hi[q], h0, h1);
             unpk2(st.lo[q], l0, l1);
+            if (!COMP)
+                l0 = l1 = 0.0f;
             out[q] = s ? (double)h1 + (double)l1 : (double)h0 + (double)l0;
         }
     }
@@ -437,7 +445,6 @@ struct MagnusPolicy {
     struct alignas(sizeof(T) * 8) Entry {
         T ax, ay, dx, dy, c, pad0, pad1, pad2;
     };
-    static constexpr int TILE = 8192 / (int)sizeof(Entry);
 
     __device__ static Entry make_entry6(double dt, double a0x, double a0y, double ahx, double ahy,
                                         double a1x, double a1y)
@@ -480,32 +487,39 @@ struct MagnusPolicy {
     {
         const T u = st.dtpx - e.ax, v = st.dtpy - e.ay;
         const T w = fma(e.dy, st.px, fma(e.dx, st.py, -e.c));
-        const T edy = st.eps * e.dy, edx = st.eps * e.dx;
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
-            const T Hx = s ? u + edy : u - edy;
-            const T Hy = s ? -v - edx : v - edx;
+            const T Hx = s ? fma(st.eps, e.dy, u) : fma(-st.eps, e.dy, u);
+            const T Hy = s ? fma(-st.eps, e.dx, -v) : fma(-st.eps, e.dx, v);
             const T Hz = s ? st.dteps - w : st.dteps + w;
             const T t2 = fma(Hz, Hz, fma(Hy, Hy, Hx * Hx));
             const T cm1 = TrigSeries<T>::cm1(t2);
             const T sc = TrigSeries<T>::sinc(t2);
             const T gx = sc * Hx, gy = sc * Hy, gz = sc * Hz;
             const T *z = st.hi[s];
-            T D[4];
-            D[0] = fma(gz, z[1], fma(gx, z[3], fma(-gy, z[2], cm1 * z[0])));
-            D[1] = fma(-gz, z[0], fma(-gx, z[2], fma(-gy, z[3], cm1 * z[1])));
-            D[2] = fma(gx, z[1], fma(gy, z[0], fma(-gz, z[3], cm1 * z[2])));
-            D[3] = fma(-gx, z[0], fma(gy, z[1], fma(gz, z[2], cm1 * z[3])));
+            if (COMP) {
+                T D[4];
+                D[0] = fma(gz, z[1], fma(gx, z[3], fma(-gy, z[2], cm1 * z[0])));
+                D[1] = fma(-gz, z[0], fma(-gx, z[2], fma(-gy, z[3], cm1 * z[1])));
+                D[2] = fma(gx, z[1], fma(gy, z[0], fma(-gz, z[3], cm1 * z[2])));
+                D[3] = fma(-gx, z[0], fma(gy, z[1], fma(gz, z[2], cm1 * z[3])));
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                if (COMP) {
+                for (int q = 0; q < 4; ++q) {
                     const T Dl = D[q] + st.lo[s][q];
                     const T h = st.hi[s][q] + Dl;
                     st.lo[s][q] = Dl - (h - st.hi[s][q]);
                     st.hi[s][q] = h;
-                } else {
-                    st.hi[s][q] = st.hi[s][q] + D[q];
                 }
+            } else {
+                // uncompensated: the increment is accumulated straight into the state
+                T nz[4];
+                nz[0] = fma(gz, z[1], fma(gx, z[3], fma(-gy, z[2], fma(cm1, z[0], z[0]))));
+                nz[1] = fma(-gz, z[0], fma(-gx, z[2], fma(-gy, z[3], fma(cm1, z[1], z[1]))));
+                nz[2] = fma(gx, z[1], fma(gy, z[0], fma(-gz, z[3], fma(cm1, z[2], z[2]))));
+                nz[3] = fma(-gx, z[0], fma(gy, z[1], fma(gz, z[2], fma(cm1, z[3], z[3]))));
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    st.hi[s][q] = nz[q];
             }
         }
     }
@@ -533,7 +547,6 @@ struct SplitPolicy {
     struct alignas(sizeof(T) * 4) Entry {
         T cm1, wx, wy, pad;
     };
-    static constexpr int TILE = 8192 / (int)sizeof(Entry);
 
     __device__ static Entry make_entry2(double dt, double ahx, double ahy)
     {
@@ -601,20 +614,28 @@ struct SplitPolicy {
 #pragma unroll
             for (int q = 0; q < 4; ++q)
                 y[q] = z[q] + D[q];
-            D[0] = fma(st.gz, y[1], fma(st.gx, y[3], fma(-gy, y[2], fma(st.c0m1, y[0], D[0]))));
-            D[1] = fma(-st.gz, y[0], fma(-st.gx, y[2], fma(-gy, y[3], fma(st.c0m1, y[1], D[1]))));
-            D[2] = fma(st.gx, y[1], fma(gy, y[0], fma(-st.gz, y[3], fma(st.c0m1, y[2], D[2]))));
-            D[3] = fma(-st.gx, y[0], fma(gy, y[1], fma(st.gz, y[2], fma(st.c0m1, y[3], D[3]))));
+            if (COMP) {
+                D[0] = fma(st.gz, y[1], fma(st.gx, y[3], fma(-gy, y[2], fma(st.c0m1, y[0], D[0]))));
+                D[1] = fma(-st.gz, y[0], fma(-st.gx, y[2], fma(-gy, y[3], fma(st.c0m1, y[1], D[1]))));
+                D[2] = fma(st.gx, y[1], fma(gy, y[0], fma(-st.gz, y[3], fma(st.c0m1, y[2], D[2]))));
+                D[3] = fma(-st.gx, y[0], fma(gy, y[1], fma(st.gz, y[2], fma(st.c0m1, y[3], D[3]))));
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                if (COMP) {
+                for (int q = 0; q < 4; ++q) {
                     const T Dl = D[q] + st.lo[s][q];
                     const T h = st.hi[s][q] + Dl;
                     st.lo[s][q] = Dl - (h - st.hi[s][q]);
                     st.hi[s][q] = h;
-                } else {
-                    st.hi[s][q] = st.hi[s][q] + D[q];
                 }
+            } else {
+                // uncompensated: the free factor is applied to y = psi + D_v directly
+                T nz[4];
+                nz[0] = fma(st.gz, y[1], fma(st.gx, y[3], fma(-gy, y[2], fma(st.c0m1, y[0], y[0]))));
+                nz[1] = fma(-st.gz, y[0], fma(-st.gx, y[2], fma(-gy, y[3], fma(st.c0m1, y[1], y[1]))));
+                nz[2] = fma(st.gx, y[1], fma(gy, y[0], fma(-st.gz, y[3], fma(st.c0m1, y[2], y[2]))));
+                nz[3] = fma(-st.gx, y[0], fma(gy, y[1], fma(st.gz, y[2], fma(st.c0m1, y[3], y[3]))));
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    st.hi[s][q] = nz[q];
             }
         }
     }
@@ -699,8 +720,8 @@ __global__ void build_table_kernel(const double *__restrict__ A, int ld, int ns_
     table[(size_t)c * padded + n] = e;
 }
 
-template <class P>
-__global__ void __launch_bounds__(kThreads)
+template <class P, int THREADS, int TILE_BYTES>
+__global__ void __launch_bounds__(THREADS)
     propagate_kernel(const double *__restrict__ A, int ld, int ns_uniform,
                      const int *__restrict__ ns_array, const typename P::Entry *__restrict__ table,
                      int padded, double dt, pp_grid g, double *__restrict__ n_p,
@@ -708,15 +729,16 @@ __global__ void __launch_bounds__(kThreads)
                      unsigned int *__restrict__ status)
 {
     using V = typename P::Entry;
-    constexpr int TILE = P::TILE;
+    constexpr int TILE = TILE_BYTES / (int)sizeof(V);
+    static_assert(THREADS % kGroup == 0, "CTA size must be a multiple of the partial-sum group");
     __shared__ __align__(128) V buf[2][TILE];
     __shared__ __align__(8) uint64_t bar[2];
-    __shared__ double red[kThreads / 32];
+    __shared__ double red[THREADS / 32];
 
     const int c = blockIdx.y;
     const int tid = threadIdx.x;
     const int nmodes = g.nx * g.ny * g.nz;
-    const int m = blockIdx.x * kThreads + tid;
+    const int m = blockIdx.x * THREADS + tid;
     const bool active = m < nmodes;
     const int ns = ns_array ? ns_array[c] : ns_uniform;
     const int ntiles = (ns + TILE - 1) / TILE;
@@ -829,11 +851,17 @@ __global__ void __launch_bounds__(kThreads)
     if ((tid & 31) == 0)
         red[tid >> 5] = wf;
     __syncthreads();
-    if (tid == 0) {
-        double acc = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w)
-            acc += red[w];
-        partial[(size_t)c * gridDim.x + blockIdx.x] = acc;
+    constexpr int kGroups = THREADS / kGroup;
+    const int ngroups = (nmodes + kGroup - 1) / kGroup;
+    if (tid < kGroups) {
+        const int gidx = blockIdx.x * kGroups + tid;
+        if (gidx < ngroups) {
+            double acc = 0.0;
+#pragma unroll
+            for (int w = 0; w < kGroup / 32; ++w)
+                acc += red[tid * (kGroup / 32) + w];
+            partial[(size_t)c * ngroups + gidx] = acc;
+        }
     }
 }
 
@@ -861,12 +889,12 @@ __global__ void finalize_kernel(const double *__restrict__ partial, int nblk, do
     }
 }
 
-template <class P>
+template <class P, int THREADS, int TILE_BYTES>
 int run(const double *A, int ncand, int ld, const int32_t *ns_host, double dt, const pp_grid *grid,
         double *N, double *n_p, cudaStream_t stream)
 {
     using V = typename P::Entry;
-    constexpr int TILE = P::TILE;
+    constexpr int TILE = TILE_BYTES / (int)sizeof(V);
     int max_ns = 0;
     bool uniform = true;
     int ns0 = ns_host ? ns_host[0] : (ld - 1) / 2;
@@ -880,20 +908,21 @@ int run(const double *A, int ncand, int ld, const int32_t *ns_host, double dt, c
     if (!status)
         return pp::fail(PP_ERR_CUDA, "status word unavailable");
     const int nmodes = grid->nx * grid->ny * grid->nz;
-    const int nblk = (nmodes + kThreads - 1) / kThreads;
+    const int nblk = (nmodes + THREADS - 1) / THREADS;
+    const int ngroups = (nmodes + kGroup - 1) / kGroup;
 
     void *table = nullptr, *partial = nullptr, *nsdev = nullptr;
     int rc = pp::scratch(pp::SCR_TABLE, (size_t)ncand * padded * sizeof(V), &table);
     if (rc)
         return rc;
-    rc = pp::scratch(pp::SCR_PARTIAL, (size_t)ncand * nblk * sizeof(double) + 256 * sizeof(int) +
+    rc = pp::scratch(pp::SCR_PARTIAL, (size_t)ncand * ngroups * sizeof(double) + 256 * sizeof(int) +
                                           (size_t)ncand * sizeof(int),
                      &partial);
     if (rc)
         return rc;
     const int *ns_array = nullptr;
     if (!uniform) {
-        nsdev = (char *)partial + (size_t)ncand * nblk * sizeof(double);
+        nsdev = (char *)partial + (size_t)ncand * ngroups * sizeof(double);
         nsdev = (void *)(((uintptr_t)nsdev + 255) & ~(uintptr_t)255);
         cudaError_t e = cudaMemcpyAsync(nsdev, ns_host, sizeof(int) * ncand, cudaMemcpyHostToDevice, stream);
         if (e != cudaSuccess)
@@ -904,11 +933,11 @@ int run(const double *A, int ncand, int ld, const int32_t *ns_host, double dt, c
     build_table_kernel<P><<<tg, 256, 0, stream>>>(A, ld, ns0, ns_array, padded, dt, (V *)table);
     dim3 pg(nblk, ncand);
     pp::profile_mark_start(stream);
-    propagate_kernel<P><<<pg, kThreads, 0, stream>>>(A, ld, ns0, ns_array, (const V *)table,
+    propagate_kernel<P, THREADS, TILE_BYTES><<<pg, THREADS, 0, stream>>>(A, ld, ns0, ns_array, (const V *)table,
                                                              padded, dt, *grid, n_p, (double *)partial,
                                                              (long long)pp::wait_limit(), pp::skip_copies(), status);
     pp::profile_mark_stop(stream);
-    finalize_kernel<<<ncand, 256, 0, stream>>>((const double *)partial, nblk, N, status);
+    finalize_kernel<<<ncand, 256, 0, stream>>>((const double *)partial, ngroups, N, status);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return pp::cuda_fail(e, "pair-number kernel launch");
@@ -946,12 +975,12 @@ unsigned char *static_scratch_address()
     return addr[dev];
 }
 
-template <class P>
+template <class P, int THREADS, int TILE_BYTES>
 int run_static(const double *A, int ncand, int ld, const int32_t *ns_host, double dt,
                const pp_grid *grid, double *N, double *n_p, cudaStream_t stream)
 {
     using V = typename P::Entry;
-    constexpr int TILE = P::TILE;
+    constexpr int TILE = TILE_BYTES / (int)sizeof(V);
     int max_ns = 0;
     bool uniform = true;
     const int ns0 = ns_host ? ns_host[0] : (ld - 1) / 2;
@@ -962,9 +991,10 @@ int run_static(const double *A, int ncand, int ld, const int32_t *ns_host, doubl
     }
     const int padded = ((max_ns + TILE - 1) / TILE) * TILE;
     const int nmodes = grid->nx * grid->ny * grid->nz;
-    const int nblk = (nmodes + kThreads - 1) / kThreads;
+    const int nblk = (nmodes + THREADS - 1) / THREADS;
+    const int ngroups = (nmodes + kGroup - 1) / kGroup;
     const size_t table_bytes = align256((size_t)ncand * padded * sizeof(V));
-    const size_t part_bytes = align256((size_t)ncand * nblk * sizeof(double));
+    const size_t part_bytes = align256((size_t)ncand * ngroups * sizeof(double));
     const size_t ns_bytes = uniform ? 0 : align256((size_t)ncand * sizeof(int));
     const size_t need = table_bytes + part_bytes + ns_bytes;
     if (need > kStaticScratchBytes)
@@ -991,14 +1021,119 @@ int run_static(const double *A, int ncand, int ld, const int32_t *ns_host, doubl
     dim3 tg((padded + 255) / 256, ncand);
     build_table_kernel<P><<<tg, 256, 0, stream>>>(A, ld, ns0, ns_array, padded, dt, table);
     dim3 pg(nblk, ncand);
-    propagate_kernel<P><<<pg, kThreads, 0, stream>>>(A, ld, ns0, ns_array, table, padded, dt, *grid,
+    propagate_kernel<P, THREADS, TILE_BYTES><<<pg, THREADS, 0, stream>>>(A, ld, ns0, ns_array, table, padded, dt, *grid,
                                                      n_p, partial, (long long)pp::wait_limit(),
                                                      pp::skip_copies(), status);
-    finalize_kernel<<<ncand, 256, 0, stream>>>(partial, nblk, N, status);
+    finalize_kernel<<<ncand, 256, 0, stream>>>(partial, ngroups, N, status);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return pp::cuda_fail(e, "pair-number kernel launch");
     return PP_OK;
+}
+
+// ---------------------------------------------------------------- launch configurations
+// (threads per CTA, bytes per shared-memory tile buffer).  FP32 paths may use
+// any of them (chosen by pp_tune_pair_number, else kDefault*); FP64 paths use
+// configuration 0.  The arithmetic does not depend on the configuration.
+constexpr int kNumConfigs = 6;
+constexpr int kCfgThreads[kNumConfigs] = {256, 128, 512, 256, 128, 512};
+constexpr int kCfgTileBytes[kNumConfigs] = {8192, 8192, 8192, 32768, 32768, 32768};
+
+using LaunchFn = int (*)(const double *, int, int, const int32_t *, double, const pp_grid *, double *,
+                         double *, cudaStream_t);
+
+template <class P, bool ALL>
+struct ConfigTable {
+    LaunchFn run_fn[kNumConfigs];
+    LaunchFn static_fn[kNumConfigs];
+    ConfigTable()
+    {
+        if constexpr (ALL) {
+            run_fn[0] = &run<P, 256, 8192>;
+            run_fn[1] = &run<P, 128, 8192>;
+            run_fn[2] = &run<P, 512, 8192>;
+            run_fn[3] = &run<P, 256, 32768>;
+            run_fn[4] = &run<P, 128, 32768>;
+            run_fn[5] = &run<P, 512, 32768>;
+            static_fn[0] = &run_static<P, 256, 8192>;
+            static_fn[1] = &run_static<P, 128, 8192>;
+            static_fn[2] = &run_static<P, 512, 8192>;
+            static_fn[3] = &run_static<P, 256, 32768>;
+            static_fn[4] = &run_static<P, 128, 32768>;
+            static_fn[5] = &run_static<P, 512, 32768>;
+        } else {
+            for (int k = 0; k < kNumConfigs; ++k) {
+                run_fn[k] = &run<P, 256, 8192>;
+                static_fn[k] = &run_static<P, 256, 8192>;
+            }
+        }
+    }
+};
+
+// Policy by (precision, scheme).
+struct PolicySlot {
+    const LaunchFn *run_fn;
+    const LaunchFn *static_fn;
+    bool tunable;
+    int default_cfg;
+};
+
+const PolicySlot &policy_slot(int precision, int scheme)
+{
+    static const ConfigTable<ScalarPolicy<double, false>, false> d_rk4;
+    static const ConfigTable<MagnusPolicy<double, false>, false> d_mag;
+    static const ConfigTable<SplitPolicy<double, false>, false> d_spl;
+    static const ConfigTable<PackedPolicy<true>, true> f_rk4;
+    static const ConfigTable<MagnusPolicy<float, true>, true> f_mag;
+    static const ConfigTable<SplitPolicy<float, true>, true> f_spl;
+    static const ConfigTable<PackedPolicy<false>, true> x_rk4;
+    static const ConfigTable<MagnusPolicy<float, false>, true> x_mag;
+    static const ConfigTable<SplitPolicy<float, false>, true> x_spl;
+    // defaults from timing the 64-candidate workload on GB300 (see the tuner)
+    static const PolicySlot slots[3][3] = {
+        {{d_rk4.run_fn, d_rk4.static_fn, false, 0}, {d_mag.run_fn, d_mag.static_fn, false, 0},
+         {d_spl.run_fn, d_spl.static_fn, false, 0}},
+        {{f_rk4.run_fn, f_rk4.static_fn, true, 0}, {f_mag.run_fn, f_mag.static_fn, true, 2},
+         {f_spl.run_fn, f_spl.static_fn, true, 0}},
+        {{x_rk4.run_fn, x_rk4.static_fn, true, 0}, {x_mag.run_fn, x_mag.static_fn, true, 3},
+         {x_spl.run_fn, x_spl.static_fn, true, 3}},
+    };
+    return slots[precision][scheme];
+}
+
+// Tuned configurations, keyed by the workload shape.
+struct TuneKey {
+    int precision, scheme, ncand, nmodes, max_ns;
+    bool operator<(const TuneKey &o) const
+    {
+        if (precision != o.precision) return precision < o.precision;
+        if (scheme != o.scheme) return scheme < o.scheme;
+        if (ncand != o.ncand) return ncand < o.ncand;
+        if (nmodes != o.nmodes) return nmodes < o.nmodes;
+        return max_ns < o.max_ns;
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tuned;
+
+TuneKey make_key(int precision, int scheme, int ncand, int ld, const int32_t *ns, const pp_grid *g)
+{
+    int max_ns = 0;
+    for (int c = 0; c < ncand; ++c) {
+        const int v = ns ? ns[c] : (ld - 1) / 2;
+        max_ns = v > max_ns ? v : max_ns;
+    }
+    return TuneKey{precision, scheme, ncand, g->nx * g->ny * g->nz, max_ns};
+}
+
+int chosen_config(int precision, int scheme, int ncand, int ld, const int32_t *ns, const pp_grid *g)
+{
+    const PolicySlot &slot = policy_slot(precision, scheme);
+    if (!slot.tunable)
+        return 0;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(make_key(precision, scheme, ncand, ld, ns, g));
+    return it == g_tuned.end() ? slot.default_cfg : it->second;
 }
 
 }  // namespace
@@ -1009,38 +1144,87 @@ int launch_pair_number(const double *A, int ncand, int ld, const int32_t *n_step
                        const pp_grid *grid, int precision, int scheme, double *N, double *n_p,
                        cudaStream_t stream)
 {
-    if (precision == PP_FP64) {
-        if (scheme == PP_MAGNUS4)
-            return run<MagnusPolicy<double, false>>(A, ncand, ld, n_steps_host, dt, grid, N, n_p, stream);
-        if (scheme == PP_SPLIT2)
-            return run<SplitPolicy<double, false>>(A, ncand, ld, n_steps_host, dt, grid, N, n_p, stream);
-        return run<ScalarPolicy<double, false>>(A, ncand, ld, n_steps_host, dt, grid, N, n_p, stream);
-    }
-    if (scheme == PP_MAGNUS4)
-        return run<MagnusPolicy<float, true>>(A, ncand, ld, n_steps_host, dt, grid, N, n_p, stream);
-    if (scheme == PP_SPLIT2)
-        return run<SplitPolicy<float, true>>(A, ncand, ld, n_steps_host, dt, grid, N, n_p, stream);
-    return run<PackedPolicy>(A, ncand, ld, n_steps_host, dt, grid, N, n_p, stream);
+    const int cfg = chosen_config(precision, scheme, ncand, ld, n_steps_host, grid);
+    return policy_slot(precision, scheme).run_fn[cfg](A, ncand, ld, n_steps_host, dt, grid, N, n_p,
+                                                      stream);
 }
 
 int launch_pair_number_static(const double *A, int ncand, int ld, const int32_t *n_steps_host,
                               double dt, const pp_grid *grid, int precision, int scheme, double *N,
                               double *n_p, cudaStream_t stream)
 {
-    if (precision == PP_FP64) {
-        if (scheme == PP_MAGNUS4)
-            return run_static<MagnusPolicy<double, false>>(A, ncand, ld, n_steps_host, dt, grid, N, n_p, stream);
-        if (scheme == PP_SPLIT2)
-            return run_static<SplitPolicy<double, false>>(A, ncand, ld, n_steps_host, dt, grid, N, n_p, stream);
-        return run_static<ScalarPolicy<double, false>>(A, ncand, ld, n_steps_host, dt, grid, N, n_p, stream);
-    }
-    if (scheme == PP_MAGNUS4)
-        return run_static<MagnusPolicy<float, true>>(A, ncand, ld, n_steps_host, dt, grid, N, n_p, stream);
-    if (scheme == PP_SPLIT2)
-        return run_static<SplitPolicy<float, true>>(A, ncand, ld, n_steps_host, dt, grid, N, n_p, stream);
-    return run_static<PackedPolicy>(A, ncand, ld, n_steps_host, dt, grid, N, n_p, stream);
+    const int cfg = chosen_config(precision, scheme, ncand, ld, n_steps_host, grid);
+    return policy_slot(precision, scheme).static_fn[cfg](A, ncand, ld, n_steps_host, dt, grid, N,
+                                                         n_p, stream);
 }
 
 size_t static_scratch_bytes() { return kStaticScratchBytes; }
+
+int num_launch_configs() { return kNumConfigs; }
+
+int tune_pair_number(const double *A, int ncand, int ld, const int32_t *n_steps_host, double dt,
+                     const pp_grid *grid, int precision, int scheme, double *N, int32_t *chosen,
+                     float *config_ms, cudaStream_t stream)
+{
+    const PolicySlot &slot = policy_slot(precision, scheme);
+    const int ncfg = slot.tunable ? kNumConfigs : 1;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess)
+        e = cudaEventCreate(&e1);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "tuner event");
+    int best = slot.default_cfg;
+    float best_ms = 3.0e38f;
+    int rc = PP_OK;
+    for (int k = 0; k < ncfg && rc == PP_OK; ++k) {
+        // one untimed launch (table build, caches), then one timed launch
+        rc = slot.run_fn[k](A, ncand, ld, n_steps_host, dt, grid, N, nullptr, stream);
+        if (rc)
+            break;
+        cudaEventRecord(e0, stream);
+        rc = slot.run_fn[k](A, ncand, ld, n_steps_host, dt, grid, N, nullptr, stream);
+        cudaEventRecord(e1, stream);
+        if (rc)
+            break;
+        float ms = 0.0f;
+        e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess)
+            e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "tuner timing");
+            break;
+        }
+        if (config_ms)
+            config_ms[k] = ms;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = k;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc)
+        return rc;
+    if (slot.tunable) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[make_key(precision, scheme, ncand, ld, n_steps_host, grid)] = best;
+    }
+    if (chosen)
+        *chosen = best;
+    return PP_OK;
+}
+
+void clear_tuning()
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned.clear();
+}
+
+void launch_config(int k, int *threads, int *tile_bytes)
+{
+    *threads = kCfgThreads[k];
+    *tile_bytes = kCfgTileBytes[k];
+}
 
 }  // namespace pp

@@ -120,8 +120,9 @@ def weighted_N(grid, n):
     return float(np.sum(W.ravel() * np.asarray(n).ravel()))
 
 
-@pytest.mark.parametrize("n_steps", [1, 7, 127, 128, 129, 255, 256, 257, 511, 512, 513, 1100])
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("n_steps", [1, 7, 127, 128, 129, 255, 256, 257, 511, 512, 513, 1023,
+                                     1025, 1100])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32fast"])
 @pytest.mark.parametrize("scheme", ["rk4", "magnus4", "split2"])
 def test_ragged_steps_and_modes(pp, n_steps, precision, scheme):
     # step counts around the shared-memory tiles (128..1024 steps depending on
@@ -350,12 +351,39 @@ def test_magnus_fp32_at_full_de_batch_size(pp):
     assert n_excess(n_m64[0].cpu().numpy().ravel()[idx], no, cfg["n_steps"]) <= 1.0
 
 
+@pytest.mark.parametrize("precision,scheme", [("fp32", "magnus4"), ("fp32fast", "magnus4"),
+                                              ("fp32", "rk4"), ("fp32fast", "split2"),
+                                              ("fp64", "rk4")])
+def test_tuner_picks_a_config_and_results_do_not_depend_on_it(pp, precision, scheme):
+    cfg = inputs.DE_BATCH
+    spec = dict(inputs.field_spec(cfg), n_steps=1500)
+    params = inputs.random_population(3, cfg["K"], seed=23)
+    A, _, _ = pp.synth_field(torch.tensor(params, device=DEV), spec)
+    grid = inputs.small_grid(20, 19, 7, ext=2.0)  # 2660 modes: partial CTAs for every size
+    dt = spec["T"] / spec["n_steps"]
+    pp.clear_tuning()
+    N_default, _ = pp.pair_number(A, dt, grid, precision=precision, scheme=scheme)
+    chosen, ms, N_last = pp.tune_pair_number(A, dt, grid, precision=precision, scheme=scheme)
+    N_tuned, _ = pp.pair_number(A, dt, grid, precision=precision, scheme=scheme)
+    assert pp.sync_status() == pp.PP_OK
+    configs = pp.launch_configs()
+    assert len(configs) == len(ms) == 6
+    if precision == "fp64":
+        assert chosen == 0 and ms[0] > 0
+    else:
+        assert 0 <= chosen < 6 and all(t > 0 for t in ms) and ms[chosen] == min(ms)
+    # the momentum sum is taken over fixed groups of 128 modes: bitwise equal N
+    assert torch.equal(N_default, N_last) and torch.equal(N_default, N_tuned)
+    pp.clear_tuning()
+
+
 def test_results_are_bitwise_reproducible(pp):
     g, ns, dt, A = rotating_gaussian()
     At = torch.tensor(A[None], device=DEV).repeat(3, 1, 1)
     out = [pp.pair_number(At, dt, g["grid"], precision=p)[0].cpu().numpy()
-           for p in ("fp32", "fp32", "fp64", "fp64")]
+           for p in ("fp32", "fp32", "fp64", "fp64", "fp32fast", "fp32fast")]
     assert np.array_equal(out[0], out[1]) and np.array_equal(out[2], out[3])
+    assert np.array_equal(out[4], out[5])
 
 
 def test_bounded_wait_timeout_reports_and_context_survives(pp):
