@@ -161,6 +161,51 @@ int pp_num_launch_configs(void);
 int pp_launch_config(int32_t k, int32_t *threads_per_cta, int32_t *tile_bytes);
 void pp_clear_tuning(void);
 
+/* ---- Uneven batches (candidates with their own pulse length, step count and
+ * momentum grid) and captured DE loops.  A pp_batch fixes, per population slot
+ * c, the pulse model specs[c] (same K, order, band and fluence for all slots;
+ * T and n_steps per slot with T / n_steps = dt) and the momentum grid grids[c],
+ * plus the precision and scheme.  pp_batch_create allocates every device
+ * buffer the batch needs (the step table, partial sums, work lists, potential,
+ * trial vectors and a device-resident DE generation counter); nothing later
+ * allocates, so the DE loop can be captured in a CUDA graph.
+ *  pp_batch_synth        params (device [ncand][4K]) -> A (device [ncand][2][ld],
+ *                        ld from pp_batch_info; slot c fills 2 n_steps[c] + 1 samples).
+ *  pp_batch_pair_number  A -> N (device [ncand]) and n_p (device, the slots'
+ *                        n(p) arrays concatenated in slot order, or NULL).  One
+ *                        persistent launch: CTAs take (slot, block of modes)
+ *                        items, longest slots first, from an atomic counter.
+ *                        N[c] is bitwise what pp_pair_number gives for slot c.
+ *  pp_batch_tune         times every launch configuration on A, keeps the fastest
+ *                        for this batch (waits for the stream).
+ *  pp_batch_de_step      one DE generation (propose, synthesise, score, select) on
+ *                        pop (device [ncand][4K]) and fit (device [ncand]); the
+ *                        generation number comes from the device counter, which
+ *                        the step then advances (pp_batch_set_generation sets it).
+ *  pp_batch_de_run       `generations` DE generations as one CUDA graph launch on
+ *                        `stream`: captured on first use (and again whenever an
+ *                        argument or the tuned configuration changes), then
+ *                        relaunched; generations continue from the device counter.
+ *                        Results are bitwise those of as many pp_batch_de_step calls.
+ * Errors: PP_ERR_INVALID_ARG for inconsistent specs, grids or arguments,
+ * PP_ERR_CUDA for allocation or capture failures.  A batch belongs to the device
+ * that was current at creation; calls on it must not overlap on the GPU. */
+typedef struct pp_batch pp_batch;
+int pp_batch_create(int32_t ncand, const pp_field_spec *specs, const pp_grid *grids, int32_t precision,
+                    int32_t scheme, double dt, pp_batch **out);
+void pp_batch_destroy(pp_batch *batch);
+int pp_batch_info(const pp_batch *batch, int32_t *ld, int64_t *total_modes, int32_t *config);
+int pp_batch_synth(pp_batch *batch, const double *params, double *A, void *stream);
+int pp_batch_pair_number(pp_batch *batch, const double *A, double *N, double *n_p, void *stream);
+int pp_batch_tune(pp_batch *batch, const double *A, double *N, int32_t *chosen_config,
+                  float *config_ms, void *stream);
+int pp_batch_set_generation(pp_batch *batch, uint64_t generation, void *stream);
+int pp_batch_de_step(pp_batch *batch, double *pop, double *fit, const double *lo, const double *hi,
+                     const uint8_t *periodic, double F, double CR, uint64_t seed, void *stream);
+int pp_batch_de_run(pp_batch *batch, double *pop, double *fit, const double *lo, const double *hi,
+                    const uint8_t *periodic, double F, double CR, uint64_t seed, int32_t generations,
+                    void *stream);
+
 /* pp_pair_number without any device allocation.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory --
  * for example a host application whose device memory is fully reserved by its

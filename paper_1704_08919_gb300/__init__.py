@@ -41,7 +41,9 @@ EXPORTS = ("pp_synth_field", "pp_pair_number", "pp_de_propose", "pp_de_select", 
            "pp_sync_status", "pp_set_wait_limit", "pp_set_skip_copies", "pp_last_error",
            "pp_version", "pp_profile_begin", "pp_profile_end", "pp_tune_pair_number",
            "pp_num_launch_configs", "pp_launch_config", "pp_clear_tuning", "pp_pair_number_static",
-           "pp_static_scratch_bytes")
+           "pp_static_scratch_bytes", "pp_batch_create", "pp_batch_destroy", "pp_batch_info",
+           "pp_batch_synth", "pp_batch_pair_number", "pp_batch_tune", "pp_batch_set_generation",
+           "pp_batch_de_step", "pp_batch_de_run")
 
 
 class PPError(RuntimeError):
@@ -97,6 +99,19 @@ def lib():
         L.pp_clear_tuning.restype = None
         L.pp_pair_number_static.argtypes = L.pp_pair_number.argtypes
         L.pp_static_scratch_bytes.restype = ctypes.c_size_t
+        L.pp_batch_create.argtypes = [_i32, ctypes.POINTER(FieldSpec), ctypes.POINTER(Grid), _i32,
+                                      _i32, _d, ctypes.POINTER(_vp)]
+        L.pp_batch_destroy.argtypes = [_vp]
+        L.pp_batch_destroy.restype = None
+        L.pp_batch_info.argtypes = [_vp, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_int64),
+                                    ctypes.POINTER(_i32)]
+        L.pp_batch_synth.argtypes = [_vp, _vp, _vp, _vp]
+        L.pp_batch_pair_number.argtypes = [_vp, _vp, _vp, _vp, _vp]
+        L.pp_batch_tune.argtypes = [_vp, _vp, _vp, ctypes.POINTER(_i32),
+                                    ctypes.POINTER(ctypes.c_float), _vp]
+        L.pp_batch_set_generation.argtypes = [_vp, _u64, _vp]
+        L.pp_batch_de_step.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _d, _d, _u64, _vp]
+        L.pp_batch_de_run.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _d, _d, _u64, _i32, _vp]
         _lib = L
     return _lib
 
@@ -206,6 +221,75 @@ def launch_configs():
 
 def clear_tuning():
     lib().pp_clear_tuning()
+
+
+class Batch:
+    """pp_batch_*: slots with their own pulse length, step count and momentum grid."""
+
+    def __init__(self, specs, grids, dt, precision="fp32", scheme="magnus4"):
+        n = len(specs)
+        sp = (FieldSpec * n)(*[_spec(x) for x in specs])
+        gr = (Grid * n)(*[_grid(x) for x in grids])
+        h = _vp()
+        _check(lib().pp_batch_create(n, sp, gr, PRECISIONS[precision], SCHEMES[scheme], float(dt),
+                                     ctypes.byref(h)))
+        self.h = h
+        self.ncand = n
+        self.grids = [_grid(x) for x in grids]
+        ld, tm, cfg = _i32(0), ctypes.c_int64(0), _i32(0)
+        _check(lib().pp_batch_info(h, ctypes.byref(ld), ctypes.byref(tm), ctypes.byref(cfg)))
+        self.ld, self.total_modes = ld.value, tm.value
+
+    def close(self):
+        if self.h:
+            lib().pp_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def config(self):
+        cfg = _i32(0)
+        _check(lib().pp_batch_info(self.h, None, None, ctypes.byref(cfg)))
+        return cfg.value
+
+    def synth(self, params, stream=None):
+        import torch
+        A = torch.zeros((self.ncand, 2, self.ld), dtype=torch.float64, device=params.device)
+        _check(lib().pp_batch_synth(self.h, _ptr(params), _ptr(A), _stream(stream)))
+        return A
+
+    def pair_number(self, A, want_n=False, stream=None):
+        import torch
+        N = torch.empty(self.ncand, dtype=torch.float64, device=A.device)
+        n = (torch.empty(self.total_modes, dtype=torch.float64, device=A.device) if want_n else None)
+        _check(lib().pp_batch_pair_number(self.h, _ptr(A), _ptr(N), _ptr(n), _stream(stream)))
+        return N, n
+
+    def tune(self, A, stream=None):
+        import torch
+        N = torch.empty(self.ncand, dtype=torch.float64, device=A.device)
+        ms = (ctypes.c_float * 6)()
+        chosen = _i32(-1)
+        _check(lib().pp_batch_tune(self.h, _ptr(A), _ptr(N), ctypes.byref(chosen), ms,
+                                   _stream(stream)))
+        return chosen.value, list(ms)
+
+    def set_generation(self, generation, stream=None):
+        _check(lib().pp_batch_set_generation(self.h, int(generation), _stream(stream)))
+
+    def de_step(self, pop, fit, lo, hi, periodic, F, CR, seed, stream=None):
+        _check(lib().pp_batch_de_step(self.h, _ptr(pop), _ptr(fit), _ptr(lo), _ptr(hi),
+                                      _ptr(periodic), float(F), float(CR), int(seed),
+                                      _stream(stream)))
+
+    def de_run(self, pop, fit, lo, hi, periodic, F, CR, seed, generations, stream=None):
+        _check(lib().pp_batch_de_run(self.h, _ptr(pop), _ptr(fit), _ptr(lo), _ptr(hi),
+                                     _ptr(periodic), float(F), float(CR), int(seed),
+                                     int(generations), _stream(stream)))
 
 
 def de_propose(pop, lo, hi, periodic, F, CR, seed, generation, stream=None, out=None):

@@ -35,10 +35,13 @@ __device__ __forceinline__ int below(uint64_t x, int n)
 __global__ void de_propose_kernel(const double *__restrict__ pop, int NP, int D,
                                   const double *__restrict__ lo, const double *__restrict__ hi,
                                   const uint8_t *__restrict__ periodic, double F, double CR,
-                                  uint64_t seed, uint64_t gen, double *__restrict__ trial)
+                                  uint64_t seed, uint64_t gen, double *__restrict__ trial,
+                                  const unsigned long long *__restrict__ gen_dev)
 {
     __shared__ int sr[4];  // r1, r2, r3, R (r1 = -1 on failure)
     const int i = blockIdx.x;
+    if (gen_dev)
+        gen = *gen_dev;
     const uint64_t key = sm64_at(sm64_at(seed, gen), (uint64_t)i);
     if (threadIdx.x == 0) {
         int r[3] = {-1, -1, -1};
@@ -97,6 +100,19 @@ __global__ void de_propose_kernel(const double *__restrict__ pop, int NP, int D,
     }
 }
 
+// Advances a device-resident generation counter (used by captured DE loops).
+__global__ void de_advance_kernel(unsigned long long *gen_dev)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0)
+        *gen_dev += 1ull;
+}
+
+__global__ void de_set_generation_kernel(unsigned long long *gen_dev, unsigned long long v)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0)
+        *gen_dev = v;
+}
+
 // One block per individual; the decision is read before any write.
 __global__ void de_select_kernel(double *__restrict__ pop, double *__restrict__ fit,
                                  const double *__restrict__ trial, const double *__restrict__ tfit,
@@ -121,9 +137,34 @@ int launch_de_propose(const double *pop, int NP, int D, const double *lo, const 
                       const uint8_t *periodic, double F, double CR, uint64_t seed, uint64_t gen,
                       double *trial, cudaStream_t stream)
 {
-    de_propose_kernel<<<NP, 64, 0, stream>>>(pop, NP, D, lo, hi, periodic, F, CR, seed, gen, trial);
+    de_propose_kernel<<<NP, 64, 0, stream>>>(pop, NP, D, lo, hi, periodic, F, CR, seed, gen, trial,
+                                             nullptr);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? PP_OK : cuda_fail(e, "DE propose launch");
+}
+
+int launch_de_propose_devgen(const double *pop, int NP, int D, const double *lo, const double *hi,
+                             const uint8_t *periodic, double F, double CR, uint64_t seed,
+                             const unsigned long long *gen_dev, double *trial, cudaStream_t stream)
+{
+    de_propose_kernel<<<NP, 64, 0, stream>>>(pop, NP, D, lo, hi, periodic, F, CR, seed, 0, trial,
+                                             gen_dev);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PP_OK : cuda_fail(e, "DE propose launch");
+}
+
+int launch_de_advance(unsigned long long *gen_dev, cudaStream_t stream)
+{
+    de_advance_kernel<<<1, 32, 0, stream>>>(gen_dev);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PP_OK : cuda_fail(e, "DE generation advance");
+}
+
+int launch_de_set_generation(unsigned long long *gen_dev, uint64_t v, cudaStream_t stream)
+{
+    de_set_generation_kernel<<<1, 32, 0, stream>>>(gen_dev, v);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PP_OK : cuda_fail(e, "DE generation set");
 }
 
 int launch_de_select(double *pop, double *fit, const double *trial, const double *trial_fit, int NP,

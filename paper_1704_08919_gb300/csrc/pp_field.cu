@@ -15,6 +15,8 @@
 // s = sqrt(U_const / that).
 #include <math.h>
 
+#include <vector>
+
 #include "pp_internal.cuh"
 
 namespace {
@@ -153,9 +155,148 @@ __global__ void samples_kernel(const double2 *__restrict__ coef, int M, int j0, 
     (void)d0r;
 }
 
+// ---- batches of candidates with their own pulse length and step count (same K,
+// order, band and fluence): per-candidate spectrum descriptors.
+struct SynthCand {
+    double T;
+    int n_steps, j0, M;
+    long long coef_off;  // into the coefficient buffer, 4 M double2 per candidate
+};
+
+__global__ void spectrum_batch_kernel(const double *__restrict__ params, int K, int order, double wmin,
+                                      double wmax, double U, const SynthCand *__restrict__ sc,
+                                      double2 *__restrict__ coef, unsigned int *__restrict__ status)
+{
+    __shared__ double red[256];
+    const int c = blockIdx.x;
+    const SynthCand d = sc[c];
+    const double *prm = params + (size_t)c * 4 * K;
+    const double dw = 2.0 * M_PI / d.T;
+    double2 *cf = coef + d.coef_off;
+    double ssq = 0.0;
+    for (int m = threadIdx.x; m < d.M; m += blockDim.x) {
+        const int j = d.j0 + m;
+        const double W = (double)j * dw;
+        double B[kMaxK];
+        bspline_basis(K, order, wmin, wmax, W, B);
+        for (int l = 0; l < 2; ++l) {
+            double e = 0.0, ph = 0.0;
+            for (int i = 0; i < K; ++i) {
+                e += prm[(2 * l) * K + i] * B[i];
+                ph += prm[(2 * l + 1) * K + i] * B[i];
+            }
+            ssq += e * e;
+            double sn, cs;
+            sincos(ph, &sn, &cs);
+            const double sg = (j & 1) ? -1.0 : 1.0;
+            cf[(size_t)l * 2 * d.M + m] = make_double2(sg * e * cs, -sg * e * sn);
+            cf[(size_t)l * 2 * d.M + d.M + m] = make_double2(sg * e * cs / W, -sg * e * sn / W);
+        }
+    }
+    red[threadIdx.x] = ssq;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    const double Uraw = 0.5 * d.T * red[0];
+    const double s = Uraw > 0.0 ? sqrt(U / Uraw) : 0.0;
+    if (threadIdx.x == 0 && !(Uraw > 0.0))
+        pp_flag(status, PP_FLAG_DEGENERATE);
+    for (int q = threadIdx.x; q < 4 * d.M; q += blockDim.x) {
+        double2 v = cf[q];
+        cf[q] = make_double2(s * v.x, s * v.y);
+    }
+}
+
+__global__ void samples_batch_kernel(const double2 *__restrict__ coef, const SynthCand *__restrict__ sc,
+                                     int ld, double *__restrict__ A)
+{
+    extern __shared__ double2 scf[];
+    const int c = blockIdx.y, l = blockIdx.z;
+    const SynthCand d = sc[c];
+    const int nsamp = 2 * d.n_steps + 1;
+    if (blockIdx.x * blockDim.x >= nsamp)
+        return;  // the whole block is past this candidate's samples
+    const double2 *cf = coef + d.coef_off + (size_t)l * 2 * d.M;
+    for (int q = threadIdx.x; q < 2 * d.M; q += blockDim.x)
+        scf[q] = cf[q];
+    __syncthreads();
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nsamp)
+        return;
+    const int M = d.M;
+    const long long two_n = 2ll * d.n_steps;
+    double zs, zc, js, jc;
+    sincospi((double)(k % two_n) / (double)d.n_steps, &zs, &zc);
+    sincospi((double)(((long long)k * d.j0) % two_n) / (double)d.n_steps, &js, &jc);
+    double dr = 0.0, di = 0.0, d0i = 0.0;
+    for (int m = M - 1; m >= 0; --m) {
+        const double2 D = scf[M + m];
+        const double tr = dr * zc - di * zs + D.x;
+        di = dr * zs + di * zc + D.y;
+        dr = tr;
+        d0i += D.y;
+    }
+    const double Di = dr * js + di * jc;
+    A[((size_t)c * 2 + l) * ld + k] = -(Di - d0i);
+}
+
 }  // namespace
 
 namespace pp {
+
+// Device descriptors for a batch of pulse lengths (pp_batch): built once on the host.
+int synth_batch_prepare(int ncand, const pp_field_spec *specs, void **d_desc, void **d_coef,
+                        int *max_M)
+{
+    std::vector<SynthCand> h(ncand);
+    long long off = 0;
+    int mm = 0;
+    for (int c = 0; c < ncand; ++c) {
+        const double dw = 2.0 * M_PI / specs[c].T;
+        int j0 = (int)ceil(specs[c].w_min / dw - 1e-12);
+        if (j0 < 1)
+            j0 = 1;
+        const int j1 = (int)floor(specs[c].w_max / dw + 1e-12);
+        h[c].T = specs[c].T;
+        h[c].n_steps = specs[c].n_steps;
+        h[c].j0 = j0;
+        h[c].M = j1 - j0 + 1;
+        h[c].coef_off = off;
+        off += 4ll * h[c].M;
+        mm = h[c].M > mm ? h[c].M : mm;
+    }
+    cudaError_t e = cudaMalloc(d_desc, sizeof(SynthCand) * (size_t)ncand);
+    if (e == cudaSuccess)
+        e = cudaMalloc(d_coef, sizeof(double2) * (size_t)(off > 0 ? off : 1));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(*d_desc, h.data(), sizeof(SynthCand) * (size_t)ncand, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "batch synthesis descriptors");
+    *max_M = mm;
+    return PP_OK;
+}
+
+int launch_synth_batch(const double *params, int ncand, const pp_field_spec *spec0, const void *d_desc,
+                       void *d_coef, int max_M, int max_nsamp, int ld, double *A, cudaStream_t stream)
+{
+    unsigned int *status = status_word();
+    if (!status)
+        return fail(PP_ERR_CUDA, "status word unavailable");
+    spectrum_batch_kernel<<<ncand, 128, 0, stream>>>(params, spec0->K, spec0->order, spec0->w_min,
+                                                     spec0->w_max, spec0->fluence,
+                                                     (const SynthCand *)d_desc, (double2 *)d_coef,
+                                                     status);
+    dim3 g((max_nsamp + 255) / 256, ncand, 2);
+    samples_batch_kernel<<<g, 256, 2 * max_M * sizeof(double2), stream>>>(
+        (const double2 *)d_coef, (const SynthCand *)d_desc, ld, A);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return cuda_fail(e, "batch synthesis launch");
+    return PP_OK;
+}
 
 int launch_synth_field(const double *params, int ncand, const pp_field_spec *spec, double *A, int ld,
                        double *E, double *scale, cudaStream_t stream)

@@ -70,6 +70,18 @@ int launch_de_propose(const double *pop, int NP, int D, const double *lo, const 
                       double *trial, cudaStream_t stream);
 int launch_de_select(double *pop, double *fit, const double *trial, const double *trial_fit,
                      int NP, int D, cudaStream_t stream);
+// DE with a device-resident generation counter (captured loops, pp_batch).
+int launch_de_propose_devgen(const double *pop, int NP, int D, const double *lo, const double *hi,
+                             const uint8_t *periodic, double F, double CR, uint64_t seed,
+                             const unsigned long long *gen_dev, double *trial, cudaStream_t stream);
+int launch_de_advance(unsigned long long *gen_dev, cudaStream_t stream);
+int launch_de_set_generation(unsigned long long *gen_dev, uint64_t v, cudaStream_t stream);
+
+// Batch synthesis (pp_field.cu): per-candidate pulse lengths.
+int synth_batch_prepare(int ncand, const pp_field_spec *specs, void **d_desc, void **d_coef,
+                        int *max_M);
+int launch_synth_batch(const double *params, int ncand, const pp_field_spec *spec0, const void *d_desc,
+                       void *d_coef, int max_M, int max_nsamp, int ld, double *A, cudaStream_t stream);
 
 }  // namespace pp
 
