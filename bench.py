@@ -61,6 +61,9 @@ def parse():
                     help="modes of one candidate in the CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="de-batch", choices=["de-batch", "uneven"],
+                    help="de-batch: the 64-candidate DE generation (default); uneven: 128 slots "
+                         "of uneven length and grid, generations in one CUDA graph")
     ap.add_argument("--ncand", type=int, default=CFG["NP"],
                     help="population size (smaller values only for profiling runs)")
     return ap.parse_args()
@@ -214,6 +217,101 @@ def reference_main(args):
     return 0
 
 
+# ----------------------------------------------------------------------------- uneven batch
+
+
+def uneven_main(args):
+    """128 slots of uneven length and grid; each timed step is one DE generation, all
+    K timed generations in one CUDA graph launch (pp_batch_de_run)."""
+    import torch
+    import paper_1704_08919_gb300 as pp
+    U = inputs.UNEVEN_BATCH
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    pp.lib()
+    stream = torch.cuda.current_stream()
+    pop_seed, seed = rank_seeds(rank)
+    steps = inputs.uneven_steps(U, pop_seed)
+    specs = inputs.uneven_specs(U, steps)
+    pop = torch.tensor(inputs.random_population(U["NP"], U["K"], seed=pop_seed), device=dev)
+    peaks = []
+    for c, sp in enumerate(specs):
+        _, E, _ = pp.synth_field(pop[c:c + 1].contiguous(), sp, want_E=True)
+        peaks.append(torch.sqrt(E[0, 0] ** 2 + E[0, 1] ** 2).max().item())
+    grids = inputs.grids_by_rank(U, peaks)
+    b = pp.Batch(specs, grids, U["dt"], precision=args.precision, scheme=args.scheme)
+    lo, hi, per = inputs.param_bounds(U["K"])
+    lo_t, hi_t, per_t = (torch.tensor(x, device=dev) for x in (lo, hi, per))
+    A = b.synth(pop)
+    tuned = None
+    if not args.no_tune:
+        chosen, cfg_ms = b.tune(A)
+        tuned = {"chosen": pp.launch_configs()[chosen], "ms": [round(x, 2) for x in cfg_ms]}
+    fit, _ = b.pair_number(A)
+    b.set_generation(0)
+    G = args.steps
+    b.de_run(pop, fit, lo_t, hi_t, per_t, U["F"], U["CR"], seed, G)  # capture + warm-up
+    torch.cuda.synchronize()
+    if pp.sync_status() != pp.PP_OK:
+        raise RuntimeError("warm-up failed")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist is not None:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    e0.record(stream)
+    b.de_run(pop, fit, lo_t, hi_t, per_t, U["F"], U["CR"], seed, G)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if pp.sync_status() != pp.PP_OK:
+        raise RuntimeError("device status after the timed region")
+    total_ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+    modes = np.array([g["nx"] * g["ny"] * g["nz"] for g in grids], dtype=np.float64)
+    mode_steps = float(np.sum(modes * steps)) * G
+    # accuracy: 4 slots of the final population, this path against FP64 RK4
+    idx = list(range(4))
+    sub_specs = [specs[i] for i in idx]
+    sub_grids = [grids[i] for i in idx]
+    bf = pp.Batch(sub_specs, sub_grids, U["dt"], precision=args.precision, scheme=args.scheme)
+    b64 = pp.Batch(sub_specs, sub_grids, U["dt"], precision="fp64", scheme="rk4")
+    As = bf.synth(pop[idx].contiguous())
+    Nf, _ = bf.pair_number(As)
+    N64, _ = b64.pair_number(As)
+    pp.sync_status()
+    rel_err = (Nf / N64 - 1).abs().max().item()
+    if rel_err > 1e-4:
+        raise RuntimeError("N error %.3e vs FP64 RK4 exceeds 1e-4" % rel_err)
+    if rank == 0:
+        cand = throughput(ws, U["NP"], G, total_ms)
+        print(json.dumps({
+            "metric": "candidate pulses scored/s (uneven batch, rel. N err <= 1e-4 vs FP64 oracle)",
+            "value": cand, "unit": "candidates/s", "n_gpus": ws, "steps": G, "warmup": G,
+            "ms_per_step": total_ms / G, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
+            "scheme": args.scheme, "data": "synthetic (seeded B-spline pulses, uniform in bounds)",
+            "config": {"workload": U["name"], "NP": U["NP"], "precision": args.precision,
+                       "steps_per_slot": [int(steps.min()), int(steps.max())],
+                       "modes_per_slot": [int(modes.min()), int(modes.max())],
+                       "graph": "%d generations per CUDA graph launch" % G,
+                       "l2": "not flushed between generations inside the graph (ALU-bound kernel)"},
+            "mode_steps_per_s": ws * mode_steps / (total_ms / 1000.0),
+            "n_rel_err_vs_fp64_rk4_max": rel_err, "launch_tuning": tuned, "clocks": clk,
+            "gpu_launches": 8 * G}), flush=True)
+    for x in (bf, b64, b):
+        x.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
 # ----------------------------------------------------------------------------- GPU leg
 
 
@@ -221,6 +319,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return reference_main(args)
+    if args.workload == "uneven":
+        return uneven_main(args)
     import torch
     import paper_1704_08919_gb300 as pp
 

@@ -12,6 +12,11 @@ windows, Sec. V, scaled to the configurations below):
   E(t) = E0 exp(-t^2/tau^2) (cos w t, sin w t, 0), E0 = 0.1, w = 0.7, tau = 10,
   t in [-40, 40], dt = 0.02 (4000 RK4 steps), A(-40) = 0; grid 32 x 32 x 16 on
   [-1.5, 1.5]^2 x [0, 1.5] with the p_z mirror.
+* ``UNEVEN_BATCH``: a population of 128 slots with pulse lengths T = 0.02 n,
+  n uniform in [2500, 20000] (one RK4-grid step count per slot), K = 8 cubic
+  B-splines on [0, 2], fluence 2.0; momentum grids of side 32, 48, 64, 80 or 96
+  (n_z = side / 2) over [-2, 2]^2 x [0, 2], mirrored, by the quintile of the
+  slot's initial peak field; DE with F = 0.8, CR = 0.9.
 * ``DE_BATCH``: a population of 64 B-spline pulses (K = 8 control points per
   amplitude and phase per polarisation, cubic splines on [0, 2], T = 200,
   8192 RK4 steps, fluence 2.0) on a 64 x 64 x 32 grid over [-2, 2]^2 x [0, 2]
@@ -33,6 +38,36 @@ DE_BATCH = dict(
     F=0.8, CR=0.9,
     grid=dict(nx=64, ny=64, nz=32, x0=-2.0, x1=2.0, y0=-2.0, y1=2.0, z0=0.0, z1=2.0, mirror_z=1),
 )
+
+
+UNEVEN_BATCH = dict(
+    name="uneven-batch 128 slots T~U[50,400] dt=0.02 grids 32..96 by peak-field quintile",
+    NP=128, K=8, order=4, w_min=0.0, w_max=2.0, fluence=2.0, dt=0.02, n_min=2500, n_max=20000,
+    sides=(32, 48, 64, 80, 96), ext=2.0, F=0.8, CR=0.9,
+)
+
+
+def uneven_steps(cfg, seed):
+    """Step count of every slot (uniform integers in [n_min, n_max])."""
+    rng = np.random.default_rng(seed)
+    return rng.integers(cfg["n_min"], cfg["n_max"] + 1, size=cfg["NP"])
+
+
+def uneven_specs(cfg, steps):
+    return [dict(K=cfg["K"], order=cfg["order"], w_min=cfg["w_min"], w_max=cfg["w_max"],
+                 T=float(n) * cfg["dt"], fluence=cfg["fluence"], n_steps=int(n)) for n in steps]
+
+
+def grids_by_rank(cfg, peaks):
+    """Slot grids by the quintile of each slot's peak field (weakest fields get the
+    smallest grid): sides[q] x sides[q] x sides[q]/2 for quintile q."""
+    peaks = np.asarray(peaks)
+    order = np.argsort(peaks, kind="stable")
+    q = np.empty(len(peaks), dtype=int)
+    q[order] = (np.arange(len(peaks)) * len(cfg["sides"])) // len(peaks)
+    e = cfg["ext"]
+    return [dict(nx=cfg["sides"][k], ny=cfg["sides"][k], nz=cfg["sides"][k] // 2, x0=-e, x1=e,
+                 y0=-e, y1=e, z0=0.0, z1=e, mirror_z=1) for k in q]
 
 
 def field_spec(cfg):
