@@ -206,6 +206,53 @@ int pp_batch_de_run(pp_batch *batch, double *pop, double *fit, const double *lo,
                     const uint8_t *periodic, double F, double CR, uint64_t seed, int32_t generations,
                     void *stream);
 
+/* ---- BF16 tensor-core GEMM (tcgen05, FP32 accumulation in tensor memory): the
+ * dense contractions of the surrogate network.  Not in the paper.
+ * Operands are BF16 matrices in the packed tile layout: 128-row x 64-column
+ * tiles, each a contiguous 16 KiB block of 8 x 8 core matrices (K-major, no
+ * swizzle), rows padded to 128 and columns to 64 with zeros;
+ * pp_packed_bf16_bytes(rows, cols) is the size of a packed matrix.
+ * pp_pack_bf16 packs the FP32 matrix X (rows x cols, row-major with leading
+ * dimension ldx; with transpose = 1, X is stored cols x rows and packed
+ * transposed) into P (device), rounding to nearest.
+ * pp_gemm_bf16 computes D[M][N] = A[M][K] . B[N][K]^T into FP32 D (device,
+ * row-major, leading dimension ldd) from packed A (M x K) and B (N x K):
+ * M % 128 == 0, 16 <= N <= 256 with N % 16 == 0, K % 64 == 0. */
+size_t pp_packed_bf16_bytes(int32_t rows, int32_t cols);
+int pp_pack_bf16(const float *X, int32_t rows, int32_t cols, int32_t ldx, int32_t transpose, void *P,
+                 void *stream);
+int pp_gemm_bf16(const void *A, const void *B, float *D, int32_t M, int32_t N, int32_t K, int32_t ldd,
+                 void *stream);
+
+/* ---- Surrogate network for screened DE (not in the paper): an MLP
+ * d_in -> H -> H -> H -> 1 with GELU activations predicting a normalised log10 N
+ * from normalised pulse parameters, trained on the GPU by its own forward and
+ * backward kernels (hidden layers on the tensor cores via pp_gemm_bf16; FP32
+ * master weights, biases, activations and Adam).  Parameters are one FP32 vector
+ * [W1 (H x d_in), b1, W2 (H x H), b2, W3 (H x H), b3, w4 (H), b4].
+ *  pp_mlp_create       allocates everything for batches up to max_batch.
+ *  pp_mlp_set_params / pp_mlp_get_params  copy the parameter vector (host or device
+ *                      pointer); set_params also resets Adam.
+ *  pp_mlp_forward      y (device [B]) for inputs X (device FP32 [B][d_in]).
+ *  pp_mlp_loss_grad    loss = mean (y - t)^2 (device float, or NULL) and its
+ *                      gradient (device FP32 [n_params], or NULL).
+ *  pp_mlp_train_step   one Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on that loss.
+ *  pp_mlp_features     FP64 parameter vectors (device [B][D]) -> network inputs
+ *                      (x - lo) / (hi - lo) - 1/2 as FP32 (device [B][D]). */
+typedef struct pp_mlp pp_mlp;
+int pp_mlp_create(int32_t d_in, int32_t hidden, int32_t max_batch, pp_mlp **out);
+void pp_mlp_destroy(pp_mlp *mlp);
+int64_t pp_mlp_num_params(const pp_mlp *mlp);
+int pp_mlp_set_params(pp_mlp *mlp, const float *params, void *stream);
+int pp_mlp_get_params(const pp_mlp *mlp, float *params, void *stream);
+int pp_mlp_forward(pp_mlp *mlp, const float *X, int32_t B, float *y, void *stream);
+int pp_mlp_loss_grad(pp_mlp *mlp, const float *X, const float *t, int32_t B, float *loss, float *grad,
+                     void *stream);
+int pp_mlp_train_step(pp_mlp *mlp, const float *X, const float *t, int32_t B, float lr, float *loss,
+                      void *stream);
+int pp_mlp_features(const double *params, int32_t B, int32_t D, const double *lo, const double *hi,
+                    float *X, void *stream);
+
 /* pp_pair_number without any device allocation.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory --
  * for example a host application whose device memory is fully reserved by its

@@ -43,7 +43,10 @@ EXPORTS = ("pp_synth_field", "pp_pair_number", "pp_de_propose", "pp_de_select", 
            "pp_num_launch_configs", "pp_launch_config", "pp_clear_tuning", "pp_pair_number_static",
            "pp_static_scratch_bytes", "pp_batch_create", "pp_batch_destroy", "pp_batch_info",
            "pp_batch_synth", "pp_batch_pair_number", "pp_batch_tune", "pp_batch_set_generation",
-           "pp_batch_de_step", "pp_batch_de_run")
+           "pp_batch_de_step", "pp_batch_de_run", "pp_packed_bf16_bytes", "pp_pack_bf16",
+           "pp_gemm_bf16", "pp_mlp_create", "pp_mlp_destroy", "pp_mlp_num_params",
+           "pp_mlp_set_params", "pp_mlp_get_params", "pp_mlp_forward", "pp_mlp_loss_grad",
+           "pp_mlp_train_step", "pp_mlp_features")
 
 
 class PPError(RuntimeError):
@@ -111,6 +114,21 @@ def lib():
                                     ctypes.POINTER(ctypes.c_float), _vp]
         L.pp_batch_set_generation.argtypes = [_vp, _u64, _vp]
         L.pp_batch_de_step.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _d, _d, _u64, _vp]
+        L.pp_packed_bf16_bytes.argtypes = [_i32, _i32]
+        L.pp_packed_bf16_bytes.restype = ctypes.c_size_t
+        L.pp_pack_bf16.argtypes = [_vp, _i32, _i32, _i32, _i32, _vp, _vp]
+        L.pp_gemm_bf16.argtypes = [_vp, _vp, _vp, _i32, _i32, _i32, _i32, _vp]
+        L.pp_mlp_create.argtypes = [_i32, _i32, _i32, ctypes.POINTER(_vp)]
+        L.pp_mlp_destroy.argtypes = [_vp]
+        L.pp_mlp_destroy.restype = None
+        L.pp_mlp_num_params.argtypes = [_vp]
+        L.pp_mlp_num_params.restype = ctypes.c_int64
+        L.pp_mlp_set_params.argtypes = [_vp, _vp, _vp]
+        L.pp_mlp_get_params.argtypes = [_vp, _vp, _vp]
+        L.pp_mlp_forward.argtypes = [_vp, _vp, _i32, _vp, _vp]
+        L.pp_mlp_loss_grad.argtypes = [_vp, _vp, _vp, _i32, _vp, _vp, _vp]
+        L.pp_mlp_train_step.argtypes = [_vp, _vp, _vp, _i32, ctypes.c_float, _vp, _vp]
+        L.pp_mlp_features.argtypes = [_vp, _i32, _i32, _vp, _vp, _vp, _vp]
         L.pp_batch_de_run.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _d, _d, _u64, _i32, _vp]
         _lib = L
     return _lib
@@ -221,6 +239,87 @@ def launch_configs():
 
 def clear_tuning():
     lib().pp_clear_tuning()
+
+
+def pack_bf16(X, transpose=False, stream=None):
+    """pp_pack_bf16: FP32 CUDA matrix -> packed BF16 tile layout (uint8 tensor).
+    With transpose=True, X (cols x rows) is packed as its transpose (rows x cols)."""
+    import torch
+    rows, cols = (X.shape[1], X.shape[0]) if transpose else (X.shape[0], X.shape[1])
+    P = torch.empty(lib().pp_packed_bf16_bytes(rows, cols), dtype=torch.uint8, device=X.device)
+    _check(lib().pp_pack_bf16(_ptr(X), rows, cols, X.stride(0), int(transpose), _ptr(P),
+                              _stream(stream)))
+    return P, rows, cols
+
+
+def gemm_bf16(Ap, Bp, M, N, K, out=None, stream=None):
+    """pp_gemm_bf16: D[M][N] = A . B^T from packed BF16 operands (FP32 result)."""
+    import torch
+    D = out if out is not None else torch.empty((M, N), dtype=torch.float32, device=Ap.device)
+    _check(lib().pp_gemm_bf16(_ptr(Ap), _ptr(Bp), _ptr(D), M, N, K, D.stride(0), _stream(stream)))
+    return D
+
+
+class Surrogate:
+    """pp_mlp_*: the surrogate network (d_in -> H -> H -> H -> 1, GELU)."""
+
+    def __init__(self, d_in, hidden=256, max_batch=4096):
+        h = _vp()
+        _check(lib().pp_mlp_create(int(d_in), int(hidden), int(max_batch), ctypes.byref(h)))
+        self.h = h
+        self.d_in, self.hidden, self.max_batch = d_in, hidden, max_batch
+        self.nparam = lib().pp_mlp_num_params(h)
+
+    def close(self):
+        if self.h:
+            lib().pp_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params, stream=None):
+        """params: FP32 CUDA tensor [n_params]."""
+        _check(lib().pp_mlp_set_params(self.h, _ptr(params), _stream(stream)))
+
+    def get_params(self, stream=None):
+        import torch
+        out = torch.empty(self.nparam, dtype=torch.float32, device="cuda")
+        _check(lib().pp_mlp_get_params(self.h, _ptr(out), _stream(stream)))
+        return out
+
+    def forward(self, X, stream=None):
+        import torch
+        y = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+        _check(lib().pp_mlp_forward(self.h, _ptr(X), X.shape[0], _ptr(y), _stream(stream)))
+        return y
+
+    def loss_grad(self, X, t, stream=None):
+        import torch
+        loss = torch.empty(1, dtype=torch.float32, device=X.device)
+        g = torch.empty(self.nparam, dtype=torch.float32, device=X.device)
+        _check(lib().pp_mlp_loss_grad(self.h, _ptr(X), _ptr(t), X.shape[0], _ptr(loss), _ptr(g),
+                                      _stream(stream)))
+        return loss, g
+
+    def train_step(self, X, t, lr, stream=None):
+        import torch
+        loss = torch.empty(1, dtype=torch.float32, device=X.device)
+        _check(lib().pp_mlp_train_step(self.h, _ptr(X), _ptr(t), X.shape[0], float(lr), _ptr(loss),
+                                       _stream(stream)))
+        return loss
+
+
+def mlp_features(params, lo, hi, stream=None):
+    """pp_mlp_features: FP64 parameter vectors -> normalised FP32 network inputs."""
+    import torch
+    B, D = params.shape
+    X = torch.empty((B, D), dtype=torch.float32, device=params.device)
+    _check(lib().pp_mlp_features(_ptr(params), B, D, _ptr(lo), _ptr(hi), _ptr(X), _stream(stream)))
+    return X
 
 
 class Batch:

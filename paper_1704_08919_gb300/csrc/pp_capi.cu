@@ -378,6 +378,40 @@ int pp_tune_pair_number(const double *A, int32_t ncand, int32_t ld, const int32_
 
 int pp_num_launch_configs(void) { return num_launch_configs(); }
 
+size_t pp_packed_bf16_bytes(int32_t rows, int32_t cols)
+{
+    if (rows < 1 || cols < 1)
+        return 0;
+    const size_t r = ((size_t)rows + 127) / 128 * 128, c = ((size_t)cols + 63) / 64 * 64;
+    return r * c * 2;
+}
+
+int pp_pack_bf16(const float *X, int32_t rows, int32_t cols, int32_t ldx, int32_t transpose, void *P,
+                 void *stream)
+{
+    clear_error();
+    if (!X || !P || rows < 1 || cols < 1)
+        return fail(PP_ERR_INVALID_ARG, "X and P must not be NULL; rows, cols >= 1");
+    const int src_cols = transpose ? rows : cols;
+    if (ldx < src_cols)
+        return fail(PP_ERR_INVALID_ARG, "ldx smaller than the stored row length");
+    const int rp = (rows + 127) / 128 * 128, cp = (cols + 63) / 64 * 64;
+    return launch_pack_bf16(X, rows, cols, ldx, transpose ? 1 : 0, P, rp, cp, (cudaStream_t)stream);
+}
+
+int pp_gemm_bf16(const void *A, const void *B, float *D, int32_t M, int32_t N, int32_t K, int32_t ldd,
+                 void *stream)
+{
+    clear_error();
+    if (!A || !B || !D)
+        return fail(PP_ERR_INVALID_ARG, "A, B and D must not be NULL");
+    if (M < 128 || M % 128 || N < 16 || N > 256 || N % 16 || K < 64 || K % 64 || ldd < N)
+        return fail(PP_ERR_INVALID_ARG, "need M %% 128 == 0, 16 <= N <= 256 with N %% 16 == 0, "
+                                        "K %% 64 == 0 and ldd >= N (got M=%d N=%d K=%d ldd=%d)",
+                    M, N, K, ldd);
+    return launch_gemm_bf16(A, B, D, M, N, K, ldd, (cudaStream_t)stream);
+}
+
 int pp_launch_config(int32_t k, int32_t *threads_per_cta, int32_t *tile_bytes)
 {
     clear_error();

@@ -77,6 +77,12 @@ int launch_de_propose_devgen(const double *pop, int NP, int D, const double *lo,
 int launch_de_advance(unsigned long long *gen_dev, cudaStream_t stream);
 int launch_de_set_generation(unsigned long long *gen_dev, uint64_t v, cudaStream_t stream);
 
+// BF16 tensor-core GEMM and operand packing (pp_gemm.cu).
+int launch_gemm_bf16(const void *A, const void *B, float *D, int M, int N, int K, int ldd,
+                     cudaStream_t stream);
+int launch_pack_bf16(const float *X, int rows, int cols, int ldx, int trans, void *P, int rows_pad,
+                     int cols_pad, cudaStream_t stream);
+
 // Batch synthesis (pp_field.cu): per-candidate pulse lengths.
 int synth_batch_prepare(int ncand, const pp_field_spec *specs, void **d_desc, void **d_coef,
                         int *max_M);

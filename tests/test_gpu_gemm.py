@@ -1,0 +1,64 @@
+"""The BF16 tensor-core GEMM (tcgen05, FP32 accumulation) against an FP64
+product of the same BF16-rounded operands."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1704_08919_gb300 import build
+    build.build()
+    import paper_1704_08919_gb300 as pp
+    pp.lib()
+    assert pp.sync_status() == pp.PP_OK
+    return pp
+
+
+def bf16(x):
+    return x.to(torch.bfloat16).to(torch.float64)
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 16, 64), (128, 256, 64), (256, 256, 256), (384, 32, 128),
+                                   (128, 48, 1024), (512, 256, 32), (256, 1, 256)])
+def test_gemm_matches_fp64_product_of_bf16_operands(pp, M, N, K):
+    g = torch.Generator(device="cpu").manual_seed(M * 7 + N * 3 + K)
+    A = torch.randn(M, K, generator=g).cuda()
+    B = torch.randn(N, K, generator=g).cuda()
+    Np = max(16, (N + 15) // 16 * 16)
+    Kp = (K + 63) // 64 * 64
+    Ap, _, _ = pp.pack_bf16(A)
+    Bp, _, _ = pp.pack_bf16(B)
+    D = pp.gemm_bf16(Ap, Bp, M, Np, Kp)
+    assert pp.sync_status() == pp.PP_OK
+    ref = (bf16(A.cpu()) @ bf16(B.cpu()).T).numpy()
+    got = D[:, :N].cpu().double().numpy()
+    scale = np.sqrt(K) * 1.0
+    assert np.abs(got - ref).max() < 2e-5 * scale * np.abs(ref).max() / np.sqrt(K) + 1e-5 * scale
+    assert np.abs(D[:, N:].cpu().numpy()).max() == 0.0 if Np > N else True
+
+
+def test_gemm_transposed_packing(pp):
+    g = torch.Generator(device="cpu").manual_seed(1)
+    X = torch.randn(64, 256, generator=g).cuda()  # stored as (K rows) x (M cols): pack X^T
+    W = torch.randn(32, 64, generator=g).cuda()
+    Xp, rows, cols = pp.pack_bf16(X, transpose=True)  # 256 x 64
+    assert (rows, cols) == (256, 64)
+    Wp, _, _ = pp.pack_bf16(W)
+    D = pp.gemm_bf16(Xp, Wp, 256, 32, 64)
+    ref = (bf16(X.cpu()).T @ bf16(W.cpu()).T).numpy()
+    assert np.abs(D.cpu().double().numpy() - ref).max() < 1e-4 * np.abs(ref).max()
+
+
+def test_gemm_rejects_bad_shapes(pp):
+    A = torch.zeros(16384, dtype=torch.uint8, device="cuda")
+    with pytest.raises(pp.PPError):
+        pp.gemm_bf16(A, A, 100, 16, 64)
+    with pytest.raises(pp.PPError):
+        pp.gemm_bf16(A, A, 128, 24, 64)
+    with pytest.raises(pp.PPError):
+        pp.gemm_bf16(A, A, 128, 16, 48)
