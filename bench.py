@@ -61,9 +61,17 @@ def parse():
                     help="modes of one candidate in the CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="de-batch", choices=["de-batch", "uneven"],
+    ap.add_argument("--workload", default="de-batch", choices=["de-batch", "uneven", "surrogate"],
                     help="de-batch: the 64-candidate DE generation (default); uneven: 128 slots "
-                         "of uneven length and grid, generations in one CUDA graph")
+                         "of uneven length and grid, generations in one CUDA graph; surrogate: "
+                         "exact calls of surrogate-screened DE against plain DE")
+    ap.add_argument("--train", type=int, default=None, help="surrogate: training pulses")
+    ap.add_argument("--generations", type=int, default=None, help="surrogate: DE generations")
+    ap.add_argument("--seeds", type=int, default=3, help="surrogate: DE runs (seeds) per form")
+    ap.add_argument("--screen", default="individual", choices=["individual", "global"],
+                    help="surrogate: screening mode reported as the value")
+    ap.add_argument("--online", type=int, default=0,
+                    help="surrogate: also run a screened DE refitted every N generations (0: off)")
     ap.add_argument("--ncand", type=int, default=CFG["NP"],
                     help="population size (smaller values only for profiling runs)")
     return ap.parse_args()
@@ -312,6 +320,97 @@ def uneven_main(args):
     return 0
 
 
+# ----------------------------------------------------------------------------- surrogate
+
+
+def surrogate_main(args):
+    """Surrogate-screened DE against plain DE on the de-batch solver settings: the
+    network is trained on exact evaluations of random pulses, then both forms run
+    from the same initial population; reports exact solver calls and wall-clock
+    time to reach plain DE's best N, and the network's held-out error."""
+    import torch
+    import paper_1704_08919_gb300 as pp
+    from paper_1704_08919_gb300 import screening as scr
+    S = inputs.SURROGATE_DE
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    pp.lib()
+    spec, grid = inputs.field_spec(CFG), CFG["grid"]
+    K, D, NP = CFG["K"], 4 * CFG["K"], S["NP"]
+    n_train = args.train or S["n_train"]
+    G = args.generations or S["generations"]
+    prec, sch = args.precision, args.scheme
+    lo, hi, per = (torch.tensor(x, device="cuda") for x in inputs.param_bounds(K))
+    clocks = ClockSampler(local)
+    clocks.start()
+    P_tr, N_tr, t_gen = scr.score_random(pp, n_train, spec, grid, S["train_seed"], precision=prec,
+                                          scheme=sch)
+    P_te, N_te, _ = scr.score_random(pp, S["n_heldout"], spec, grid, S["heldout_seed"],
+                                     precision=prec, scheme=sch)
+    lt = scr.LogTarget(N_tr)
+    net = pp.Surrogate(D, S["hidden"], max_batch=max(S["R"] * NP, S["batch"], 1024))
+    net.init(1)
+    X_tr = pp.mlp_features(P_tr, lo, hi)
+    t_tr = lt.targets(pp, N_tr)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = net.fit(X_tr, t_tr, S["batch"], S["epochs"], S["lr0"], S["lr1"])
+    torch.cuda.synchronize()
+    t_fit = time.perf_counter() - t0
+    held = scr.held_out_error(pp, net, lt, P_te, N_te, lo, hi)
+    de = dict(F=CFG["F"], CR=CFG["CR"], precision=prec, scheme=sch)
+    modes = ["individual", "global"]
+    per_seed = []
+    for s_i in range(args.seeds):
+        pop0 = torch.tensor(inputs.random_population(NP, K, seed=S["pop_seed"] + s_i), device="cuda")
+        A0, _, _ = pp.synth_field(pop0, spec)
+        fit0, _ = pp.pair_number(A0, spec["T"] / spec["n_steps"], grid, precision=prec, scheme=sch)
+        seed = S["de_seed"] + s_i
+        plain = scr.run_de(pp, pop0, fit0, spec, grid, G, seed, **de)
+        target = plain["best"][-1]
+        pc = scr.calls_to_reach(plain, target)
+        rec = {"seed": seed, "plain": {"calls_to_best": pc, "best_N": target,
+                                       "seconds_total": plain["seconds"],
+                                       "seconds_to_best": plain["seconds"] * (pc // NP - 1) / G}}
+        runs = {m: scr.run_de(pp, pop0, fit0, spec, grid, G, seed, net=net, R=S["R"], lt=lt,
+                              mode=m, **de) for m in modes}
+        if args.online:
+            net_o = pp.Surrogate(D, S["hidden"], max_batch=net.max_batch)
+            net_o.set_params(net.get_params())
+            runs["individual_online"] = scr.run_de(pp, pop0, fit0, spec, grid, G, seed, net=net_o,
+                                                   R=S["R"], lt=lt, online=(args.online, 4, 128, 2e-4),
+                                                   **de)
+        for m, r in runs.items():
+            c = scr.calls_to_reach(r, target)
+            rec[m] = {"calls_to_plain_best": c, "best_N": r["best"][-1],
+                      "seconds_total": r["seconds"],
+                      "seconds_to_plain_best": (r["seconds"] * (c // NP - 1) / G if c else None),
+                      "gain_in_exact_calls": (pc / c) if c else 0.0}
+        per_seed.append(rec)
+    clk = clocks.stop()
+    if pp.sync_status() != pp.PP_OK:
+        raise RuntimeError("device status after the surrogate run")
+    gains = {m: [r[m]["gain_in_exact_calls"] for r in per_seed] for m in per_seed[0] if m not in ("seed", "plain")}
+    med = {m: statistics.median(v) for m, v in gains.items()}
+    print(json.dumps({
+        "metric": "exact solver calls to reach plain-DE best N, plain / surrogate-screened "
+                  "(median over seeds, %s screening)" % args.screen,
+        "value": med[args.screen], "unit": "x", "n_gpus": 1, "steps": G, "warmup": 0,
+        "higher_is_better": True, "scaling": "none", "vs_baseline": None,
+        "dtype": "f32" if prec != "fp64" else "f64", "data": "synthetic (seeded B-spline pulses)",
+        "config": {"workload": S["name"], "solver": workload_config(prec, NP, sch),
+                   "R": S["R"], "n_train": n_train, "n_heldout": S["n_heldout"],
+                   "epochs": S["epochs"], "batch": S["batch"], "generations": G,
+                   "seeds": args.seeds},
+        "gain_median": med, "gains": gains,
+        "training": {"pulses": n_train, "seconds_generate": t_gen, "seconds_fit": t_fit,
+                     "final_epoch_loss": float(losses[-1].item())},
+        "heldout": held, "per_seed": per_seed, "clocks": clk}), flush=True)
+    return 0
+
+
 # ----------------------------------------------------------------------------- GPU leg
 
 
@@ -321,6 +420,8 @@ def main():
         return reference_main(args)
     if args.workload == "uneven":
         return uneven_main(args)
+    if args.workload == "surrogate":
+        return surrogate_main(args)
     import torch
     import paper_1704_08919_gb300 as pp
 

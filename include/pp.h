@@ -244,6 +244,12 @@ int pp_mlp_create(int32_t d_in, int32_t hidden, int32_t max_batch, pp_mlp **out)
 void pp_mlp_destroy(pp_mlp *mlp);
 int64_t pp_mlp_num_params(const pp_mlp *mlp);
 int pp_mlp_set_params(pp_mlp *mlp, const float *params, void *stream);
+
+/* He initialisation on the device: every weight of a block with fan-in f is
+ * sqrt(2/f) z, z a standard normal from the Box-Muller transform of SplitMix64
+ * outputs 2i and 2i+1 (i = the parameter's index, generator seeded with seed);
+ * biases are zero.  Resets the Adam moments and step count. */
+int pp_mlp_init(pp_mlp *mlp, uint64_t seed, void *stream);
 int pp_mlp_get_params(const pp_mlp *mlp, float *params, void *stream);
 int pp_mlp_forward(pp_mlp *mlp, const float *X, int32_t B, float *y, void *stream);
 int pp_mlp_loss_grad(pp_mlp *mlp, const float *X, const float *t, int32_t B, float *loss, float *grad,
@@ -252,6 +258,50 @@ int pp_mlp_train_step(pp_mlp *mlp, const float *X, const float *t, int32_t B, fl
                       void *stream);
 int pp_mlp_features(const double *params, int32_t B, int32_t D, const double *lo, const double *hi,
                     float *X, void *stream);
+
+/* Mini-batch training: `epochs` passes over the n rows of X (device FP32
+ * [n][d_in]) and t (device FP32 [n]) in order, in slices of `batch` rows (the
+ * last one ragged), one pp_mlp_train_step per slice, the learning rate
+ * following a cosine from lr0 (first step) to lr1 (last step).  epoch_loss
+ * (device FP32 [epochs], or NULL) receives the loss of each epoch's last slice.
+ * Rows are not shuffled: pass data in random order. */
+int pp_mlp_fit(pp_mlp *h, const float *X, const float *t, int32_t n, int32_t batch, int32_t epochs,
+               float lr0, float lr1, float *epoch_loss, void *stream);
+
+/* Training targets from pair numbers: t[i] = (log10(max(N[i], floor)) - shift)
+ * / scale for device FP64 N[n] into device FP32 t[n]; floor > 0, scale != 0. */
+int pp_mlp_log_targets(const double *N, int32_t n, double floor_value, double shift, double scale, float *t,
+                       void *stream);
+
+/* Screening modes of pp_de_screened_step. */
+enum pp_screen_mode {
+    PP_SCREEN_PER_INDIVIDUAL = 0, /* each individual's best-predicted proposal */
+    PP_SCREEN_GLOBAL = 1          /* the NP best-predicted of all R NP proposals */
+};
+
+/* Surrogate-screened DE generation (an extension; the paper's DE scores every
+ * trial exactly).  For each individual R DE/rand/1/bin trials are proposed
+ * (trial r of generation g uses the counter-RNG key of generation R g + r in
+ * pp_de_propose's scheme; proposal k = r NP + i belongs to individual i), the
+ * network predicts all R NP of them and NP are kept for exact scoring
+ * (pp_synth_field, pp_pair_number), so a generation costs NP exact evaluations
+ * as plain DE does:
+ *  PP_SCREEN_PER_INDIVIDUAL: row i is individual i's best-predicted proposal
+ *    (first maximum); selection as pp_de_select.  With R = 1 this is pp_de_step.
+ *  PP_SCREEN_GLOBAL: rows are the NP best-predicted proposals of all R NP in
+ *    order (ties to the lower k, NaN predictions last); individual i takes the
+ *    exactly best of its kept proposals, if any, when that N >= its fitness.
+ * The exact pair number alone decides selection.  trial_out (device [NP][4K]),
+ * trial_fit_out (device [NP]), pred_out (device FP32 [R NP]) and kept_out
+ * (device int32 [NP], the k of each row) receive the scored trials, their pair
+ * numbers, all predictions and the kept indices; each may be NULL.  Needs
+ * 4 <= NP <= 65535, 1 <= R <= 64, R NP at most the network's max_batch (rounded
+ * up to 128) and a network input size of 4K. */
+int pp_de_screened_step(double *pop, double *fit, int32_t NP, const pp_field_spec *spec,
+                        const pp_grid *grid, int32_t precision, int32_t scheme, const double *lo,
+                        const double *hi, const uint8_t *periodic, double F, double CR, uint64_t seed,
+                        uint64_t generation, int32_t R, int32_t mode, pp_mlp *mlp, double *trial_out,
+                        double *trial_fit_out, float *pred_out, int32_t *kept_out, void *stream);
 
 /* pp_pair_number without any device allocation.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory --

@@ -46,7 +46,8 @@ EXPORTS = ("pp_synth_field", "pp_pair_number", "pp_de_propose", "pp_de_select", 
            "pp_batch_de_step", "pp_batch_de_run", "pp_packed_bf16_bytes", "pp_pack_bf16",
            "pp_gemm_bf16", "pp_mlp_create", "pp_mlp_destroy", "pp_mlp_num_params",
            "pp_mlp_set_params", "pp_mlp_get_params", "pp_mlp_forward", "pp_mlp_loss_grad",
-           "pp_mlp_train_step", "pp_mlp_features")
+           "pp_mlp_train_step", "pp_mlp_features", "pp_de_screened_step", "pp_mlp_fit",
+           "pp_mlp_log_targets", "pp_mlp_init")
 
 
 class PPError(RuntimeError):
@@ -129,6 +130,13 @@ def lib():
         L.pp_mlp_loss_grad.argtypes = [_vp, _vp, _vp, _i32, _vp, _vp, _vp]
         L.pp_mlp_train_step.argtypes = [_vp, _vp, _vp, _i32, ctypes.c_float, _vp, _vp]
         L.pp_mlp_features.argtypes = [_vp, _i32, _i32, _vp, _vp, _vp, _vp]
+        L.pp_de_screened_step.argtypes = [_vp, _vp, _i32, ctypes.POINTER(FieldSpec),
+                                          ctypes.POINTER(Grid), _i32, _i32, _vp, _vp, _vp, _d, _d,
+                                          _u64, _u64, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp]
+        L.pp_mlp_fit.argtypes = [_vp, _vp, _vp, _i32, _i32, _i32, ctypes.c_float, ctypes.c_float,
+                                 _vp, _vp]
+        L.pp_mlp_log_targets.argtypes = [_vp, _i32, _d, _d, _d, _vp, _vp]
+        L.pp_mlp_init.argtypes = [_vp, _u64, _vp]
         L.pp_batch_de_run.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _d, _d, _u64, _i32, _vp]
         _lib = L
     return _lib
@@ -285,6 +293,10 @@ class Surrogate:
         """params: FP32 CUDA tensor [n_params]."""
         _check(lib().pp_mlp_set_params(self.h, _ptr(params), _stream(stream)))
 
+    def init(self, seed, stream=None):
+        """pp_mlp_init: He initialisation from a counter-based generator."""
+        _check(lib().pp_mlp_init(self.h, int(seed), _stream(stream)))
+
     def get_params(self, stream=None):
         import torch
         out = torch.empty(self.nparam, dtype=torch.float32, device="cuda")
@@ -311,6 +323,39 @@ class Surrogate:
         _check(lib().pp_mlp_train_step(self.h, _ptr(X), _ptr(t), X.shape[0], float(lr), _ptr(loss),
                                        _stream(stream)))
         return loss
+
+    def fit(self, X, t, batch, epochs, lr0, lr1, stream=None):
+        """pp_mlp_fit; returns the loss of each epoch's last slice (FP32 CUDA tensor)."""
+        import torch
+        loss = torch.empty(epochs, dtype=torch.float32, device=X.device)
+        _check(lib().pp_mlp_fit(self.h, _ptr(X), _ptr(t), X.shape[0], int(batch), int(epochs),
+                                float(lr0), float(lr1), _ptr(loss), _stream(stream)))
+        return loss
+
+
+def log_targets(N, floor, shift, scale, stream=None):
+    """pp_mlp_log_targets: (log10(max(N, floor)) - shift) / scale as FP32."""
+    import torch
+    t = torch.empty(N.shape[0], dtype=torch.float32, device=N.device)
+    _check(lib().pp_mlp_log_targets(_ptr(N), N.shape[0], float(floor), float(shift), float(scale),
+                                    _ptr(t), _stream(stream)))
+    return t
+
+
+SCREEN_MODES = {"individual": 0, "global": 1}
+
+
+def de_screened_step(pop, fit, spec, grid, lo, hi, periodic, F, CR, seed, generation, R, net,
+                     precision="fp32fast", scheme="magnus4", mode="individual", trial_out=None,
+                     trial_fit_out=None, pred_out=None, kept_out=None, stream=None):
+    """pp_de_screened_step: R proposals per individual, the network keeps NP, exact scoring."""
+    sp, g = _spec(spec), _grid(grid)
+    _check(lib().pp_de_screened_step(_ptr(pop), _ptr(fit), pop.shape[0], ctypes.byref(sp),
+                                     ctypes.byref(g), PRECISIONS[precision], SCHEMES[scheme],
+                                     _ptr(lo), _ptr(hi), _ptr(periodic), float(F), float(CR),
+                                     int(seed), int(generation), int(R), SCREEN_MODES[mode], net.h,
+                                     _ptr(trial_out), _ptr(trial_fit_out), _ptr(pred_out),
+                                     _ptr(kept_out), _stream(stream)))
 
 
 def mlp_features(params, lo, hi, stream=None):

@@ -135,8 +135,6 @@ void profile_mark_stop(cudaStream_t stream)
 int64_t wait_limit() { return g_wait_limit; }
 int skip_copies() { return g_skip_copies; }
 
-namespace {
-
 int check_grid(const pp_grid *g)
 {
     if (!g)
@@ -187,7 +185,6 @@ int check_spec(const pp_field_spec *s)
     return PP_OK;
 }
 
-}  // namespace
 }  // namespace pp
 
 using namespace pp;

@@ -27,8 +27,15 @@ void clear_error();
 
 // Per-device grow-only scratch buffers (slot index -> pointer).  Growth
 // synchronises the device, frees the old buffer and allocates a new one.
-enum ScratchSlot { SCR_TABLE = 0, SCR_PARTIAL, SCR_A, SCR_TRIAL, SCR_TFIT, SCR_COEF, SCR_NSLOTS };
+enum ScratchSlot {
+    SCR_TABLE = 0, SCR_PARTIAL, SCR_A, SCR_TRIAL, SCR_TFIT, SCR_COEF,
+    SCR_SCREEN_PROPS, SCR_SCREEN_X, SCR_SCREEN_Y, SCR_SCREEN_KEPT, SCR_NSLOTS
+};
 int scratch(int slot, size_t bytes, void **ptr);
+
+// Argument checks shared by the entry points (pp_capi.cu); they record the message.
+int check_grid(const pp_grid *g);
+int check_spec(const pp_field_spec *s);
 
 // Device address of the status word of the current device (nullptr on failure).
 unsigned int *status_word();

@@ -186,6 +186,138 @@ __global__ void features_kernel(const double *__restrict__ P, int B, int D, cons
     X[(size_t)r * ldx + c] = (float)((P[i] - lo[c]) / (hi[c] - lo[c]) - 0.5);
 }
 
+// trial[i] = props[r*][i] with r* = argmax_r y[r NP + i] (first maximum);
+// kept[i] = r* NP + i
+__global__ void pick_best_kernel(const double *__restrict__ props, const float *__restrict__ y, int R, int NP,
+                                 int D, double *__restrict__ trial, int32_t *__restrict__ kept)
+{
+    const int i = blockIdx.x;
+    int best = 0;
+    float bv = y[i];
+    for (int r = 1; r < R; ++r) {
+        const float v = y[(size_t)r * NP + i];
+        if (v > bv) {
+            bv = v;
+            best = r;
+        }
+    }
+    for (int j = threadIdx.x; j < D; j += blockDim.x)
+        trial[(size_t)i * D + j] = props[((size_t)best * NP + i) * D + j];
+    if (threadIdx.x == 0)
+        kept[i] = best * NP + i;
+}
+
+__device__ __forceinline__ float rank_key(float v) { return isnan(v) ? -INFINITY : v; }
+
+// Global top-NP of the n = R NP predictions: element k has rank
+// #{j : y_j > y_k or (y_j = y_k and j < k)} (NaN ranks as -inf); the element of
+// rank r < NP goes to row r of trial and kept[r] = k.
+constexpr int kRankThreads = 256;
+__global__ void __launch_bounds__(kRankThreads) rank_top_kernel(const double *__restrict__ props,
+                                                                const float *__restrict__ y, int n, int NP,
+                                                                int D, double *__restrict__ trial,
+                                                                int32_t *__restrict__ kept)
+{
+    __shared__ float tile[kRankThreads];
+    const int k = blockIdx.x * kRankThreads + threadIdx.x;
+    const float yk = k < n ? rank_key(y[k]) : 0.0f;
+    int rank = 0;
+    for (int j0 = 0; j0 < n; j0 += kRankThreads) {
+        const int j = j0 + threadIdx.x;
+        tile[threadIdx.x] = j < n ? rank_key(y[j]) : -INFINITY;
+        __syncthreads();
+        const int m = min(kRankThreads, n - j0);
+        for (int q = 0; q < m; ++q) {
+            const float v = tile[q];
+            rank += (v > yk) || (v == yk && j0 + q < k);
+        }
+        __syncthreads();
+    }
+    if (k < n && rank < NP) {
+        kept[rank] = k;
+        for (int c = 0; c < D; ++c)
+            trial[(size_t)rank * D + c] = props[(size_t)k * D + c];
+    }
+}
+
+// Selection after global screening: individual i takes the best exactly scored
+// trial among those whose parent (kept[r] mod NP) is i (first maximum, NaN never
+// chosen) when its pair number is >= fit[i].  One block per individual.
+__global__ void group_select_kernel(double *__restrict__ pop, double *__restrict__ fit,
+                                    const double *__restrict__ trial, const double *__restrict__ tfit,
+                                    const int32_t *__restrict__ kept, int NP, int D)
+{
+    __shared__ int s_best;
+    const int i = blockIdx.x;
+    if (threadIdx.x == 0) {
+        int best = -1;
+        double bv = 0.0;
+        for (int r = 0; r < NP; ++r) {
+            const double v = tfit[r];
+            if (kept[r] % NP != i || isnan(v))
+                continue;
+            if (best < 0 || v > bv) {
+                best = r;
+                bv = v;
+            }
+        }
+        s_best = (best >= 0 && bv >= fit[i]) ? best : -1;
+    }
+    __syncthreads();
+    const int r = s_best;
+    if (r < 0)
+        return;
+    for (int j = threadIdx.x; j < D; j += blockDim.x)
+        pop[(size_t)i * D + j] = trial[(size_t)r * D + j];
+    if (threadIdx.x == 0)
+        fit[i] = tfit[r];
+}
+
+// SplitMix64 output k of the generator seeded with s (Steele, Lea, Flood 2014).
+__device__ __forceinline__ uint64_t mlp_sm64_at(uint64_t s, uint64_t k)
+{
+    uint64_t z = s + (k + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// He initialisation: parameter i of a weight block with fan-in f is
+// sqrt(2/f) times a standard normal from the Box-Muller transform of outputs
+// 2i and 2i+1; biases are zero.  Blocks: [W1 | b1 | W2 | b2 | W3 | b3 | w4 | b4].
+__global__ void he_init_kernel(float *__restrict__ p, long long n, long long oW1, long long ob1,
+                               long long oW2, long long ob2, long long oW3, long long ob3, long long ow4,
+                               long long ob4, int din, int H, uint64_t seed)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    int fan = 0;
+    if (i >= oW1 && i < ob1)
+        fan = din;
+    else if ((i >= oW2 && i < ob2) || (i >= oW3 && i < ob3) || (i >= ow4 && i < ob4))
+        fan = H;
+    if (!fan) {
+        p[i] = 0.0f;
+        return;
+    }
+    const double u1 = ((double)(mlp_sm64_at(seed, 2 * (uint64_t)i) >> 11) + 1.0) * 0x1.0p-53;  // (0, 1]
+    const double u2 = (double)(mlp_sm64_at(seed, 2 * (uint64_t)i + 1) >> 11) * 0x1.0p-53;
+    const double z = sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
+    p[i] = (float)(z * sqrt(2.0 / fan));
+}
+
+// t = (log10(max(N, floor)) - shift) / scale
+__global__ void log_targets_kernel(const double *__restrict__ N, int n, double floor_, double shift,
+                                   double scale, float *__restrict__ t)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const double v = N[i];
+        t[i] = (float)((log10(v > floor_ ? v : floor_) - shift) / scale);
+    }
+}
+
 inline unsigned nb(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
@@ -422,6 +554,26 @@ int pp_mlp_set_params(pp_mlp *h, const float *params, void *stream)
     return repack_weights(h, st);
 }
 
+int pp_mlp_init(pp_mlp *h, uint64_t seed, void *stream)
+{
+    clear_error();
+    if (!h)
+        return fail(PP_ERR_INVALID_ARG, "network handle is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    he_init_kernel<<<nb(h->nparam), 256, 0, st>>>(h->p, h->nparam, h->off_W1, h->off_b1, h->off_W2, h->off_b2,
+                                                   h->off_W3, h->off_b3, h->off_w4, h->off_b4, h->din, h->H,
+                                                   seed);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(h->m, 0, sizeof(float) * h->nparam, st);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(h->v, 0, sizeof(float) * h->nparam, st);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "surrogate initialisation");
+    h->step = 0;
+    return repack_weights(h, st);
+}
+
 int pp_mlp_get_params(const pp_mlp *h, float *params, void *stream)
 {
     clear_error();
@@ -488,6 +640,127 @@ int pp_mlp_train_step(pp_mlp *h, const float *X, const float *t, int32_t B, floa
     if (e != cudaSuccess)
         return cuda_fail(e, "Adam");
     return repack_weights(h, st);
+}
+
+int pp_mlp_fit(pp_mlp *h, const float *X, const float *t, int32_t n, int32_t batch, int32_t epochs,
+               float lr0, float lr1, float *epoch_loss, void *stream)
+{
+    clear_error();
+    if (!h || !X || !t || n < 1 || batch < 1 || batch > h->bmax || epochs < 1)
+        return fail(PP_ERR_INVALID_ARG, "need a network, X and t, n >= 1, 1 <= batch <= max_batch, epochs >= 1");
+    if (!(lr0 >= 0.0f) || !(lr1 >= 0.0f))
+        return fail(PP_ERR_INVALID_ARG, "learning rates must be non-negative");
+    const long long per = (n + (long long)batch - 1) / batch, total = per * epochs;
+    long long k = 0;
+    for (int e = 0; e < epochs; ++e)
+        for (long long b = 0; b < per; ++b, ++k) {
+            const int r0 = (int)(b * batch), rows = (int)std::min<long long>(batch, n - r0);
+            // cosine schedule from lr0 (first step) to lr1 (last step)
+            const double c = total > 1 ? 0.5 * (1.0 + cos(M_PI * (double)k / (double)(total - 1))) : 1.0;
+            const float lr = (float)(lr1 + (lr0 - lr1) * c);
+            float *loss = (epoch_loss && b == per - 1) ? epoch_loss + e : nullptr;
+            const int rc = pp_mlp_train_step(h, X + (size_t)r0 * h->din, t + r0, rows, lr, loss, stream);
+            if (rc)
+                return rc;
+        }
+    return PP_OK;
+}
+
+int pp_mlp_log_targets(const double *N, int32_t n, double floor_value, double shift, double scale, float *t,
+                       void *stream)
+{
+    clear_error();
+    if (!N || !t || n < 0 || !(floor_value > 0.0) || !(scale != 0.0) || !isfinite(shift) || !isfinite(scale))
+        return fail(PP_ERR_INVALID_ARG, "need N and t, n >= 0, floor > 0, finite shift and non-zero scale");
+    if (n == 0)
+        return PP_OK;
+    log_targets_kernel<<<nb(n), 256, 0, (cudaStream_t)stream>>>(N, n, floor_value, shift, scale, t);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PP_OK : cuda_fail(e, "log targets");
+}
+
+int pp_de_screened_step(double *pop, double *fit, int32_t NP, const pp_field_spec *spec,
+                        const pp_grid *grid, int32_t precision, int32_t scheme, const double *lo,
+                        const double *hi, const uint8_t *periodic, double F, double CR, uint64_t seed,
+                        uint64_t generation, int32_t R, int32_t mode, pp_mlp *mlp, double *trial_out,
+                        double *trial_fit_out, float *pred_out, int32_t *kept_out, void *stream)
+{
+    clear_error();
+    int rc = check_spec(spec);
+    if (!rc)
+        rc = check_grid(grid);
+    if (rc)
+        return rc;
+    if (!pop || !fit || !lo || !hi || !mlp)
+        return fail(PP_ERR_INVALID_ARG, "pop, fit, lo, hi and mlp must not be NULL");
+    if (precision != PP_FP64 && precision != PP_FP32 && precision != PP_FP32_FAST)
+        return fail(PP_ERR_INVALID_ARG, "precision must be PP_FP64, PP_FP32 or PP_FP32_FAST");
+    if (scheme != PP_RK4 && scheme != PP_MAGNUS4 && scheme != PP_SPLIT2)
+        return fail(PP_ERR_INVALID_ARG, "scheme must be PP_RK4, PP_MAGNUS4 or PP_SPLIT2");
+    const int D = 4 * spec->K;
+    if (NP < 4 || NP > 65535 || R < 1 || R > 64 || (long long)R * NP > mlp->bmax || D != mlp->din)
+        return fail(PP_ERR_INVALID_ARG, "need NP >= 4, 1 <= R <= 64, R NP <= the network's max_batch "
+                                        "and 4K equal to its input size");
+    if (!(CR >= 0.0 && CR <= 1.0) || !isfinite(F))
+        return fail(PP_ERR_INVALID_ARG, "CR must be in [0, 1] and F finite");
+    if (mode != PP_SCREEN_PER_INDIVIDUAL && mode != PP_SCREEN_GLOBAL)
+        return fail(PP_ERR_INVALID_ARG, "mode must be PP_SCREEN_PER_INDIVIDUAL or PP_SCREEN_GLOBAL");
+    cudaStream_t st = (cudaStream_t)stream;
+    void *props = nullptr, *X = nullptr, *y = nullptr, *trial = nullptr, *tfit = nullptr, *A = nullptr;
+    void *kept = nullptr;
+    const int ld = 2 * spec->n_steps + 1;
+    rc = scratch(SCR_SCREEN_PROPS, sizeof(double) * (size_t)R * NP * D, &props);
+    if (!rc)
+        rc = scratch(SCR_SCREEN_X, sizeof(float) * (size_t)R * NP * D, &X);
+    if (!rc)
+        rc = scratch(SCR_SCREEN_Y, sizeof(float) * (size_t)R * NP, &y);
+    if (!rc && !trial_out)
+        rc = scratch(SCR_TRIAL, sizeof(double) * (size_t)NP * D, &trial);
+    if (!rc && !trial_fit_out)
+        rc = scratch(SCR_TFIT, sizeof(double) * (size_t)NP, &tfit);
+    if (!rc)
+        rc = scratch(SCR_A, sizeof(double) * 2 * (size_t)ld * NP, &A);
+    if (!rc && !kept_out)
+        rc = scratch(SCR_SCREEN_KEPT, sizeof(int32_t) * (size_t)NP, &kept);
+    if (rc)
+        return rc;
+    int32_t *kp = kept_out ? kept_out : (int32_t *)kept;
+    double *tr = trial_out ? trial_out : (double *)trial;
+    double *tf = trial_fit_out ? trial_fit_out : (double *)tfit;
+    // R proposals per individual, each from its own counter-RNG stream (generation R g + r)
+    for (int r = 0; r < R && !rc; ++r)
+        rc = launch_de_propose(pop, NP, D, lo, hi, periodic, F, CR, seed, generation * (uint64_t)R + r,
+                               (double *)props + (size_t)r * NP * D, st);
+    if (rc)
+        return rc;
+    features_kernel<<<nb((long long)R * NP * D), 256, 0, st>>>((const double *)props, R * NP, D, lo, hi, D,
+                                                                (float *)X);
+    rc = pp_mlp_forward(mlp, (const float *)X, R * NP, (float *)y, stream);
+    if (rc)
+        return rc;
+    if (pred_out) {
+        cudaError_t e = cudaMemcpyAsync(pred_out, y, sizeof(float) * (size_t)R * NP, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "screening predictions");
+    }
+    if (mode == PP_SCREEN_PER_INDIVIDUAL)
+        pick_best_kernel<<<NP, 64, 0, st>>>((const double *)props, (const float *)y, R, NP, D, tr, kp);
+    else
+        rank_top_kernel<<<nb((long long)R * NP, kRankThreads), kRankThreads, 0, st>>>(
+            (const double *)props, (const float *)y, R * NP, NP, D, tr, kp);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return cuda_fail(e, "screening pick");
+    if ((rc = launch_synth_field(tr, NP, spec, (double *)A, ld, nullptr, nullptr, st)))
+        return rc;
+    if ((rc = launch_pair_number((double *)A, NP, ld, nullptr, spec->T / spec->n_steps, grid, precision,
+                                 scheme, tf, nullptr, st)))
+        return rc;
+    if (mode == PP_SCREEN_PER_INDIVIDUAL)
+        return launch_de_select(pop, fit, tr, tf, NP, D, st);
+    group_select_kernel<<<NP, 64, 0, st>>>(pop, fit, tr, tf, kp, NP, D);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? PP_OK : cuda_fail(e, "screening selection");
 }
 
 int pp_mlp_features(const double *params, int32_t B, int32_t D, const double *lo, const double *hi,

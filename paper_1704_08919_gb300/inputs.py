@@ -17,6 +17,10 @@ windows, Sec. V, scaled to the configurations below):
   B-splines on [0, 2], fluence 2.0; momentum grids of side 32, 48, 64, 80 or 96
   (n_z = side / 2) over [-2, 2]^2 x [0, 2], mirrored, by the quintile of the
   slot's initial peak field; DE with F = 0.8, CR = 0.9.
+* ``SURROGATE_DE``: surrogate-screened DE on the DE_BATCH solver settings: a
+  network 32 -> 256 -> 256 -> 256 -> 1 trained on 50,000 seeded random pulses
+  scored exactly (2,048 more held out), population 128, 8 proposals per
+  individual per generation of which the network keeps one.
 * ``DE_BATCH``: a population of 64 B-spline pulses (K = 8 control points per
   amplitude and phase per polarisation, cubic splines on [0, 2], T = 200,
   8192 RK4 steps, fluence 2.0) on a 64 x 64 x 32 grid over [-2, 2]^2 x [0, 2]
@@ -37,6 +41,14 @@ DE_BATCH = dict(
     NP=64, K=8, order=4, w_min=0.0, w_max=2.0, T=200.0, fluence=2.0, n_steps=8192,
     F=0.8, CR=0.9,
     grid=dict(nx=64, ny=64, nz=32, x0=-2.0, x1=2.0, y0=-2.0, y1=2.0, z0=0.0, z1=2.0, mirror_z=1),
+)
+
+SURROGATE_DE = dict(
+    name="surrogate-screened DE: pop 128, 8 proposals/individual, MLP 32-256-256-256-1 on 50k "
+         "exact samples, solver as de-batch (K=8 T=200 8192 steps grid 64x64x32)",
+    NP=128, R=8, hidden=256, n_train=50000, n_heldout=2048, generations=60,
+    epochs=60, batch=256, lr0=2e-3, lr1=5e-5,
+    train_seed=424242, heldout_seed=434343, pop_seed=7, de_seed=77,
 )
 
 
