@@ -61,7 +61,7 @@ def parse():
                     help="modes of one candidate in the CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="de-batch", choices=["de-batch", "uneven", "surrogate"],
+    ap.add_argument("--workload", default="de-batch", choices=["de-batch", "uneven", "surrogate", "gemm"],
                     help="de-batch: the 64-candidate DE generation (default); uneven: 128 slots "
                          "of uneven length and grid, generations in one CUDA graph; surrogate: "
                          "exact calls of surrogate-screened DE against plain DE")
@@ -323,6 +323,72 @@ def uneven_main(args):
 # ----------------------------------------------------------------------------- surrogate
 
 
+GEMM_SHAPES = ((65536, 256, 256), (16384, 256, 4096))
+
+
+def measured_peaks():
+    """HBM copy bandwidth (GB/s) and bf16 GEMM rate (TFLOP/s) measured on this GPU model,
+    else the fallback figures of an earlier GB300 measurement."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "source": "measured"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
+
+
+def gemm_measure(pp, torch, reps=20):
+    """Live timing of pp_gemm_bf16 (the tensor-core kernel of the surrogate) on two
+    shapes: a hidden layer over a large batch (HBM-bound: FP32 output) and a
+    long contraction (tensor-bound).  Algorithmic bytes = packed A and B read once
+    + FP32 D written once; flop = 2 M N K."""
+    import math as _m
+    PEAKS = measured_peaks()
+    out = []
+    for M, N, K in GEMM_SHAPES:
+        g = torch.Generator(device="cuda").manual_seed(M + K)
+        A = torch.rand((M, K), device="cuda", generator=g) - 0.5
+        B = torch.rand((N, K), device="cuda", generator=g) - 0.5
+        Ap, _, _ = pp.pack_bf16(A)
+        Bp, _, _ = pp.pack_bf16(B)
+        del A, B
+        D = torch.empty((M, N), dtype=torch.float32, device="cuda")
+        for _ in range(3):
+            pp.gemm_bf16(Ap, Bp, M, N, K, out=D)
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(reps):
+            pp.gemm_bf16(Ap, Bp, M, N, K, out=D)
+        e1.record(st)
+        torch.cuda.synchronize()
+        if pp.sync_status() != pp.PP_OK:
+            raise RuntimeError("GEMM failed")
+        ms = e0.elapsed_time(e1) / reps
+        flop = 2.0 * M * N * K
+        byts = 2.0 * (M * K + N * K) + 4.0 * M * N
+        tf = flop / (ms * 1e-3) / 1e12
+        gbs = byts / (ms * 1e-3) / 1e9
+        ai = flop / byts
+        bound = "tensor" if ai > 1e3 * PEAKS["bf16_tflops"] / PEAKS["hbm_gbs"] else "hbm"
+        frac = tf / PEAKS["bf16_tflops"] if bound == "tensor" else gbs / PEAKS["hbm_gbs"]
+        out.append({"M": M, "N": N, "K": K, "ms": ms, "tflops": tf, "gbs": gbs,
+                    "flop_per_byte": _m.floor(ai * 10) / 10, "bound": bound,
+                    "frac": frac, "peak_source": PEAKS["source"]})
+    return out
+
+
+def gemm_main(args):
+    import torch
+    import paper_1704_08919_gb300 as pp
+    pp.lib()
+    print(json.dumps({"metric": "pp_gemm_bf16 throughput", "gemm": gemm_measure(pp, torch)}),
+          flush=True)
+    return 0
+
+
 def surrogate_main(args):
     """Surrogate-screened DE against plain DE on the de-batch solver settings: the
     network is trained on exact evaluations of random pulses, then both forms run
@@ -407,7 +473,8 @@ def surrogate_main(args):
         "gain_median": med, "gains": gains,
         "training": {"pulses": n_train, "seconds_generate": t_gen, "seconds_fit": t_fit,
                      "final_epoch_loss": float(losses[-1].item())},
-        "heldout": held, "per_seed": per_seed, "clocks": clk}), flush=True)
+        "heldout": held, "per_seed": per_seed, "gemm": gemm_measure(pp, torch),
+        "clocks": clk}), flush=True)
     return 0
 
 
@@ -422,6 +489,8 @@ def main():
         return uneven_main(args)
     if args.workload == "surrogate":
         return surrogate_main(args)
+    if args.workload == "gemm":
+        return gemm_main(args)
     import torch
     import paper_1704_08919_gb300 as pp
 

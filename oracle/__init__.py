@@ -53,6 +53,13 @@ def lib():
         L.orc_de_propose.argtypes = [_pd, _i, _i, _pd, _pd, _pu8, _d, _d, _u64, _u64, _pd]
         L.orc_de_select.argtypes = [_pd, _pd, _pd, _pd, _i, _i]
         L.orc_num_threads.argtypes = [_i]
+        L.orc_synth_raw.argtypes = [_pd, _i, _i, _i, _d, _d, _d, _i, _i, _pd, _pd, _pd, _pd]
+        L.orc_fluence_raw.argtypes = [_pd, _i, _i, _d, _d, _d, _pd, _pd]
+        L.orc_qke6_adjoint_mode.argtypes = [_pd, _pd, _pd, _i, _i, _d, _pd, _d, _pd, _pd, _pd]
+        L.orc_qke6_adjoint_mode.restype = _d
+        L.orc_qke6_grad.argtypes = [_pd, _pd, _pd, _i, _i, _d, _pd, _pd, _i, _pd, _pd, _pd, _pd,
+                                    _pd, _i]
+        L.orc_synth_vjp.argtypes = [_pd, _i, _i, _d, _d, _d, _i, _i, _pd, _pd, _pd, _pd]
         _lib = L
     return _lib
 
@@ -243,3 +250,106 @@ def de_select(pop, fit, trial, trial_fit):
     if rc:
         raise ValueError("orc_de_select rc=%d" % rc)
     return pop, fit
+
+
+# ----------------------------------------------------------------------------- local search
+
+
+def synth_raw(params, K, order, wmin, wmax, T, n_steps):
+    """(A, E, Edot [c,2,2n+1], U[c]): Eq. (field) with g = 1 and no renormalisation,
+    and the fluence of Eq. (energy) over one period (Sec. IV.A keeps U by a penalty)."""
+    params = _f64(params).reshape(-1, 4 * K)
+    nc = params.shape[0]
+    ld = 2 * n_steps + 1
+    A, E, Ed = np.zeros((nc, 2, ld)), np.zeros((nc, 2, ld)), np.zeros((nc, 2, ld))
+    U = np.zeros(nc)
+    rc = lib().orc_synth_raw(_p(params), nc, K, order, wmin, wmax, T, n_steps, ld, _p(A), _p(E),
+                             _p(Ed), _p(U))
+    if rc:
+        raise ValueError("orc_synth_raw rc=%d" % rc)
+    return A, E, Ed, U
+
+
+def fluence_raw(params, K, order, wmin, wmax, T):
+    """(U, dU/dparams[4K]) of the un-normalised field, Eq. (energy)."""
+    params = _f64(params).reshape(4 * K)
+    U = np.zeros(1)
+    dU = np.zeros(4 * K)
+    rc = lib().orc_fluence_raw(_p(params), K, order, wmin, wmax, T, _p(U), _p(dU))
+    if rc:
+        raise ValueError("orc_fluence_raw rc=%d" % rc)
+    return float(U[0]), dU
+
+
+def qke6_adjoint_mode(A, E, Edot, n_steps, dt, p, weight=1.0):
+    """(f, gA, gE, gEd): f = 1 - chi_1 of one mode and d(weight f)/d(samples), Eqs. (adj), (grad)."""
+    A, E, Ed = (_f64(x).reshape(2, -1) for x in (A, E, Edot))
+    ld = A.shape[1]
+    g = [np.zeros((2, ld)) for _ in range(3)]
+    f = lib().orc_qke6_adjoint_mode(_p(A), _p(E), _p(Ed), ld, n_steps, dt, _p(_f64(p)), weight,
+                                    _p(g[0]), _p(g[1]), _p(g[2]))
+    return f, g[0], g[1], g[2]
+
+
+def qke6_grad(A, E, Edot, n_steps, dt, p, w, nthreads=0):
+    """(J, f[m], gA, gE, gEd): J = sum_m w_m f(p_m) and dJ/d(samples), Eqs. (opt_prob), (grad)."""
+    A, E, Ed = (_f64(x).reshape(2, -1) for x in (A, E, Edot))
+    ld = A.shape[1]
+    p = _f64(p).reshape(-1, 3)
+    w = _f64(w).reshape(-1)
+    nm = p.shape[0]
+    f = np.zeros(nm)
+    J = np.zeros(1)
+    g = [np.zeros((2, ld)) for _ in range(3)]
+    rc = lib().orc_qke6_grad(_p(A), _p(E), _p(Ed), ld, n_steps, dt, _p(p), _p(w), nm, _p(f), _p(J),
+                             _p(g[0]), _p(g[1]), _p(g[2]), nthreads)
+    if rc:
+        raise ValueError("orc_qke6_grad rc=%d" % rc)
+    return float(J[0]), f, g[0], g[1], g[2]
+
+
+def synth_vjp(params, K, order, wmin, wmax, T, n_steps, gA, gE, gEd):
+    """dJ/dparams[4K] from dJ/d(samples of A, E, Edot), through Eqs. (field), (coeff_basis_E/phi)."""
+    params = _f64(params).reshape(4 * K)
+    gA, gE, gEd = (_f64(x).reshape(2, -1) for x in (gA, gE, gEd))
+    out = np.zeros(4 * K)
+    rc = lib().orc_synth_vjp(_p(params), K, order, wmin, wmax, T, n_steps, gA.shape[1], _p(gA),
+                             _p(gE), _p(gEd), _p(out))
+    if rc:
+        raise ValueError("orc_synth_vjp rc=%d" % rc)
+    return out
+
+
+def grid_modes(grid):
+    """(p[m,3], w[m]): the grid momenta (x fastest) and their trapezoid weights, Eq. (opt_prob)."""
+    g = grid
+
+    def ax(n, a, b):
+        return np.array([a]) if n == 1 else a + (b - a) * np.arange(n) / (n - 1)
+    x, y, z = ax(g["nx"], g["x0"], g["x1"]), ax(g["ny"], g["y0"], g["y1"]), ax(g["nz"], g["z0"], g["z1"])
+    wx = trapz_weights(g["nx"], g["x0"], g["x1"])
+    wy = trapz_weights(g["ny"], g["y0"], g["y1"])
+    wz = trapz_weights(g["nz"], g["z0"], g["z1"], int(g.get("mirror_z", 0)))
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    WZ, WY, WX = np.meshgrid(wz, wy, wx, indexing="ij")
+    p = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+    return p, (WX * WY * WZ).ravel()
+
+
+def al_objective(params, spec, grid, U_const, lam, mu, nthreads=0):
+    """The augmented Lagrangian of Sec. IV.A for one parameter vector:
+    L = -J - lam C + C^2 / (2 mu), C = U_const - U, with J from the QKE (Eq. (opt_prob)),
+    and its gradient, Eq. (grad): grad L = -grad J - (lam - C / mu) grad C.
+    Returns dict(L, grad, J, C, gJ, gC)."""
+    K, n = spec["K"], spec["n_steps"]
+    args = (K, spec["order"], spec["w_min"], spec["w_max"], spec["T"])
+    A, E, Ed, _ = synth_raw(params, *args, n)
+    p, w = grid_modes(grid)
+    J, _, gA, gE, gEd = qke6_grad(A[0], E[0], Ed[0], n, spec["T"] / n, p, w, nthreads)
+    gJ = synth_vjp(params, *args, n, gA, gE, gEd)
+    U, dU = fluence_raw(params, *args)
+    C = U_const - U
+    gC = -dU
+    L = -J - lam * C + C * C / (2.0 * mu)
+    grad = -gJ - (lam - C / mu) * gC
+    return {"L": L, "grad": grad, "J": J, "C": C, "gJ": gJ, "gC": gC}

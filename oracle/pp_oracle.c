@@ -19,6 +19,7 @@
  *   - pair density ....................... Sec. II.A, Eq. (pair_prod_homo)
  *   - total density (momentum integral) .. Sec. II.A last paragraph, Eq. (opt_prob)
  *   - quantum kinetic equation (6 comp.) . Sec. II.B, Eqs. (qke), (matrix)
+ *   - its adjoint and the gradient ........ Sec. IV.A, Eqs. (eom2), (adj), (grad)
  *   - differential evolution ............. Sec. IV.B, DE/rand/1/bin steps 1-4
  *
  * Compile with -ffp-contract=off so that every product and sum is rounded as
@@ -819,6 +820,382 @@ int orc_qke6_modes(const double *A, const double *E, const double *Edot, int ld,
         return ORC_ERR_ARG;
     mode_job J = {A, E, Edot, ld, n_steps, 0, 1, dt, p, nm, 1, 0, f_out, NULL};
     run_modes(&J, nthreads);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Local search, Sec. IV.A: the field without renormalisation and with its   */
+/* time derivative, the adjoint of the QKE forward solve (Eqs. (eom2), (adj), */
+/* (grad)) and the chain rule back to the B-spline parameters.               */
+/* ------------------------------------------------------------------------- */
+
+/* Field of Eq. (field) with g = 1 and no renormalisation (the local search
+ * holds the fluence through the augmented Lagrangian's penalty instead): A and
+ * E as orc_synth_field gives them with s = 1, Ed = dE/dt, all [c][2][ld] on the
+ * half-step grid.  U_out[c] (may be NULL) = the fluence of Eq. (energy) over one
+ * period, (T/2) sum_{l,j} E_{l,j}^2 (orthogonality of the modes). */
+int orc_synth_raw(const double *params, int ncand, int K, int order, double wmin, double wmax,
+                  double T, int n_steps, int ld, double *A, double *E, double *Ed, double *U_out)
+{
+    if (ncand < 0 || n_steps < 1 || ld < 2 * n_steps + 1 || !(T > 0) || !A)
+        return ORC_ERR_ARG;
+    int M = orc_mode_range(wmin, wmax, T, NULL);
+    if (M <= 0)
+        return ORC_ERR_ARG;
+    double *Om = malloc(sizeof(double) * M);
+    double *amp = malloc(sizeof(double) * 2 * M);
+    double *ph = malloc(sizeof(double) * 2 * M);
+    int status = ORC_OK;
+    double h = T / (2.0 * n_steps), ti = -0.5 * T;
+    for (int c = 0; c < ncand && status == ORC_OK; c++) {
+        int rc = orc_spectrum(params + (size_t)c * 4 * K, K, order, wmin, wmax, T, Om, amp, ph);
+        if (rc < 0) {
+            status = -rc;
+            break;
+        }
+        if (U_out) {
+            double U = 0.0;
+            for (int q = 0; q < 2 * M; q++)
+                U += amp[q] * amp[q];
+            U_out[c] = 0.5 * T * U;
+        }
+        for (int l = 0; l < 2; l++) {
+            double *Ar = A + ((size_t)c * 2 + l) * ld;
+            double *Er = E ? E + ((size_t)c * 2 + l) * ld : NULL;
+            double *Dr = Ed ? Ed + ((size_t)c * 2 + l) * ld : NULL;
+            for (int k = 0; k <= 2 * n_steps; k++) {
+                double t = ti + (double)k * h;
+                double a = 0.0, e = 0.0, d = 0.0;
+                for (int m = 0; m < M; m++) {
+                    double Ej = amp[l * M + m], Pj = ph[l * M + m], W = Om[m];
+                    e += Ej * cos(W * t - Pj);
+                    a += Ej * (sin(W * t - Pj) - sin(W * ti - Pj)) / W;
+                    d -= Ej * W * sin(W * t - Pj);
+                }
+                Ar[k] = -a;
+                if (Er)
+                    Er[k] = e;
+                if (Dr)
+                    Dr[k] = d;
+            }
+        }
+    }
+    free(Om);
+    free(amp);
+    free(ph);
+    return status;
+}
+
+/* The fluence U of the un-normalised field and its gradient with respect to
+ * the 4K parameters: dU/da^E_{l,i} = T sum_j E_{l,j} B_i(Omega_j), zero for the
+ * phase weights. */
+int orc_fluence_raw(const double *params, int K, int order, double wmin, double wmax, double T,
+                    double *U_out, double *dU)
+{
+    int M = orc_mode_range(wmin, wmax, T, NULL);
+    if (M <= 0 || !U_out || !dU)
+        return ORC_ERR_ARG;
+    double *Om = malloc(sizeof(double) * M);
+    double *amp = malloc(sizeof(double) * 2 * M);
+    double *ph = malloc(sizeof(double) * 2 * M);
+    double *B = malloc(sizeof(double) * K);
+    int rc = orc_spectrum(params, K, order, wmin, wmax, T, Om, amp, ph);
+    if (rc < 0) {
+        free(Om), free(amp), free(ph), free(B);
+        return -rc;
+    }
+    double U = 0.0;
+    for (int q = 0; q < 2 * M; q++)
+        U += amp[q] * amp[q];
+    *U_out = 0.5 * T * U;
+    for (int i = 0; i < 4 * K; i++)
+        dU[i] = 0.0;
+    for (int m = 0; m < M; m++) {
+        orc_bspline_basis(K, order, wmin, wmax, Om[m], B);
+        for (int l = 0; l < 2; l++)
+            for (int i = 0; i < K; i++)
+                dU[2 * l * K + i] += T * amp[l * M + m] * B[i];
+    }
+    free(Om), free(amp), free(ph), free(B);
+    return ORC_OK;
+}
+
+/* The three coefficients of the QKE matrix of Eq. (matrix) at one sample,
+ * N = Q S_Q + R S_R + 2 omega S_W (S_* the constant 0/+-1 patterns), and their
+ * partial derivatives with respect to the in-plane kinetic momentum P, the
+ * field E and its derivative Ed.  X = 0 (E = 0) gives Q = R = 0 and zero
+ * derivatives, as qke_matrix does for R. */
+typedef struct {
+    double Q, R, w;
+    double dQ_dP[2], dR_dP[2], dw_dP[2], dQ_dE[2], dR_dE[2], dR_dEd[2];
+} qke_coef;
+
+static void qke_coef_eval(const double P[3], const double E[2], const double Ed[2], qke_coef *c)
+{
+    memset(c, 0, sizeof(*c));
+    double w2 = pdot2(P) + 1.0, w = sqrt(w2);
+    double EE = E[0] * E[0] + E[1] * E[1];
+    double EP = E[0] * P[0] + E[1] * P[1];
+    double X = w2 * EE - EP * EP;
+    double eperp = sqrt(1.0 + P[2] * P[2]);
+    double cr = E[0] * Ed[1] - E[1] * Ed[0];
+    double dcr_dE[2] = {Ed[1], -Ed[0]}, dcr_dEd[2] = {-E[1], E[0]};
+    c->w = w;
+    for (int a = 0; a < 2; a++)
+        c->dw_dP[a] = P[a] / w;
+    if (!(X > 0.0))
+        return;
+    double sX = sqrt(X);
+    c->Q = sX / w2;
+    c->R = eperp * w * cr / X;
+    for (int a = 0; a < 2; a++) {
+        double dX_dP = 2.0 * P[a] * EE - 2.0 * EP * E[a];
+        double dX_dE = 2.0 * w2 * E[a] - 2.0 * EP * P[a];
+        c->dQ_dP[a] = dX_dP / (2.0 * sX * w2) - sX * 2.0 * P[a] / (w2 * w2);
+        c->dQ_dE[a] = dX_dE / (2.0 * sX * w2);
+        c->dR_dP[a] = eperp * cr * (c->dw_dP[a] / X - w * dX_dP / (X * X));
+        c->dR_dE[a] = eperp * w * (dcr_dE[a] / X - cr * dX_dE / (X * X));
+        c->dR_dEd[a] = eperp * w * dcr_dEd[a] / X;
+    }
+}
+
+/* y_j = sum_i N[i][j] x_i */
+static void mat6_tvec(const double N[6][6], const double x[6], double y[6])
+{
+    for (int j = 0; j < 6; j++) {
+        double acc = 0.0;
+        for (int i = 0; i < 6; i++)
+            acc += N[i][j] * x[i];
+        y[j] = acc;
+    }
+}
+
+/* One stage k = N y of the forward solve contributes kb (x) y to the adjoint of
+ * N; its projections on S_Q, S_R and 2 S_W are the adjoints of Q, R and omega,
+ * which the chain rule sends to the sample's A (through P = p - A), E and Ed. */
+static void coef_adjoint(const qke_coef *c, const double kb[6], const double y[6], int k, int ld,
+                         double *gA, double *gE, double *gEd)
+{
+    double Qb = -kb[0] * y[1] + kb[1] * y[0] + kb[4] * y[5] - kb[5] * y[4];
+    double Rb = kb[1] * y[3] - kb[2] * y[4] - kb[3] * y[1] + kb[4] * y[2];
+    double wb = 2.0 * (-kb[1] * y[2] + kb[2] * y[1] + kb[3] * y[4] - kb[4] * y[3]);
+    for (int l = 0; l < 2; l++) {
+        gA[l * ld + k] -= Qb * c->dQ_dP[l] + Rb * c->dR_dP[l] + wb * c->dw_dP[l];
+        gE[l * ld + k] += Qb * c->dQ_dE[l] + Rb * c->dR_dE[l];
+        gEd[l * ld + k] += Rb * c->dR_dEd[l];
+    }
+}
+
+static void qke_sample(const double *A, const double *E, const double *Ed, int ld, int k,
+                       const double p[3], qke_coef *c, double N[6][6])
+{
+    double P[3] = {p[0] - A[k], p[1] - A[ld + k], p[2]};
+    double Ek[2] = {E[k], E[ld + k]};
+    double Edk[2] = {Ed[k], Ed[ld + k]};
+    qke_coef_eval(P, Ek, Edk, c);
+    qke_matrix(P, Ek, Edk, N);
+}
+
+/* f = 1 - chi_1(t_f) of one mode by the RK4 of orc_qke6_mode and the gradient
+ * of weight * f with respect to every sample of A, E and Ed, ADDED to gA, gE,
+ * gEd ([2][ld] each).  The adjoint lambda of Eq. (adj) (final value
+ * lambda_1 = -1, the others 0, here scaled by the weight) is carried backwards
+ * through the RK4 steps as the exact adjoint of the discrete forward map, and
+ * the inner product <chi, grad N lambda> of Eq. (grad) is taken stage by stage,
+ * so the result is the exact derivative of the discrete objective. */
+double orc_qke6_adjoint_mode(const double *A, const double *E, const double *Ed, int ld,
+                             int n_steps, double dt, const double p[3], double weight, double *gA,
+                             double *gE, double *gEd)
+{
+    double (*chi)[6] = malloc(sizeof(double[6]) * (size_t)(n_steps + 1));
+    memset(chi[0], 0, sizeof(double[6]));
+    chi[0][0] = 1.0;
+    for (int n = 0; n < n_steps; n++) {
+        double N0[6][6], Nh[6][6], N1[6][6], k1[6], k2[6], k3[6], k4[6], y[6];
+        qke_coef c;
+        qke_sample(A, E, Ed, ld, 2 * n, p, &c, N0);
+        qke_sample(A, E, Ed, ld, 2 * n + 1, p, &c, Nh);
+        qke_sample(A, E, Ed, ld, 2 * n + 2, p, &c, N1);
+        mat6_vec(N0, chi[n], k1);
+        for (int i = 0; i < 6; i++)
+            y[i] = chi[n][i] + 0.5 * dt * k1[i];
+        mat6_vec(Nh, y, k2);
+        for (int i = 0; i < 6; i++)
+            y[i] = chi[n][i] + 0.5 * dt * k2[i];
+        mat6_vec(Nh, y, k3);
+        for (int i = 0; i < 6; i++)
+            y[i] = chi[n][i] + dt * k3[i];
+        mat6_vec(N1, y, k4);
+        for (int i = 0; i < 6; i++)
+            chi[n + 1][i] = chi[n][i] + dt / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+    }
+    double f = 1.0 - chi[n_steps][0];
+    double bar[6] = {-weight, 0, 0, 0, 0, 0};  /* d(weight f)/d chi(t_f) */
+    for (int n = n_steps - 1; n >= 0; n--) {
+        double N0[6][6], Nh[6][6], N1[6][6], k1[6], k2[6], k3[6], y2[6], y3[6], y4[6];
+        qke_coef c0, ch, c1;
+        qke_sample(A, E, Ed, ld, 2 * n, p, &c0, N0);
+        qke_sample(A, E, Ed, ld, 2 * n + 1, p, &ch, Nh);
+        qke_sample(A, E, Ed, ld, 2 * n + 2, p, &c1, N1);
+        const double *x = chi[n];
+        mat6_vec(N0, x, k1);
+        for (int i = 0; i < 6; i++)
+            y2[i] = x[i] + 0.5 * dt * k1[i];
+        mat6_vec(Nh, y2, k2);
+        for (int i = 0; i < 6; i++)
+            y3[i] = x[i] + 0.5 * dt * k2[i];
+        mat6_vec(Nh, y3, k3);
+        for (int i = 0; i < 6; i++)
+            y4[i] = x[i] + dt * k3[i];
+        double kb1[6], kb2[6], kb3[6], kb4[6], xb[6], yb[6];
+        for (int i = 0; i < 6; i++) {
+            kb1[i] = dt / 6.0 * bar[i];
+            kb2[i] = 2.0 * dt / 6.0 * bar[i];
+            kb3[i] = 2.0 * dt / 6.0 * bar[i];
+            kb4[i] = dt / 6.0 * bar[i];
+            xb[i] = bar[i];
+        }
+        /* k4 = N1 y4, y4 = x + dt k3 */
+        coef_adjoint(&c1, kb4, y4, 2 * n + 2, ld, gA, gE, gEd);
+        mat6_tvec(N1, kb4, yb);
+        for (int i = 0; i < 6; i++) {
+            xb[i] += yb[i];
+            kb3[i] += dt * yb[i];
+        }
+        /* k3 = Nh y3, y3 = x + dt/2 k2 */
+        coef_adjoint(&ch, kb3, y3, 2 * n + 1, ld, gA, gE, gEd);
+        mat6_tvec(Nh, kb3, yb);
+        for (int i = 0; i < 6; i++) {
+            xb[i] += yb[i];
+            kb2[i] += 0.5 * dt * yb[i];
+        }
+        /* k2 = Nh y2, y2 = x + dt/2 k1 */
+        coef_adjoint(&ch, kb2, y2, 2 * n + 1, ld, gA, gE, gEd);
+        mat6_tvec(Nh, kb2, yb);
+        for (int i = 0; i < 6; i++) {
+            xb[i] += yb[i];
+            kb1[i] += 0.5 * dt * yb[i];
+        }
+        /* k1 = N0 x */
+        coef_adjoint(&c0, kb1, x, 2 * n, ld, gA, gE, gEd);
+        mat6_tvec(N0, kb1, yb);
+        for (int i = 0; i < 6; i++)
+            bar[i] = xb[i] + yb[i];
+    }
+    free(chi);
+    return f;
+}
+
+typedef struct {
+    const double *A, *E, *Ed, *p, *w;
+    int ld, n_steps, nm, first, stride;
+    double dt;
+    double *f, *gA, *gE, *gEd;  /* private [2][ld] accumulators */
+} grad_job;
+
+static void *grad_worker(void *arg)
+{
+    grad_job *J = arg;
+    for (int m = J->first; m < J->nm; m += J->stride)
+        J->f[m] = orc_qke6_adjoint_mode(J->A, J->E, J->Ed, J->ld, J->n_steps, J->dt, J->p + 3 * m,
+                                        J->w[m], J->gA, J->gE, J->gEd);
+    return NULL;
+}
+
+/* J = sum_m w[m] f(p_m) (Eq. (opt_prob) with the QKE f) for one field and the
+ * gradient of J with respect to its samples: gA, gE, gEd ([2][ld], overwritten).
+ * f_out[m] (may be NULL) receives each f.  Threads accumulate privately and
+ * their sums are added in thread order. */
+int orc_qke6_grad(const double *A, const double *E, const double *Ed, int ld, int n_steps,
+                  double dt, const double *p, const double *w, int nm, double *f_out,
+                  double *J_out, double *gA, double *gE, double *gEd, int nthreads)
+{
+    if (!A || !E || !Ed || !p || !w || !J_out || !gA || !gE || !gEd || nm < 0 || n_steps < 1 ||
+        ld < 2 * n_steps + 1)
+        return ORC_ERR_ARG;
+    nthreads = resolve_threads(nthreads);
+    if (nthreads > nm)
+        nthreads = nm > 0 ? nm : 1;
+    size_t G = (size_t)2 * ld;
+    double *f = malloc(sizeof(double) * (nm > 0 ? nm : 1));
+    double *acc = calloc((size_t)nthreads * 3 * G, sizeof(double));
+    pthread_t *th = malloc(sizeof(pthread_t) * nthreads);
+    grad_job *jobs = malloc(sizeof(grad_job) * nthreads);
+    for (int i = 0; i < nthreads; i++) {
+        grad_job j = {A, E, Ed, p, w, ld, n_steps, nm, i, nthreads, dt, f,
+                      acc + (size_t)i * 3 * G, acc + (size_t)i * 3 * G + G,
+                      acc + (size_t)i * 3 * G + 2 * G};
+        jobs[i] = j;
+        pthread_create(&th[i], NULL, grad_worker, &jobs[i]);
+    }
+    for (int i = 0; i < nthreads; i++)
+        pthread_join(th[i], NULL);
+    memset(gA, 0, sizeof(double) * G);
+    memset(gE, 0, sizeof(double) * G);
+    memset(gEd, 0, sizeof(double) * G);
+    for (int i = 0; i < nthreads; i++)
+        for (size_t q = 0; q < G; q++) {
+            gA[q] += jobs[i].gA[q];
+            gE[q] += jobs[i].gE[q];
+            gEd[q] += jobs[i].gEd[q];
+        }
+    double J = 0.0;
+    for (int m = 0; m < nm; m++)
+        J += w[m] * f[m];
+    *J_out = J;
+    if (f_out)
+        memcpy(f_out, f, sizeof(double) * nm);
+    free(f), free(acc), free(th), free(jobs);
+    return ORC_OK;
+}
+
+/* Chain rule from the samples back to the parameters of one candidate (the
+ * field of orc_synth_raw): given gA, gE, gEd = dJ/d(samples) ([2][ld]),
+ * grad[4K] = dJ/d[a^E_x, a^phi_x, a^E_y, a^phi_y].  With theta = Omega_j t - Phi_j
+ * the samples depend on (E_{l,j}, Phi_{l,j}) through
+ *   A = -E_j (sin theta_k - sin theta_i)/Omega_j, E = E_j cos theta_k,
+ *   Ed = -E_j Omega_j sin theta_k,
+ * and E_{l,j}, Phi_{l,j} are the B-spline sums of Eqs. (coeff_basis_E/phi). */
+int orc_synth_vjp(const double *params, int K, int order, double wmin, double wmax, double T,
+                  int n_steps, int ld, const double *gA, const double *gE, const double *gEd,
+                  double *grad)
+{
+    int M = orc_mode_range(wmin, wmax, T, NULL);
+    if (M <= 0 || n_steps < 1 || ld < 2 * n_steps + 1 || !grad)
+        return ORC_ERR_ARG;
+    double *Om = malloc(sizeof(double) * M);
+    double *amp = malloc(sizeof(double) * 2 * M);
+    double *ph = malloc(sizeof(double) * 2 * M);
+    double *B = malloc(sizeof(double) * K);
+    int rc = orc_spectrum(params, K, order, wmin, wmax, T, Om, amp, ph);
+    if (rc < 0) {
+        free(Om), free(amp), free(ph), free(B);
+        return -rc;
+    }
+    for (int i = 0; i < 4 * K; i++)
+        grad[i] = 0.0;
+    double h = T / (2.0 * n_steps), ti = -0.5 * T;
+    for (int m = 0; m < M; m++) {
+        double W = Om[m];
+        orc_bspline_basis(K, order, wmin, wmax, W, B);
+        for (int l = 0; l < 2; l++) {
+            double Ej = amp[l * M + m], Pj = ph[l * M + m];
+            double si = sin(W * ti - Pj), ci = cos(W * ti - Pj);
+            double dE = 0.0, dP = 0.0;
+            for (int k = 0; k <= 2 * n_steps; k++) {
+                double t = ti + (double)k * h;
+                double sk = sin(W * t - Pj), ck = cos(W * t - Pj);
+                double ga = gA[l * ld + k], ge = gE[l * ld + k], gd = gEd[l * ld + k];
+                dE += ga * (-(sk - si) / W) + ge * ck + gd * (-W * sk);
+                dP += ga * (Ej * (ck - ci) / W) + ge * (Ej * sk) + gd * (Ej * W * ck);
+            }
+            for (int i = 0; i < K; i++) {
+                grad[2 * l * K + i] += B[i] * dE;
+                grad[(2 * l + 1) * K + i] += B[i] * dP;
+            }
+        }
+    }
+    free(Om), free(amp), free(ph), free(B);
     return ORC_OK;
 }
 
