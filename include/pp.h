@@ -402,6 +402,91 @@ const char *pp_last_error(void);
 /* Library version, major * 10000 + minor * 100 + patch. */
 int pp_version(void);
 
+/* ---- Local search of Sec. IV.A: augmented Lagrangian, BFGS, multistart ----
+ * Maximise J subject to C = U_const - U = 0 by minimising
+ *   L = -J - lambda C + C^2 / (2 mu)
+ * with BFGS (Nocedal & Wright Algorithm 6.1; inverse update Eq. 6.17, first-step
+ * scaling Eq. 6.20) and a strong-Wolfe line search (their Algorithms 3.5 and
+ * 3.6: c1 = 1e-4, c2 = 0.9, first trial step min(1, 1/|grad L|) on the first
+ * iteration of each inner minimisation and 1 after it, doubling while
+ * bracketing up to 1e3, 20 bracketing and 30 zoom evaluations, cubic
+ * interpolation kept inside the middle 80% of the bracket, else bisection);
+ * after each inner minimisation lambda <- lambda - C / mu and mu <- xi mu
+ * (steps 2-4), until |C| <= ctol or `outer` inner minimisations have run.
+ * BFGS restarts from the identity at every inner minimisation and whenever
+ * -H grad L is not a descent direction; updates with y.s <= 0 are skipped. */
+typedef struct {
+    double mu0;       /* initial penalty parameter, > 0 */
+    double xi;        /* penalty factor per outer iteration, 0 < xi < 1 */
+    int32_t outer;    /* maximum inner minimisations, >= 1 */
+    int32_t max_iter; /* maximum BFGS iterations per inner minimisation */
+    double gtol;      /* an inner minimisation stops when max |grad L| <= gtol */
+    double ctol;      /* the search stops when |C| <= ctol */
+} pp_al_options;
+
+/* Batched objective for pp_al_search: for the `count` host points x[count][n]
+ * fill J[count], gJ[count][n], C[count], gC[count][n] (host).  Returns PP_OK or
+ * a pp_status code, which ends the search with that code. */
+typedef int (*pp_objective_fn)(void *ctx, int32_t count, const double *x, double *J, double *gJ,
+                               double *C, double *gC);
+
+/* Multistart augmented-Lagrangian search (step 5) on the host: all nstart
+ * starts x[nstart][n] (host, overwritten with the results) advance in lockstep
+ * and every round evaluates the pending points of all active starts with one
+ * call of fn.  Per start (each may be NULL): J_out, C_out at the result,
+ * lam_out the final multiplier, evals_out the objective evaluations,
+ * outer_out the inner minimisations run, status_out 0 = |C| <= ctol reached,
+ * 1 = `outer` exhausted.  Each start's iterates do not depend on the others. */
+int pp_al_search(int32_t n, int32_t nstart, double *x, pp_objective_fn fn, void *ctx,
+                 const pp_al_options *opt, double *J_out, double *C_out, double *lam_out,
+                 int32_t *evals_out, int32_t *outer_out, int32_t *status_out);
+
+/* ---- The 6-component quantum kinetic equation and its adjoint (Sec. II.B,
+ * Eqs. (qke), (matrix); Sec. IV.A, Eqs. (eom2), (adj), (grad)) ----
+ *
+ * pp_synth_field_raw: the field of Eq. (field) with g = 1 WITHOUT the DE
+ *   renormalisation (the local search keeps the fluence through its penalty):
+ *   A, E and Ed = dE/dt ([ncand][2][ld] device FP64, half-step grid as in
+ *   pp_synth_field; E, Ed and U may be NULL); U[c] = the fluence of Eq.
+ *   (energy) over one period, (T/2) sum_{l,j} E_{l,j}^2.  spec->fluence is not used.
+ * pp_synth_vjp: the chain rule of that synthesis.  g ([ncand][6][ldg] device)
+ *   holds dJ/d(samples) in the order A_x, A_y, E_x, E_y, Ed_x, Ed_y; grad
+ *   ([ncand][4K] device) receives dJ/dparams.  U and dU ([ncand][4K]) receive the
+ *   fluence and its gradient.  Each output may be NULL (g is read only for grad).
+ * pp_qke_pair_number: J[c] = sum_p w(p) f(p), f = 1 - chi_1(t_f) by classical
+ *   RK4 of the QKE on the half-step grid of (A, E, Ed) ([ncand][2][ld] device),
+ *   chi(t_i) = e_1; n_p as in pp_pair_number (may be NULL).  FP64 or FP32 state
+ *   (PP_FP32 and PP_FP32_FAST are the same here); J and the sums are FP64.
+ * pp_qke_sample_gradient: J[c] and g[c][6][ldg] = dJ/d(every sample of A_x, A_y,
+ *   E_x, E_y, Ed_x, Ed_y): the exact derivative of the discrete J, computed by
+ *   the adjoint of the RK4 map (adjoint final value lambda_1 = -1 of Eq. (adj)
+ *   scaled by w(p), the inner product of Eq. (grad) taken stage by stage), the
+ *   forward states kept at every 4th (FP64) or 8th (FP32) step and recomputed.
+ *   Candidates are processed in chunks that keep the work buffers near 8 GiB.
+ * pp_qke_gradient: params -> raw field -> J[c], gJ[c][4K] = dJ/dparams (may be
+ *   NULL: J only), U[c] and dU[c][4K] (each may be NULL); all device pointers.
+ * pp_local_search: the multistart search of pp_al_search with this objective:
+ *   maximise J subject to U = U_const from the host starts x[nstart][4K]
+ *   (overwritten with the results); each round evaluates all pending points
+ *   of all starts with one pp_qke_gradient call on `stream`.
+ * Errors: PP_ERR_INVALID_ARG for bad sizes, pointers or options, PP_ERR_CUDA
+ * for a failed launch or allocation; device flags surface through pp_sync_status. */
+int pp_synth_field_raw(const double *params, int32_t ncand, const pp_field_spec *spec, double *A, double *E,
+                       double *Ed, int32_t ld, double *U, void *stream);
+int pp_synth_vjp(const double *params, int32_t ncand, const pp_field_spec *spec, const double *g, int32_t ldg,
+                 double *grad, double *U, double *dU, void *stream);
+int pp_qke_pair_number(const double *A, const double *E, const double *Ed, int32_t ncand, int32_t ld,
+                       int32_t n_steps, double dt, const pp_grid *grid, int32_t precision, double *N, double *n_p,
+                       void *stream);
+int pp_qke_sample_gradient(const double *A, const double *E, const double *Ed, int32_t ncand, int32_t ld,
+                           int32_t n_steps, double dt, const pp_grid *grid, int32_t precision, double *J, double *g,
+                           int32_t ldg, void *stream);
+int pp_qke_gradient(const double *params, int32_t ncand, const pp_field_spec *spec, const pp_grid *grid,
+                    int32_t precision, double *J, double *gJ, double *U, double *dU, void *stream);
+int pp_local_search(double *x, int32_t nstart, const pp_field_spec *spec, const pp_grid *grid, int32_t precision,
+                    double U_const, const pp_al_options *opt, double *J_out, double *C_out, double *lam_out,
+                    int32_t *evals_out, int32_t *outer_out, int32_t *status_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

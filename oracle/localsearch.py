@@ -27,6 +27,18 @@ ALPHA_MAX = 1e3    # largest trial step
 GROW = 2.0         # step growth while bracketing
 
 
+def _dot(a, b):
+    """Sum of a_i b_i in index order (one rounding per product and per sum)."""
+    s = 0.0
+    for i in range(len(a)):
+        s += float(a[i]) * float(b[i])
+    return s
+
+
+def _matvec(H, v):
+    return np.array([_dot(H[i], v) for i in range(H.shape[0])])
+
+
 def _cubic_min(a, fa, ga, b, fb, gb):
     """Minimiser of the cubic interpolating (a, fa, ga), (b, fb, gb) (Eq. 3.59),
     or None when it does not exist."""
@@ -112,18 +124,18 @@ def bfgs(fg, x0, gtol=1e-6, max_iter=200):
     for k in range(max_iter):
         if np.max(np.abs(g)) <= gtol:
             return dict(x=x, f=f, g=g, aux=aux, iters=k, evals=evals, status="converged")
-        p = -(H @ g)
-        gp = float(p @ g)
+        p = -_matvec(H, g)
+        gp = _dot(p, g)
         if not gp < 0.0:  # not a descent direction: restart from the gradient
             H = np.eye(n)
             p = -g
-            gp = float(p @ g)
-        alpha1 = min(1.0, 1.0 / math.sqrt(float(g @ g))) if first else 1.0
+            gp = _dot(p, g)
+        alpha1 = min(1.0, 1.0 / math.sqrt(_dot(g, g))) if first else 1.0
 
         def phi(a, x=x, p=p):
             xa = x + a * p
             fa, ga, auxa = fg(xa)
-            return fa, float(ga @ p), (xa, ga, auxa)
+            return fa, _dot(ga, p), (xa, ga, auxa)
         a, fa, pay, ne, ok = line_search(phi, f, gp, alpha1)
         evals += ne
         if pay is None:
@@ -131,14 +143,14 @@ def bfgs(fg, x0, gtol=1e-6, max_iter=200):
         xn, gn, auxn = pay
         s = xn - x
         y = gn - g
-        ys = float(y @ s)
+        ys = _dot(y, s)
         if ys > 0.0:
             if first:
-                H = (ys / float(y @ y)) * np.eye(n)  # Eq. 6.20
+                H = (ys / _dot(y, y)) * np.eye(n)  # Eq. 6.20
             rho = 1.0 / ys
-            Hy = H @ y
+            Hy = _matvec(H, y)
             H = (H - rho * (np.outer(s, Hy) + np.outer(Hy, s))
-                 + (rho * rho * float(y @ Hy) + rho) * np.outer(s, s))  # Eq. 6.17
+                 + (rho * rho * _dot(y, Hy) + rho) * np.outer(s, s))  # Eq. 6.17
         first = False
         x, f, g, aux = xn, fa, gn, auxn
         if not ok:

@@ -47,7 +47,21 @@ EXPORTS = ("pp_synth_field", "pp_pair_number", "pp_de_propose", "pp_de_select", 
            "pp_gemm_bf16", "pp_mlp_create", "pp_mlp_destroy", "pp_mlp_num_params",
            "pp_mlp_set_params", "pp_mlp_get_params", "pp_mlp_forward", "pp_mlp_loss_grad",
            "pp_mlp_train_step", "pp_mlp_features", "pp_de_screened_step", "pp_mlp_fit",
-           "pp_mlp_log_targets", "pp_mlp_init")
+           "pp_mlp_log_targets", "pp_mlp_init", "pp_al_search", "pp_synth_field_raw",
+           "pp_synth_vjp", "pp_qke_pair_number", "pp_qke_sample_gradient", "pp_qke_gradient",
+           "pp_local_search")
+
+
+class ALOptions(ctypes.Structure):
+    """pp_al_options."""
+    _fields_ = [("mu0", ctypes.c_double), ("xi", ctypes.c_double), ("outer", ctypes.c_int32),
+                ("max_iter", ctypes.c_int32), ("gtol", ctypes.c_double), ("ctol", ctypes.c_double)]
+
+
+ObjectiveFn = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int32,
+                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(ctypes.c_double))
 
 
 class PPError(RuntimeError):
@@ -137,6 +151,21 @@ def lib():
                                  _vp, _vp]
         L.pp_mlp_log_targets.argtypes = [_vp, _i32, _d, _d, _d, _vp, _vp]
         L.pp_mlp_init.argtypes = [_vp, _u64, _vp]
+        L.pp_synth_field_raw.argtypes = [_vp, _i32, ctypes.POINTER(FieldSpec), _vp, _vp, _vp, _i32,
+                                         _vp, _vp]
+        L.pp_synth_vjp.argtypes = [_vp, _i32, ctypes.POINTER(FieldSpec), _vp, _i32, _vp, _vp, _vp,
+                                   _vp]
+        L.pp_qke_pair_number.argtypes = [_vp, _vp, _vp, _i32, _i32, _i32, _d, ctypes.POINTER(Grid),
+                                         _i32, _vp, _vp, _vp]
+        L.pp_qke_sample_gradient.argtypes = [_vp, _vp, _vp, _i32, _i32, _i32, _d,
+                                             ctypes.POINTER(Grid), _i32, _vp, _vp, _i32, _vp]
+        L.pp_qke_gradient.argtypes = [_vp, _i32, ctypes.POINTER(FieldSpec), ctypes.POINTER(Grid),
+                                      _i32, _vp, _vp, _vp, _vp, _vp]
+        L.pp_local_search.argtypes = [_vp, _i32, ctypes.POINTER(FieldSpec), ctypes.POINTER(Grid),
+                                      _i32, _d, ctypes.POINTER(ALOptions), _vp, _vp, _vp, _vp, _vp,
+                                      _vp, _vp]
+        L.pp_al_search.argtypes = [_i32, _i32, _vp, ObjectiveFn, _vp, ctypes.POINTER(ALOptions),
+                                   _vp, _vp, _vp, _vp, _vp, _vp]
         L.pp_batch_de_run.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _d, _d, _u64, _i32, _vp]
         _lib = L
     return _lib
@@ -489,3 +518,127 @@ def set_wait_limit(limit):
 
 def set_skip_copies(skip):
     return lib().pp_set_skip_copies(int(skip))
+
+
+def al_search(x0, fn, mu0=1.0, xi=0.5, outer=10, max_iter=200, gtol=1e-6, ctol=1e-8):
+    """pp_al_search with a Python objective fn(X[count, n]) -> (J, gJ, C, gC) (numpy).
+
+    Returns dict(x, J, C, lam, evals, outer, status) with one row / entry per start."""
+    import numpy as np
+    x = np.array(x0, dtype=np.float64, copy=True, ndmin=2)
+    nstart, n = x.shape
+    err = []
+
+    def cb(ctx, count, xp, Jp, gJp, Cp, gCp):
+        try:
+            X = np.ctypeslib.as_array(xp, shape=(count, n)).copy()
+            J, gJ, C, gC = fn(X)
+            np.ctypeslib.as_array(Jp, shape=(count,))[:] = J
+            np.ctypeslib.as_array(gJp, shape=(count, n))[:] = gJ
+            np.ctypeslib.as_array(Cp, shape=(count,))[:] = C
+            np.ctypeslib.as_array(gCp, shape=(count, n))[:] = gC
+            return 0
+        except Exception as e:  # noqa: BLE001 -- reported after the search returns
+            err.append(e)
+            return PP_ERR_INVALID_ARG
+    opt = ALOptions(mu0, xi, outer, max_iter, gtol, ctol)
+    J, C, lam = np.zeros(nstart), np.zeros(nstart), np.zeros(nstart)
+    ev, ou, stt = (np.zeros(nstart, dtype=np.int32) for _ in range(3))
+    f = ObjectiveFn(cb)
+    rc = lib().pp_al_search(n, nstart, x.ctypes.data, f, None, ctypes.byref(opt), J.ctypes.data,
+                            C.ctypes.data, lam.ctypes.data, ev.ctypes.data, ou.ctypes.data,
+                            stt.ctypes.data)
+    if err:
+        raise err[0]
+    _check(rc)
+    return dict(x=x, J=J, C=C, lam=lam, evals=ev, outer=ou, status=stt)
+
+
+# ----------------------------------------------------------------------------- QKE local search
+
+
+def synth_field_raw(params, spec, stream=None):
+    """pp_synth_field_raw: (A, E, Ed [ncand, 2, 2n+1], U [ncand]) without renormalisation."""
+    import torch
+    sp = _spec(dict(spec, fluence=spec.get("fluence", 1.0)))
+    ncand, ld = params.shape[0], 2 * sp.n_steps + 1
+    A, E, Ed = (torch.empty((ncand, 2, ld), dtype=torch.float64, device=params.device)
+                for _ in range(3))
+    U = torch.empty(ncand, dtype=torch.float64, device=params.device)
+    _check(lib().pp_synth_field_raw(_ptr(params), ncand, ctypes.byref(sp), _ptr(A), _ptr(E),
+                                    _ptr(Ed), ld, _ptr(U), _stream(stream)))
+    return A, E, Ed, U
+
+
+def synth_vjp(params, spec, g, stream=None):
+    """pp_synth_vjp: g [ncand, 6, ldg] = dJ/d(samples) -> (grad [ncand, 4K], U, dU)."""
+    import torch
+    sp = _spec(dict(spec, fluence=spec.get("fluence", 1.0)))
+    ncand = params.shape[0]
+    grad, dU = (torch.empty((ncand, 4 * sp.K), dtype=torch.float64, device=params.device)
+                for _ in range(2))
+    U = torch.empty(ncand, dtype=torch.float64, device=params.device)
+    _check(lib().pp_synth_vjp(_ptr(params), ncand, ctypes.byref(sp), _ptr(g), g.shape[-1],
+                              _ptr(grad), _ptr(U), _ptr(dU), _stream(stream)))
+    return grad, U, dU
+
+
+def qke_pair_number(A, E, Ed, dt, grid, precision="fp64", n_steps=None, want_n=False, stream=None):
+    """pp_qke_pair_number: J [ncand] (and f [ncand, nz, ny, nx])."""
+    import torch
+    g = _grid(grid)
+    ncand, _, ld = A.shape
+    ns = n_steps if n_steps is not None else (ld - 1) // 2
+    J = torch.empty(ncand, dtype=torch.float64, device=A.device)
+    n = (torch.empty((ncand, g.nz, g.ny, g.nx), dtype=torch.float64, device=A.device)
+         if want_n else None)
+    _check(lib().pp_qke_pair_number(_ptr(A), _ptr(E), _ptr(Ed), ncand, ld, ns, float(dt),
+                                    ctypes.byref(g), PRECISIONS[precision], _ptr(J), _ptr(n),
+                                    _stream(stream)))
+    return J, n
+
+
+def qke_sample_gradient(A, E, Ed, dt, grid, precision="fp64", n_steps=None, stream=None):
+    """pp_qke_sample_gradient: (J [ncand], g [ncand, 6, 2n+1]) with g = dJ/d(samples)."""
+    import torch
+    gr = _grid(grid)
+    ncand, _, ld = A.shape
+    ns = n_steps if n_steps is not None else (ld - 1) // 2
+    J = torch.empty(ncand, dtype=torch.float64, device=A.device)
+    g = torch.empty((ncand, 6, 2 * ns + 1), dtype=torch.float64, device=A.device)
+    _check(lib().pp_qke_sample_gradient(_ptr(A), _ptr(E), _ptr(Ed), ncand, ld, ns, float(dt),
+                                        ctypes.byref(gr), PRECISIONS[precision], _ptr(J), _ptr(g),
+                                        g.shape[-1], _stream(stream)))
+    return J, g
+
+
+def qke_gradient(params, spec, grid, precision="fp64", want_grad=True, stream=None):
+    """pp_qke_gradient: (J, gJ, U, dU) for params [ncand, 4K] (gJ None unless want_grad)."""
+    import torch
+    sp = _spec(dict(spec, fluence=spec.get("fluence", 1.0)))
+    ncand = params.shape[0]
+    J, U = (torch.empty(ncand, dtype=torch.float64, device=params.device) for _ in range(2))
+    gJ = (torch.empty((ncand, 4 * sp.K), dtype=torch.float64, device=params.device)
+          if want_grad else None)
+    dU = torch.empty((ncand, 4 * sp.K), dtype=torch.float64, device=params.device)
+    _check(lib().pp_qke_gradient(_ptr(params), ncand, ctypes.byref(sp), ctypes.byref(_grid(grid)),
+                                 PRECISIONS[precision], _ptr(J), _ptr(gJ), _ptr(U), _ptr(dU),
+                                 _stream(stream)))
+    return J, gJ, U, dU
+
+
+def local_search(x0, spec, grid, U_const, precision="fp64", mu0=1.0, xi=0.5, outer=10,
+                 max_iter=200, gtol=1e-6, ctol=1e-8, stream=None):
+    """pp_local_search from host starts x0 [nstart, 4K]; returns dict like al_search."""
+    import numpy as np
+    x = np.array(x0, dtype=np.float64, copy=True, ndmin=2)
+    nstart = x.shape[0]
+    sp = _spec(dict(spec, fluence=spec.get("fluence", 1.0)))
+    opt = ALOptions(mu0, xi, outer, max_iter, gtol, ctol)
+    J, C, lam = np.zeros(nstart), np.zeros(nstart), np.zeros(nstart)
+    ev, ou, stt = (np.zeros(nstart, dtype=np.int32) for _ in range(3))
+    _check(lib().pp_local_search(x.ctypes.data, nstart, ctypes.byref(sp), ctypes.byref(_grid(grid)),
+                                 PRECISIONS[precision], float(U_const), ctypes.byref(opt),
+                                 J.ctypes.data, C.ctypes.data, lam.ctypes.data, ev.ctypes.data,
+                                 ou.ctypes.data, stt.ctypes.data, _stream(stream)))
+    return dict(x=x, J=J, C=C, lam=lam, evals=ev, outer=ou, status=stt)

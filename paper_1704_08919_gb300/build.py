@@ -41,7 +41,9 @@ def build(force=False, verbose_ptxas=False):
     objs = [os.path.join(OUT_DIR, os.path.basename(s)[:-3] + ".o") for s in srcs]
     # -fmad=false: only explicit fma() calls fuse, so every kernel instantiation (any
     # launch configuration) rounds exactly as the source is written.
+    # -ffp-contract=off: the host code (the optimiser) rounds as written too.
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC",
+                    "-Xcompiler", "-ffp-contract=off",
                     "-I", INCLUDE, "-I", CSRC, "--expt-relaxed-constexpr"]
     if verbose_ptxas:
         flags += ["-Xptxas", "-v"]

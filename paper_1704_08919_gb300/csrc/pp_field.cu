@@ -64,7 +64,7 @@ __device__ void bspline_basis(int K, int order, double wmin, double wmax, double
 __global__ void spectrum_kernel(const double *__restrict__ params, int K, int order, double wmin,
                                 double wmax, double T, double U, int j0, int M,
                                 double2 *__restrict__ coef, double *__restrict__ scale_out,
-                                unsigned int *__restrict__ status)
+                                unsigned int *__restrict__ status, int normalize)
 {
     __shared__ double red[256];
     const int c = blockIdx.x;
@@ -99,12 +99,13 @@ __global__ void spectrum_kernel(const double *__restrict__ params, int K, int or
         __syncthreads();
     }
     const double Uraw = 0.5 * T * red[0];
-    const double s = Uraw > 0.0 ? sqrt(U / Uraw) : 0.0;
+    // normalize = 0: the un-normalised field (s = 1) and scale_out receives its fluence
+    const double s = normalize ? (Uraw > 0.0 ? sqrt(U / Uraw) : 0.0) : 1.0;
     if (threadIdx.x == 0) {
-        if (!(Uraw > 0.0))
+        if (normalize && !(Uraw > 0.0))
             pp_flag(status, PP_FLAG_DEGENERATE);
         if (scale_out)
-            scale_out[c] = s;
+            scale_out[c] = normalize ? s : Uraw;
     }
     for (int q = threadIdx.x; q < 4 * M; q += blockDim.x) {
         double2 v = coef[(size_t)c * 4 * M + q];
@@ -114,7 +115,8 @@ __global__ void spectrum_kernel(const double *__restrict__ params, int K, int or
 
 // Samples: grid (ceil(nsamp / 256), ncand, 2 polarisations).
 __global__ void samples_kernel(const double2 *__restrict__ coef, int M, int j0, int n_steps,
-                               int ld, double *__restrict__ A, double *__restrict__ E)
+                               int ld, double *__restrict__ A, double *__restrict__ E, double dw,
+                               double *__restrict__ Ed)
 {
     extern __shared__ double2 sc[];  // [2M]: C then D
     const int c = blockIdx.y, l = blockIdx.z;
@@ -132,7 +134,7 @@ __global__ void samples_kernel(const double2 *__restrict__ coef, int M, int j0, 
     sincospi((double)(k % two_n) / (double)n_steps, &zs, &zc);
     sincospi((double)(((long long)k * j0) % two_n) / (double)n_steps, &js, &jc);
     // Horner: sum_{m=0}^{M-1} X_m z^m
-    double cr = 0.0, ci = 0.0, dr = 0.0, di = 0.0;
+    double cr = 0.0, ci = 0.0, dr = 0.0, di = 0.0, gr = 0.0, gi = 0.0;
     double d0r = 0.0, d0i = 0.0;  // sum of D_j (the z = 1 value)
     for (int m = M - 1; m >= 0; --m) {
         const double2 C = sc[m], D = sc[M + m];
@@ -144,6 +146,12 @@ __global__ void samples_kernel(const double2 *__restrict__ coef, int M, int j0, 
         dr = tr;
         d0r += D.x;
         d0i += D.y;
+        if (Ed) {  // dE/dt: coefficients i Omega_j C_j
+            const double W = (double)(j0 + m) * dw;
+            tr = gr * zc - gi * zs - W * C.y;
+            gi = gr * zs + gi * zc + W * C.x;
+            gr = tr;
+        }
     }
     // multiply by z^{j0}
     const double Cr = cr * jc - ci * js;
@@ -152,7 +160,118 @@ __global__ void samples_kernel(const double2 *__restrict__ coef, int M, int j0, 
     Arow[k] = -(Di - d0i);
     if (E)
         E[((size_t)c * 2 + l) * ld + k] = Cr;
+    if (Ed)
+        Ed[((size_t)c * 2 + l) * ld + k] = gr * jc - gi * js;
     (void)d0r;
+}
+
+// ---- chain rule of the un-normalised synthesis (the local search's gradient):
+// with theta_k = Omega_j t_k - Phi_j = pi j k / n - (j pi + Phi_j), the samples
+// depend on (E_j, Phi_j) through A = -E_j (sin theta_k - sin theta_0) / Omega_j,
+// E = E_j cos theta_k, Ed = -E_j Omega_j sin theta_k.  One block per (mode j,
+// polarisation l, candidate): dEP = (dJ/dE_j, dJ/dPhi_j) from dJ/d(samples)
+// g[c][q][k], q = (A_x, A_y, E_x, E_y, Ed_x, Ed_y).
+constexpr int kVjpThreads = 256;
+__global__ void __launch_bounds__(kVjpThreads) vjp_modes_kernel(
+    const double *__restrict__ params, int K, int order, double wmin, double wmax, double T, int j0,
+    int n_steps, const double *__restrict__ g, int ldg, double2 *__restrict__ dEP)
+{
+    __shared__ double sh[3];
+    __shared__ double red[2][kVjpThreads];
+    const int m = blockIdx.x, l = blockIdx.y, c = blockIdx.z, M = gridDim.x;
+    const int j = j0 + m;
+    const double W = (double)j * (2.0 * M_PI / T);
+    if (threadIdx.x == 0) {
+        double B[kMaxK];
+        bspline_basis(K, order, wmin, wmax, W, B);
+        const double *prm = params + (size_t)c * 4 * K;
+        double e = 0.0, ph = 0.0;
+        for (int i = 0; i < K; ++i) {
+            e += prm[(2 * l) * K + i] * B[i];
+            ph += prm[(2 * l + 1) * K + i] * B[i];
+        }
+        double sn, cs;
+        sincos(ph, &sn, &cs);
+        const double sg = (j & 1) ? -1.0 : 1.0;
+        sh[0] = e;
+        sh[1] = sg * cs;  // cos(j pi + Phi)
+        sh[2] = sg * sn;  // sin(j pi + Phi)
+    }
+    __syncthreads();
+    const double Ej = sh[0], cb = sh[1], sb = sh[2];
+    const double si = -sb, ci = cb;  // theta_0 = -(j pi + Phi)
+    const double *gA = g + ((size_t)c * 6 + l) * ldg;
+    const double *gE = g + ((size_t)c * 6 + 2 + l) * ldg;
+    const double *gD = g + ((size_t)c * 6 + 4 + l) * ldg;
+    const long long two_n = 2ll * n_steps;
+    double dE = 0.0, dP = 0.0;
+    for (int k = threadIdx.x; k <= 2 * n_steps; k += kVjpThreads) {
+        double sa, ca;
+        sincospi((double)(((long long)j * k) % two_n) / (double)n_steps, &sa, &ca);
+        const double ck = ca * cb + sa * sb, sk = sa * cb - ca * sb;
+        const double ga = gA[k], ge = gE[k], gd = gD[k];
+        dE += ga * (-(sk - si) / W) + ge * ck + gd * (-W * sk);
+        dP += ga * (Ej * (ck - ci) / W) + ge * (Ej * sk) + gd * (Ej * W * ck);
+    }
+    red[0][threadIdx.x] = dE;
+    red[1][threadIdx.x] = dP;
+    __syncthreads();
+    for (int h = kVjpThreads / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + h];
+            red[1][threadIdx.x] += red[1][threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        dEP[((size_t)c * 2 + l) * M + m] = make_double2(red[0][0], red[1][0]);
+}
+
+// One block per candidate, one thread per parameter o = (2l + kind) K + i:
+// grad_o = sum_j B_i(Omega_j) dEP[l][j].{E or Phi}; the un-normalised fluence
+// U = (T/2) sum E_{l,j}^2 and dU_o = T sum_j E_{l,j} B_i(Omega_j) (0 for phases).
+__global__ void vjp_params_kernel(const double *__restrict__ params, int K, int order, double wmin,
+                                  double wmax, double T, int j0, int M, const double2 *__restrict__ dEP,
+                                  double *__restrict__ grad, double *__restrict__ U_out,
+                                  double *__restrict__ dU)
+{
+    const int c = blockIdx.x;
+    const double *prm = params + (size_t)c * 4 * K;
+    const double dw = 2.0 * M_PI / T;
+    for (int o = threadIdx.x; o < 4 * K; o += blockDim.x) {
+        const int l = o / (2 * K), kind = (o / K) % 2, i = o % K;
+        double acc = 0.0, accU = 0.0;
+        for (int m = 0; m < M; ++m) {
+            double B[kMaxK];
+            bspline_basis(K, order, wmin, wmax, (double)(j0 + m) * dw, B);
+            const double2 v = dEP[((size_t)c * 2 + l) * M + m];
+            acc += B[i] * (kind ? v.y : v.x);
+            if (!kind) {
+                double e = 0.0;
+                for (int q = 0; q < K; ++q)
+                    e += prm[(2 * l) * K + q] * B[q];
+                accU += e * B[i];
+            }
+        }
+        if (grad)
+            grad[(size_t)c * 4 * K + o] = acc;
+        if (dU)
+            dU[(size_t)c * 4 * K + o] = kind ? 0.0 : T * accU;
+    }
+    if (threadIdx.x == 0 && U_out) {
+        double u = 0.0;
+        for (int m = 0; m < M; ++m) {
+            double B[kMaxK];
+            bspline_basis(K, order, wmin, wmax, (double)(j0 + m) * dw, B);
+            for (int l = 0; l < 2; ++l) {
+                double e = 0.0;
+                for (int q = 0; q < K; ++q)
+                    e += prm[(2 * l) * K + q] * B[q];
+                u += e * e;
+            }
+        }
+        U_out[c] = 0.5 * T * u;
+    }
 }
 
 // ---- batches of candidates with their own pulse length and step count (same K,
@@ -298,15 +417,24 @@ int launch_synth_batch(const double *params, int ncand, const pp_field_spec *spe
     return PP_OK;
 }
 
-int launch_synth_field(const double *params, int ncand, const pp_field_spec *spec, double *A, int ld,
-                       double *E, double *scale, cudaStream_t stream)
+namespace {
+int mode_band(const pp_field_spec *spec, int *j0_out)
 {
     const double dw = 2.0 * M_PI / spec->T;
     int j0 = (int)ceil(spec->w_min / dw - 1e-12);
     if (j0 < 1)
         j0 = 1;
     const int j1 = (int)floor(spec->w_max / dw + 1e-12);
-    const int M = j1 - j0 + 1;
+    *j0_out = j0;
+    return j1 - j0 + 1;
+}
+}  // namespace
+
+int launch_synth(const double *params, int ncand, const pp_field_spec *spec, int normalize, double *A,
+                 int ld, double *E, double *Ed, double *scale, cudaStream_t stream)
+{
+    int j0;
+    const int M = mode_band(spec, &j0);
     void *coef = nullptr;
     int rc = scratch(SCR_COEF, (size_t)ncand * 4 * M * sizeof(double2), &coef);
     if (rc)
@@ -317,15 +445,42 @@ int launch_synth_field(const double *params, int ncand, const pp_field_spec *spe
     if (!status)
         return fail(PP_ERR_CUDA, "status word unavailable");
     spectrum_kernel<<<ncand, 128, 0, stream>>>(params, spec->K, spec->order, spec->w_min, spec->w_max,
-                                               spec->T, spec->fluence, j0, M, (double2 *)coef, scale, status);
+                                               spec->T, spec->fluence, j0, M, (double2 *)coef, scale, status,
+                                               normalize);
     const int nsamp = 2 * spec->n_steps + 1;
     dim3 g((nsamp + 255) / 256, ncand, 2);
     samples_kernel<<<g, 256, 2 * M * sizeof(double2), stream>>>((const double2 *)coef, M, j0,
-                                                                spec->n_steps, ld, A, E);
+                                                                spec->n_steps, ld, A, E,
+                                                                2.0 * M_PI / spec->T, Ed);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return cuda_fail(e, "synthesis kernel launch");
     return PP_OK;
+}
+
+int launch_synth_field(const double *params, int ncand, const pp_field_spec *spec, double *A, int ld,
+                       double *E, double *scale, cudaStream_t stream)
+{
+    return launch_synth(params, ncand, spec, 1, A, ld, E, nullptr, scale, stream);
+}
+
+int launch_synth_vjp(const double *params, int ncand, const pp_field_spec *spec, const double *g, int ldg,
+                     double *grad, double *U, double *dU, cudaStream_t stream)
+{
+    int j0;
+    const int M = mode_band(spec, &j0);
+    void *dep = nullptr;
+    int rc = scratch(SCR_VJP, (size_t)ncand * 2 * M * sizeof(double2), &dep);
+    if (rc || ncand == 0)
+        return rc;
+    if (grad)
+        vjp_modes_kernel<<<dim3(M, 2, ncand), kVjpThreads, 0, stream>>>(params, spec->K, spec->order,
+                                                                        spec->w_min, spec->w_max, spec->T, j0,
+                                                                        spec->n_steps, g, ldg, (double2 *)dep);
+    vjp_params_kernel<<<ncand, 128, 0, stream>>>(params, spec->K, spec->order, spec->w_min, spec->w_max, spec->T,
+                                                 j0, M, (const double2 *)dep, grad, U, dU);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PP_OK : cuda_fail(e, "synthesis chain-rule launch");
 }
 
 }  // namespace pp

@@ -29,7 +29,8 @@ void clear_error();
 // synchronises the device, frees the old buffer and allocates a new one.
 enum ScratchSlot {
     SCR_TABLE = 0, SCR_PARTIAL, SCR_A, SCR_TRIAL, SCR_TFIT, SCR_COEF,
-    SCR_SCREEN_PROPS, SCR_SCREEN_X, SCR_SCREEN_Y, SCR_SCREEN_KEPT, SCR_NSLOTS
+    SCR_SCREEN_PROPS, SCR_SCREEN_X, SCR_SCREEN_Y, SCR_SCREEN_KEPT,
+    SCR_VJP, SCR_QKE_TABLE, SCR_QKE_CKPT, SCR_QKE_PART, SCR_QKE_G, SCR_QKE_FIELD, SCR_QKE_X, SCR_NSLOTS
 };
 int scratch(int slot, size_t bytes, void **ptr);
 
@@ -70,6 +71,22 @@ void clear_tuning();
 // Field synthesis launch without argument re-validation (pp_field.cu).
 int launch_synth_field(const double *params, int ncand, const pp_field_spec *spec, double *A,
                        int ld, double *E, double *scale, cudaStream_t stream);
+
+// Synthesis with a choice of renormalisation (normalize = 0: s = 1 and `scale`
+// receives the fluence) and the time derivative Ed (may be NULL) (pp_field.cu).
+int launch_synth(const double *params, int ncand, const pp_field_spec *spec, int normalize, double *A,
+                 int ld, double *E, double *Ed, double *scale, cudaStream_t stream);
+// Chain rule of the un-normalised synthesis: g[c][6][ldg] = dJ/d(A_x, A_y, E_x, E_y,
+// Ed_x, Ed_y samples) -> grad[c][4K] (may be NULL: then g is not read); U[c], dU[c][4K]
+// the fluence and its gradient (each may be NULL).
+int launch_synth_vjp(const double *params, int ncand, const pp_field_spec *spec, const double *g, int ldg,
+                     double *grad, double *U, double *dU, cudaStream_t stream);
+
+// QKE forward and adjoint (pp_qke.cu).
+int launch_qke_pair_number(const double *A, const double *E, const double *Ed, int ncand, int ld, int n_steps,
+                           double dt, const pp_grid *g, int precision, double *N, double *n_p, cudaStream_t st);
+int launch_qke_gradient(const double *A, const double *E, const double *Ed, int ncand, int ld, int n_steps,
+                        double dt, const pp_grid *g, int precision, double *J, double *gs, int ldg, cudaStream_t st);
 
 // DE launches (pp_de.cu).
 int launch_de_propose(const double *pop, int NP, int D, const double *lo, const double *hi,

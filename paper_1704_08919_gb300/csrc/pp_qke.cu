@@ -1,0 +1,797 @@
+// pp_qke.cu -- the 6-component quantum kinetic equation of Sec. II.B of
+// arXiv 1704.08919 (Eqs. (qke), (matrix); f = 1 - chi_1) and its adjoint
+// (Sec. IV.A, Eqs. (eom2), (adj), (grad)): the pair density of every momentum
+// mode and the gradient of J = sum_p w(p) f(p) with respect to every sample of
+// A, E and dE/dt, for the local search.
+//
+// Per mode, chi' = N(t) chi with the skew-symmetric
+//   N = Q S_Q + R S_R + 2 omega S_W,  omega = sqrt(1 + P^2),  P = p - A(t),
+//   X = omega^2 |E|^2 - (E.P)^2,  Q = sqrt(X) / omega^2,
+//   R = eps_perp omega (E x Ed)_z / X      (Q = R = 0 where X = 0),
+// integrated by classical RK4 on the half-step sample grid (N at t_n, t_{n+1/2},
+// t_{n+1}).  The state is carried as delta = chi - e_1 (delta(t_i) = 0), the same
+// RK4 iterates, so that f = -delta_1 keeps its relative precision when f is small.
+//
+// The gradient is the exact adjoint of the discrete forward map: the adjoint
+// state (final value -w(p) e_1, i.e. lambda_1(t_f) = -1 of Eq. (adj) times the
+// quadrature weight) runs backwards through the transposed RK4 stages, and each
+// stage k = N y contributes kb (x) y to the adjoint of N, whose projections on
+// S_Q, S_R, S_W are the adjoints of Q, R, omega -- the inner product
+// <chi, grad N lambda> of Eq. (grad) taken stage by stage.  The forward states
+// are kept at every S-th step (checkpoints in HBM) and recomputed a segment at a
+// time into registers for the backward sweep.  Each sample's six sensitivities
+// are summed over the CTA's modes (warp shuffles, then warps in fixed order) into
+// a per-CTA row; a second kernel sums the rows in fixed order.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "pp_policies.cuh"
+
+namespace {
+
+constexpr int kQThreads = 256;
+constexpr int kQWarps = kQThreads / 32;
+
+// Mode-independent values of one sample: A, E, dE/dt, |E|^2, (E x Ed)_z.
+template <typename T>
+struct alignas(sizeof(T) * 8) QkeS {
+    T ax, ay, ex, ey, edx, edy, ee, cr;
+};
+
+template <typename T>
+struct Coef {
+    T Q, R, W2;  // W2 = 2 omega
+};
+
+template <typename T>
+__device__ __forceinline__ Coef<T> coef_at(const QkeS<T> &s, T px, T py, T pz2, T eperp)
+{
+    const T Px = px - s.ax, Py = py - s.ay;
+    const T w2 = ((Px * Px + Py * Py) + pz2) + T(1);
+    const T w = sqrt(w2);
+    const T EP = s.ex * Px + s.ey * Py;
+    const T X = w2 * s.ee - EP * EP;
+    Coef<T> c;
+    c.W2 = T(2) * w;
+    if (X > T(0)) {
+        c.Q = sqrt(X) / w2;
+        c.R = eperp * w * s.cr / X;
+    } else {
+        c.Q = T(0);
+        c.R = T(0);
+    }
+    return c;
+}
+
+// out = N (one e_1 + v)
+template <typename T>
+__device__ __forceinline__ void nmul(const Coef<T> &c, const T v[6], T one, T out[6])
+{
+    out[0] = -c.Q * v[1];
+    out[1] = c.Q * (one + v[0]) - c.W2 * v[2] + c.R * v[3];
+    out[2] = c.W2 * v[1] - c.R * v[4];
+    out[3] = -c.R * v[1] + c.W2 * v[4];
+    out[4] = c.R * v[2] - c.W2 * v[3] + c.Q * v[5];
+    out[5] = -c.Q * v[4];
+}
+
+// One RK4 step of delta: chi = e_1 + delta.
+template <typename T>
+__device__ __forceinline__ void rk4_step(T d[6], const Coef<T> &c0, const Coef<T> &ch, const Coef<T> &c1, T dt)
+{
+    const T hd = T(0.5) * dt, sx = dt / T(6);
+    T k1[6], k2[6], k3[6], k4[6], y[6];
+    nmul(c0, d, T(1), k1);
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+        y[i] = d[i] + hd * k1[i];
+    nmul(ch, y, T(1), k2);
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+        y[i] = d[i] + hd * k2[i];
+    nmul(ch, y, T(1), k3);
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+        y[i] = d[i] + dt * k3[i];
+    nmul(c1, y, T(1), k4);
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+        d[i] = d[i] + sx * (((k1[i] + T(2) * k2[i]) + T(2) * k3[i]) + k4[i]);
+}
+
+// Adjoints of (Q, R, omega) from one stage k = N (e_1 + y) with stage adjoint kb.
+template <typename T>
+__device__ __forceinline__ void coef_adj(const T kb[6], const T y[6], T acc[3])
+{
+    acc[0] += (-kb[0] * y[1] + kb[1] * (T(1) + y[0])) + (kb[4] * y[5] - kb[5] * y[4]);
+    acc[1] += (kb[1] * y[3] - kb[2] * y[4]) + (kb[4] * y[2] - kb[3] * y[1]);
+    acc[2] += T(2) * ((kb[2] * y[1] - kb[1] * y[2]) + (kb[3] * y[4] - kb[4] * y[3]));
+}
+
+// Sensitivities (A_x, A_y, E_x, E_y, Ed_x, Ed_y) of one sample from the
+// adjoints (Qb, Rb, wb) of its coefficients.
+template <typename T>
+__device__ __forceinline__ void sample_sens(const QkeS<T> &s, T px, T py, T pz2, T eperp, const T ab[3], T out[6])
+{
+    const T Px = px - s.ax, Py = py - s.ay;
+    const T w2 = ((Px * Px + Py * Py) + pz2) + T(1);
+    const T w = sqrt(w2);
+    const T EP = s.ex * Px + s.ey * Py;
+    const T X = w2 * s.ee - EP * EP;
+    const T P[2] = {Px, Py}, E[2] = {s.ex, s.ey};
+    const T dcr_dE[2] = {s.edy, -s.edx}, dcr_dEd[2] = {-s.ey, s.ex};
+    const T Qb = ab[0], Rb = ab[1], wb = ab[2];
+    const bool pos = X > T(0);
+    const T sX = pos ? sqrt(X) : T(0);
+    const T iX = pos ? T(1) / X : T(0);
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        const T dw_dP = P[a] / w;
+        T dQ_dP = 0, dQ_dE = 0, dR_dP = 0, dR_dE = 0, dR_dEd = 0;
+        if (pos) {
+            const T dX_dP = T(2) * P[a] * s.ee - T(2) * EP * E[a];
+            const T dX_dE = T(2) * w2 * E[a] - T(2) * EP * P[a];
+            dQ_dP = dX_dP / (T(2) * sX * w2) - sX * T(2) * P[a] / (w2 * w2);
+            dQ_dE = dX_dE / (T(2) * sX * w2);
+            // grouped so that no 1/X^2 is formed on its own (FP32 range)
+            dR_dP = eperp * (s.cr * iX) * (dw_dP - w * (dX_dP * iX));
+            dR_dE = eperp * w * iX * (dcr_dE[a] - s.cr * (dX_dE * iX));
+            dR_dEd = eperp * w * dcr_dEd[a] * iX;
+        }
+        out[a] = -((Qb * dQ_dP + Rb * dR_dP) + wb * dw_dP);
+        out[2 + a] = Qb * dQ_dE + Rb * dR_dE;
+        out[4 + a] = Rb * dR_dEd;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+        v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+struct ModeGeom {
+    double px, py, pz, w;
+    bool active;
+};
+
+__device__ __forceinline__ ModeGeom mode_geom(const pp_grid &g, int m)
+{
+    ModeGeom r;
+    const int nmodes = g.nx * g.ny * g.nz;
+    r.active = m < nmodes;
+    int ix = 0, iy = 0, iz = 0;
+    if (r.active) {
+        ix = m % g.nx;
+        iy = (m / g.nx) % g.ny;
+        iz = m / (g.nx * g.ny);
+    }
+    r.px = axis_node(ix, g.nx, g.x0, g.x1);
+    r.py = axis_node(iy, g.ny, g.y0, g.y1);
+    r.pz = axis_node(iz, g.nz, g.z0, g.z1);
+    r.w = r.active ? __dmul_rn(__dmul_rn(axis_weight(ix, g.nx, g.x0, g.x1, 0), axis_weight(iy, g.ny, g.y0, g.y1, 0)),
+                               axis_weight(iz, g.nz, g.z0, g.z1, g.mirror_z))
+                   : 0.0;
+    return r;
+}
+
+// fixed-order CTA sum of one double per thread; the result is valid in thread 0
+__device__ __forceinline__ double cta_sum(double v, double *red)
+{
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0)
+        red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kQWarps; ++w)
+            s += red[w];
+    __syncthreads();
+    return s;
+}
+
+// table[c][k] from A, E, Ed ([c][2][ld] FP64)
+template <typename T>
+__global__ void qke_table_kernel(const double *__restrict__ A, const double *__restrict__ E,
+                                 const double *__restrict__ Ed, int ld, int nsamp, int ldt, QkeS<T> *__restrict__ tab)
+{
+    const int c = blockIdx.y;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nsamp)
+        return;
+    const size_t r0 = (size_t)c * 2 * ld, r1 = r0 + ld;
+    const double ex = E[r0 + k], ey = E[r1 + k], dx = Ed[r0 + k], dy = Ed[r1 + k];
+    QkeS<T> s;
+    s.ax = (T)A[r0 + k];
+    s.ay = (T)A[r1 + k];
+    s.ex = (T)ex;
+    s.ey = (T)ey;
+    s.edx = (T)dx;
+    s.edy = (T)dy;
+    s.ee = (T)(ex * ex + ey * ey);
+    s.cr = (T)(ex * dy - ey * dx);
+    tab[(size_t)c * ldt + k] = s;
+}
+
+// Forward only: f(p) of every mode and per-CTA partial sums of w f.
+template <typename T>
+__global__ void __launch_bounds__(kQThreads) qke_forward_kernel(const QkeS<T> *__restrict__ tab, int ldt, int n_steps,
+                                                                double dt, pp_grid g, double *__restrict__ n_out,
+                                                                double *__restrict__ part)
+{
+    __shared__ double red[kQWarps];
+    const int c = blockIdx.y, blk = blockIdx.x;
+    const int nmodes = g.nx * g.ny * g.nz;
+    const int m = blk * kQThreads + threadIdx.x;
+    const ModeGeom mg = mode_geom(g, m);
+    const T px = (T)mg.px, py = (T)mg.py, pz2 = (T)(mg.pz * mg.pz), eperp = (T)sqrt(1.0 + mg.pz * mg.pz);
+    const QkeS<T> *tr = tab + (size_t)c * ldt;
+    T d[6] = {0, 0, 0, 0, 0, 0};
+    Coef<T> c0 = coef_at(tr[0], px, py, pz2, eperp);
+    for (int n = 0; n < n_steps; ++n) {
+        const Coef<T> ch = coef_at(tr[2 * n + 1], px, py, pz2, eperp);
+        const Coef<T> c1 = coef_at(tr[2 * n + 2], px, py, pz2, eperp);
+        rk4_step(d, c0, ch, c1, (T)dt);
+        c0 = c1;
+    }
+    const double f = -(double)d[0];
+    if (mg.active && n_out)
+        n_out[(size_t)c * nmodes + m] = f;
+    const double s = cta_sum(mg.active ? mg.w * f : 0.0, red);
+    if (threadIdx.x == 0)
+        part[(size_t)c * gridDim.x + blk] = s;
+}
+
+// Forward with checkpoints, then the backward sweep segment by segment.
+// ckpt[c][seg][6][nmp] (T), part[c][blk][6][ldg] (FP64), partJ[c][blk].
+template <typename T, int S>
+__global__ void __launch_bounds__(kQThreads) qke_adjoint_kernel(const QkeS<T> *__restrict__ tab, int ldt, int n_steps,
+                                                                double dt_d, pp_grid g, T *__restrict__ ckpt, int nmp,
+                                                                double *__restrict__ part, int ldg,
+                                                                double *__restrict__ partJ)
+{
+    __shared__ double red[kQWarps];
+    __shared__ double sb[kQWarps][2 * S][6];
+    const int c = blockIdx.y, blk = blockIdx.x, nblk = gridDim.x;
+    const int m = blk * kQThreads + threadIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const ModeGeom mg = mode_geom(g, m);
+    const T px = (T)mg.px, py = (T)mg.py, pz2 = (T)(mg.pz * mg.pz), eperp = (T)sqrt(1.0 + mg.pz * mg.pz);
+    const T dt = (T)dt_d, hd = T(0.5) * dt, sx = dt / T(6);
+    const QkeS<T> *tr = tab + (size_t)c * ldt;
+    const int nseg = (n_steps + S - 1) / S;
+    const int mm = min(m, nmp - 1);  // inactive threads store into a valid slot they own alone
+    T *ck = ckpt + (size_t)c * nseg * 6 * nmp;
+
+    // ---- phase A: forward, keeping the state at the start of every segment
+    T d[6] = {0, 0, 0, 0, 0, 0};
+    {
+        Coef<T> c0 = coef_at(tr[0], px, py, pz2, eperp);
+        for (int s = 0; s < nseg; ++s) {
+            if (mg.active)
+#pragma unroll
+                for (int i = 0; i < 6; ++i)
+                    ck[((size_t)s * 6 + i) * nmp + mm] = d[i];
+            const int n0 = s * S, cnt = min(S, n_steps - n0);
+            for (int q = 0; q < cnt; ++q) {
+                const int n = n0 + q;
+                const Coef<T> ch = coef_at(tr[2 * n + 1], px, py, pz2, eperp);
+                const Coef<T> c1 = coef_at(tr[2 * n + 2], px, py, pz2, eperp);
+                rk4_step(d, c0, ch, c1, dt);
+                c0 = c1;
+            }
+        }
+    }
+    {
+        const double s = cta_sum(mg.active ? mg.w * (-(double)d[0]) : 0.0, red);
+        if (threadIdx.x == 0)
+            partJ[(size_t)c * nblk + blk] = s;
+    }
+
+    // ---- phase B: backward
+    double *prow = part + ((size_t)c * nblk + blk) * 6 * ldg;
+    T bar[6] = {(T)(-mg.w), 0, 0, 0, 0, 0};
+    T pend[3] = {0, 0, 0};  // coefficient adjoints of the sample at the top of the next step
+    Coef<T> c1 = coef_at(tr[2 * n_steps], px, py, pz2, eperp);
+    for (int s = nseg - 1; s >= 0; --s) {
+        const int n0 = s * S, cnt = min(S, n_steps - n0);
+        T st[S][6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+            d[i] = mg.active ? ck[((size_t)s * 6 + i) * nmp + mm] : T(0);
+        {
+            Coef<T> c0 = coef_at(tr[2 * n0], px, py, pz2, eperp);
+#pragma unroll
+            for (int q = 0; q < S; ++q) {
+                if (q < cnt) {
+#pragma unroll
+                    for (int i = 0; i < 6; ++i)
+                        st[q][i] = d[i];
+                    const int n = n0 + q;
+                    const Coef<T> ch = coef_at(tr[2 * n + 1], px, py, pz2, eperp);
+                    const Coef<T> cn = coef_at(tr[2 * n + 2], px, py, pz2, eperp);
+                    rk4_step(d, c0, ch, cn, dt);
+                    c0 = cn;
+                }
+            }
+        }
+#pragma unroll
+        for (int q = S - 1; q >= 0; --q) {
+            if (q < cnt) {
+                const int n = n0 + q;
+                const QkeS<T> e0 = tr[2 * n], eh = tr[2 * n + 1], e1 = tr[2 * n + 2];
+                const Coef<T> c0 = coef_at(e0, px, py, pz2, eperp);
+                const Coef<T> ch = coef_at(eh, px, py, pz2, eperp);
+                const T *x = st[q];
+                T k1[6], k2[6], k3[6], y2[6], y3[6], y4[6];
+                nmul(c0, x, T(1), k1);
+#pragma unroll
+                for (int i = 0; i < 6; ++i)
+                    y2[i] = x[i] + hd * k1[i];
+                nmul(ch, y2, T(1), k2);
+#pragma unroll
+                for (int i = 0; i < 6; ++i)
+                    y3[i] = x[i] + hd * k2[i];
+                nmul(ch, y3, T(1), k3);
+#pragma unroll
+                for (int i = 0; i < 6; ++i)
+                    y4[i] = x[i] + dt * k3[i];
+                T kb1[6], kb2[6], kb3[6], kb4[6], xb[6], yb[6];
+#pragma unroll
+                for (int i = 0; i < 6; ++i) {
+                    kb1[i] = sx * bar[i];
+                    kb2[i] = T(2) * sx * bar[i];
+                    kb3[i] = kb2[i];
+                    kb4[i] = kb1[i];
+                    xb[i] = bar[i];
+                }
+                // k4 = N1 (e1 + y4): completes the sample 2n+2
+                coef_adj(kb4, y4, pend);
+                nmul(c1, kb4, T(0), yb);
+#pragma unroll
+                for (int i = 0; i < 6; ++i) {
+                    xb[i] -= yb[i];
+                    kb3[i] -= dt * yb[i];
+                }
+                T hacc[3] = {0, 0, 0};
+                coef_adj(kb3, y3, hacc);  // k3 = Nh (e1 + y3)
+                nmul(ch, kb3, T(0), yb);
+#pragma unroll
+                for (int i = 0; i < 6; ++i) {
+                    xb[i] -= yb[i];
+                    kb2[i] -= hd * yb[i];
+                }
+                coef_adj(kb2, y2, hacc);  // k2 = Nh (e1 + y2)
+                nmul(ch, kb2, T(0), yb);
+#pragma unroll
+                for (int i = 0; i < 6; ++i) {
+                    xb[i] -= yb[i];
+                    kb1[i] -= hd * yb[i];
+                }
+                T nacc[3] = {0, 0, 0};
+                coef_adj(kb1, x, nacc);  // k1 = N0 (e1 + x)
+                nmul(c0, kb1, T(0), yb);
+#pragma unroll
+                for (int i = 0; i < 6; ++i)
+                    bar[i] = xb[i] - yb[i];
+                // emit samples 2n+2 (slot 2q+1) and 2n+1 (slot 2q)
+                T o[6];
+                sample_sens(e1, px, py, pz2, eperp, pend, o);
+#pragma unroll
+                for (int i = 0; i < 6; ++i) {
+                    const T v = warp_sum(o[i]);
+                    if (lane == 0)
+                        sb[warp][2 * q + 1][i] = (double)v;
+                }
+                sample_sens(eh, px, py, pz2, eperp, hacc, o);
+#pragma unroll
+                for (int i = 0; i < 6; ++i) {
+                    const T v = warp_sum(o[i]);
+                    if (lane == 0)
+                        sb[warp][2 * q][i] = (double)v;
+                }
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+                    pend[i] = nacc[i];
+                c1 = c0;
+            }
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < 2 * cnt * 6; t += kQThreads) {
+            const int i = t / (2 * cnt), kk = t % (2 * cnt);
+            double acc = 0.0;
+            for (int w = 0; w < kQWarps; ++w)
+                acc += sb[w][kk][i];
+            prow[(size_t)i * ldg + 2 * n0 + 1 + kk] = acc;
+        }
+        __syncthreads();
+    }
+    // sample 0 (t_i): only the first step's k1 stage reaches it
+    {
+        T o[6];
+        sample_sens(tr[0], px, py, pz2, eperp, pend, o);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            const T v = warp_sum(o[i]);
+            if (lane == 0)
+                sb[warp][0][i] = (double)v;
+        }
+        __syncthreads();
+        if (threadIdx.x < 6) {
+            double acc = 0.0;
+            for (int w = 0; w < kQWarps; ++w)
+                acc += sb[w][0][threadIdx.x];
+            prow[(size_t)threadIdx.x * ldg] = acc;
+        }
+    }
+}
+
+// out[c][...] = sum over blocks of part[c][blk][...] (fixed order); n per candidate.
+__global__ void sum_blocks_kernel(const double *__restrict__ part, int nblk, long long n, double *__restrict__ out)
+{
+    const int c = blockIdx.y;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    const double *p = part + (size_t)c * nblk * n + i;
+    double acc = 0.0;
+    for (int b = 0; b < nblk; ++b)
+        acc += p[(size_t)b * n];
+    out[(size_t)c * n + i] = acc;
+}
+
+inline unsigned nbk(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+template <typename T>
+int build_table(const double *A, const double *E, const double *Ed, int ncand, int ld, int n_steps, void **tab,
+                int *ldt_out, cudaStream_t st)
+{
+    const int nsamp = 2 * n_steps + 1;
+    const int ldt = (nsamp + 31) / 32 * 32;
+    int rc = pp::scratch(pp::SCR_QKE_TABLE, sizeof(QkeS<T>) * (size_t)ldt * ncand, tab);
+    if (rc)
+        return rc;
+    qke_table_kernel<T><<<dim3(nbk(nsamp), ncand), 256, 0, st>>>(A, E, Ed, ld, nsamp, ldt, (QkeS<T> *)*tab);
+    *ldt_out = ldt;
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PP_OK : pp::cuda_fail(e, "QKE table");
+}
+
+template <typename T>
+int forward(const double *A, const double *E, const double *Ed, int ncand, int ld, int n_steps, double dt,
+            const pp_grid *g, double *N, double *n_p, cudaStream_t st)
+{
+    void *tab = nullptr, *part = nullptr;
+    int ldt = 0;
+    int rc = build_table<T>(A, E, Ed, ncand, ld, n_steps, &tab, &ldt, st);
+    const int nmodes = g->nx * g->ny * g->nz;
+    const int nblk = (nmodes + kQThreads - 1) / kQThreads;
+    if (!rc)
+        rc = pp::scratch(pp::SCR_QKE_PART, sizeof(double) * (size_t)nblk * ncand, &part);
+    if (rc)
+        return rc;
+    qke_forward_kernel<T><<<dim3(nblk, ncand), kQThreads, 0, st>>>((const QkeS<T> *)tab, ldt, n_steps, dt, *g, n_p,
+                                                                   (double *)part);
+    sum_blocks_kernel<<<dim3(1, ncand), 32, 0, st>>>((const double *)part, nblk, 1, N);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PP_OK : pp::cuda_fail(e, "QKE forward launch");
+}
+
+// Candidates per launch of the adjoint so that checkpoints and partial rows stay
+// within about 8 GiB.
+template <typename T, int S>
+int adjoint_chunk(int ncand, int n_steps, int nmodes)
+{
+    const int nblk = (nmodes + kQThreads - 1) / kQThreads;
+    const size_t ck = sizeof(T) * 6 * (size_t)((n_steps + S - 1) / S) * nmodes;
+    const size_t pr = sizeof(double) * 6 * (size_t)nblk * (2 * n_steps + 1);
+    const size_t per = ck + pr;
+    const size_t budget = (size_t)8 << 30;
+    return (int)std::max<size_t>(1, std::min<size_t>((size_t)ncand, budget / std::max<size_t>(per, 1)));
+}
+
+template <typename T, int S>
+int gradient(const double *A, const double *E, const double *Ed, int ncand, int ld, int n_steps, double dt,
+             const pp_grid *g, double *J, double *gs, int ldg, cudaStream_t st)
+{
+    void *tab = nullptr, *ck = nullptr, *part = nullptr, *pj = nullptr;
+    int ldt = 0;
+    int rc = build_table<T>(A, E, Ed, ncand, ld, n_steps, &tab, &ldt, st);
+    if (rc)
+        return rc;
+    const int nmodes = g->nx * g->ny * g->nz;
+    const int nblk = (nmodes + kQThreads - 1) / kQThreads;
+    const int nseg = (n_steps + S - 1) / S;
+    const int chunk = adjoint_chunk<T, S>(ncand, n_steps, nmodes);
+    rc = pp::scratch(pp::SCR_QKE_CKPT, sizeof(T) * 6 * (size_t)nseg * nmodes * chunk, &ck);
+    if (!rc)
+        rc = pp::scratch(pp::SCR_QKE_PART, sizeof(double) * 6 * (size_t)nblk * ldg * chunk, &part);
+    if (!rc)
+        rc = pp::scratch(pp::SCR_QKE_X, sizeof(double) * (size_t)nblk * chunk, &pj);
+    if (rc)
+        return rc;
+    for (int c0 = 0; c0 < ncand; c0 += chunk) {
+        const int nc = std::min(chunk, ncand - c0);
+        qke_adjoint_kernel<T, S><<<dim3(nblk, nc), kQThreads, 0, st>>>(
+            (const QkeS<T> *)tab + (size_t)c0 * ldt, ldt, n_steps, dt, *g, (T *)ck, nmodes, (double *)part, ldg,
+            (double *)pj);
+        sum_blocks_kernel<<<dim3(nbk(6ll * ldg), nc), 256, 0, st>>>((const double *)part, nblk, 6ll * ldg,
+                                                                    gs + (size_t)c0 * 6 * ldg);
+        sum_blocks_kernel<<<dim3(1, nc), 32, 0, st>>>((const double *)pj, nblk, 1, J + c0);
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PP_OK : pp::cuda_fail(e, "QKE adjoint launch");
+}
+
+}  // namespace
+
+namespace pp {
+
+int launch_qke_pair_number(const double *A, const double *E, const double *Ed, int ncand, int ld, int n_steps,
+                           double dt, const pp_grid *g, int precision, double *N, double *n_p, cudaStream_t st)
+{
+    if (precision == PP_FP64)
+        return forward<double>(A, E, Ed, ncand, ld, n_steps, dt, g, N, n_p, st);
+    return forward<float>(A, E, Ed, ncand, ld, n_steps, dt, g, N, n_p, st);
+}
+
+// J[c] and gs[c][6][ldg] = dJ/d(A_x, A_y, E_x, E_y, Ed_x, Ed_y samples)
+int launch_qke_gradient(const double *A, const double *E, const double *Ed, int ncand, int ld, int n_steps,
+                        double dt, const pp_grid *g, int precision, double *J, double *gs, int ldg, cudaStream_t st)
+{
+    if (precision == PP_FP64)
+        return gradient<double, 4>(A, E, Ed, ncand, ld, n_steps, dt, g, J, gs, ldg, st);
+    return gradient<float, 8>(A, E, Ed, ncand, ld, n_steps, dt, g, J, gs, ldg, st);
+}
+
+}  // namespace pp
+
+using namespace pp;
+
+namespace {
+
+int check_raw_spec(const pp_field_spec *spec)
+{
+    if (!spec)
+        return fail(PP_ERR_INVALID_ARG, "field spec is NULL");
+    pp_field_spec s = *spec;
+    s.fluence = 1.0;  // not used without renormalisation
+    return check_spec(&s);
+}
+
+int check_precision(int precision)
+{
+    if (precision != PP_FP64 && precision != PP_FP32 && precision != PP_FP32_FAST)
+        return fail(PP_ERR_INVALID_ARG, "precision must be PP_FP64, PP_FP32 or PP_FP32_FAST");
+    return PP_OK;
+}
+
+int check_samples(int ncand, int ld, int n_steps, double dt)
+{
+    if (ncand < 0 || ncand > 65535)
+        return fail(PP_ERR_INVALID_ARG, "ncand must be in [0, 65535]");
+    if (n_steps < 1 || n_steps > (1 << 28) || ld < 2 * n_steps + 1)
+        return fail(PP_ERR_INVALID_ARG, "need 1 <= n_steps <= 2^28 and ld >= 2 n_steps + 1");
+    if (!(dt > 0.0) || !isfinite(dt))
+        return fail(PP_ERR_INVALID_ARG, "dt must be positive");
+    return PP_OK;
+}
+
+struct GpuObjective {
+    const pp_field_spec *spec;
+    const pp_grid *grid;
+    int precision;
+    double U_const;
+    cudaStream_t st;
+    double *dx = nullptr, *dJ = nullptr, *dg = nullptr, *dU = nullptr, *ddU = nullptr;
+    int cap = 0;
+    std::vector<double> hU, hdU;
+};
+
+// The search's batched objective: J, grad J from the QKE adjoint on the GPU,
+// C = U_const - U, grad C = -grad U.
+int gpu_objective(void *ctx, int32_t count, const double *x, double *J, double *gJ, double *C, double *gC)
+{
+    GpuObjective *o = (GpuObjective *)ctx;
+    const int D = 4 * o->spec->K;
+    if (count > o->cap) {
+        cudaFree(o->dx);
+        cudaFree(o->dJ);
+        cudaFree(o->dg);
+        cudaFree(o->dU);
+        cudaFree(o->ddU);
+        o->dx = o->dJ = o->dg = o->dU = o->ddU = nullptr;
+        cudaError_t e = cudaMalloc(&o->dx, sizeof(double) * (size_t)count * D);
+        if (e == cudaSuccess)
+            e = cudaMalloc(&o->dJ, sizeof(double) * count);
+        if (e == cudaSuccess)
+            e = cudaMalloc(&o->dg, sizeof(double) * (size_t)count * D);
+        if (e == cudaSuccess)
+            e = cudaMalloc(&o->dU, sizeof(double) * count);
+        if (e == cudaSuccess)
+            e = cudaMalloc(&o->ddU, sizeof(double) * (size_t)count * D);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "local-search buffers");
+        o->cap = count;
+    }
+    cudaError_t e = cudaMemcpyAsync(o->dx, x, sizeof(double) * (size_t)count * D, cudaMemcpyHostToDevice, o->st);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "local-search upload");
+    int rc = pp_qke_gradient(o->dx, count, o->spec, o->grid, o->precision, o->dJ, o->dg, o->dU, o->ddU, o->st);
+    if (rc)
+        return rc;
+    o->hU.resize(count);
+    o->hdU.resize((size_t)count * D);
+    e = cudaMemcpyAsync(J, o->dJ, sizeof(double) * count, cudaMemcpyDeviceToHost, o->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(gJ, o->dg, sizeof(double) * (size_t)count * D, cudaMemcpyDeviceToHost, o->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(o->hU.data(), o->dU, sizeof(double) * count, cudaMemcpyDeviceToHost, o->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(o->hdU.data(), o->ddU, sizeof(double) * (size_t)count * D, cudaMemcpyDeviceToHost, o->st);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(o->st);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "local-search download");
+    if ((rc = pp_sync_status(o->st)))
+        return rc;
+    for (int q = 0; q < count; ++q) {
+        C[q] = o->U_const - o->hU[q];
+        for (int i = 0; i < D; ++i)
+            gC[(size_t)q * D + i] = -o->hdU[(size_t)q * D + i];
+    }
+    return PP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pp_synth_field_raw(const double *params, int32_t ncand, const pp_field_spec *spec, double *A, double *E,
+                       double *Ed, int32_t ld, double *U, void *stream)
+{
+    clear_error();
+    int rc = check_raw_spec(spec);
+    if (rc)
+        return rc;
+    if (ncand < 0 || ncand > 65535)
+        return fail(PP_ERR_INVALID_ARG, "ncand must be in [0, 65535]");
+    if (ncand > 0 && (!params || !A))
+        return fail(PP_ERR_INVALID_ARG, "params and A must not be NULL");
+    if (ld < 2 * spec->n_steps + 1)
+        return fail(PP_ERR_INVALID_ARG, "ld must be >= 2 n_steps + 1");
+    return launch_synth(params, ncand, spec, 0, A, ld, E, Ed, U, (cudaStream_t)stream);
+}
+
+int pp_synth_vjp(const double *params, int32_t ncand, const pp_field_spec *spec, const double *g, int32_t ldg,
+                 double *grad, double *U, double *dU, void *stream)
+{
+    clear_error();
+    int rc = check_raw_spec(spec);
+    if (rc)
+        return rc;
+    if (ncand < 0 || ncand > 65535)
+        return fail(PP_ERR_INVALID_ARG, "ncand must be in [0, 65535]");
+    if (ncand > 0 && (!params || (grad && !g)))
+        return fail(PP_ERR_INVALID_ARG, "params (and g when grad is wanted) must not be NULL");
+    if (grad && ldg < 2 * spec->n_steps + 1)
+        return fail(PP_ERR_INVALID_ARG, "ldg must be >= 2 n_steps + 1");
+    return launch_synth_vjp(params, ncand, spec, g, ldg, grad, U, dU, (cudaStream_t)stream);
+}
+
+int pp_qke_pair_number(const double *A, const double *E, const double *Ed, int32_t ncand, int32_t ld,
+                       int32_t n_steps, double dt, const pp_grid *grid, int32_t precision, double *N, double *n_p,
+                       void *stream)
+{
+    clear_error();
+    int rc = check_samples(ncand, ld, n_steps, dt);
+    if (!rc)
+        rc = check_grid(grid);
+    if (!rc)
+        rc = check_precision(precision);
+    if (rc)
+        return rc;
+    if (ncand == 0)
+        return PP_OK;
+    if (!A || !E || !Ed || !N)
+        return fail(PP_ERR_INVALID_ARG, "A, E, Ed and N must not be NULL");
+    return launch_qke_pair_number(A, E, Ed, ncand, ld, n_steps, dt, grid, precision, N, n_p, (cudaStream_t)stream);
+}
+
+int pp_qke_sample_gradient(const double *A, const double *E, const double *Ed, int32_t ncand, int32_t ld,
+                           int32_t n_steps, double dt, const pp_grid *grid, int32_t precision, double *J, double *g,
+                           int32_t ldg, void *stream)
+{
+    clear_error();
+    int rc = check_samples(ncand, ld, n_steps, dt);
+    if (!rc)
+        rc = check_grid(grid);
+    if (!rc)
+        rc = check_precision(precision);
+    if (rc)
+        return rc;
+    if (ncand == 0)
+        return PP_OK;
+    if (!A || !E || !Ed || !J || !g)
+        return fail(PP_ERR_INVALID_ARG, "A, E, Ed, J and g must not be NULL");
+    if (ldg < 2 * n_steps + 1)
+        return fail(PP_ERR_INVALID_ARG, "ldg must be >= 2 n_steps + 1");
+    return launch_qke_gradient(A, E, Ed, ncand, ld, n_steps, dt, grid, precision, J, g, ldg, (cudaStream_t)stream);
+}
+
+int pp_qke_gradient(const double *params, int32_t ncand, const pp_field_spec *spec, const pp_grid *grid,
+                    int32_t precision, double *J, double *gJ, double *U, double *dU, void *stream)
+{
+    clear_error();
+    int rc = check_raw_spec(spec);
+    if (!rc)
+        rc = check_grid(grid);
+    if (!rc)
+        rc = check_precision(precision);
+    if (rc)
+        return rc;
+    if (ncand < 0 || ncand > 65535)
+        return fail(PP_ERR_INVALID_ARG, "ncand must be in [0, 65535]");
+    if (ncand == 0)
+        return PP_OK;
+    if (!params || !J)
+        return fail(PP_ERR_INVALID_ARG, "params and J must not be NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = spec->n_steps, ld = 2 * n + 1;
+    void *fld = nullptr, *gs = nullptr;
+    rc = scratch(SCR_QKE_FIELD, sizeof(double) * 3 * 2 * (size_t)ld * ncand, &fld);
+    if (!rc && gJ)
+        rc = scratch(SCR_QKE_G, sizeof(double) * 6 * (size_t)ld * ncand, &gs);
+    if (rc)
+        return rc;
+    double *A = (double *)fld, *E = A + 2 * (size_t)ld * ncand, *Ed = E + 2 * (size_t)ld * ncand;
+    if ((rc = launch_synth(params, ncand, spec, 0, A, ld, E, Ed, nullptr, st)))
+        return rc;
+    const double dt = spec->T / n;
+    if (gJ) {
+        if ((rc = launch_qke_gradient(A, E, Ed, ncand, ld, n, dt, grid, precision, J, (double *)gs, ld, st)))
+            return rc;
+    } else if ((rc = launch_qke_pair_number(A, E, Ed, ncand, ld, n, dt, grid, precision, J, nullptr, st))) {
+        return rc;
+    }
+    if (gJ || U || dU)
+        return launch_synth_vjp(params, ncand, spec, (const double *)gs, ld, gJ, U, dU, st);
+    return PP_OK;
+}
+
+int pp_local_search(double *x, int32_t nstart, const pp_field_spec *spec, const pp_grid *grid, int32_t precision,
+                    double U_const, const pp_al_options *opt, double *J_out, double *C_out, double *lam_out,
+                    int32_t *evals_out, int32_t *outer_out, int32_t *status_out, void *stream)
+{
+    clear_error();
+    int rc = check_raw_spec(spec);
+    if (!rc)
+        rc = check_grid(grid);
+    if (!rc)
+        rc = check_precision(precision);
+    if (rc)
+        return rc;
+    if (!(U_const > 0.0) || !isfinite(U_const))
+        return fail(PP_ERR_INVALID_ARG, "U_const must be positive");
+    GpuObjective o;
+    o.spec = spec;
+    o.grid = grid;
+    o.precision = precision;
+    o.U_const = U_const;
+    o.st = (cudaStream_t)stream;
+    rc = pp_al_search(4 * spec->K, nstart, x, gpu_objective, &o, opt, J_out, C_out, lam_out, evals_out, outer_out,
+                      status_out);
+    cudaFree(o.dx);
+    cudaFree(o.dJ);
+    cudaFree(o.dg);
+    cudaFree(o.dU);
+    cudaFree(o.ddU);
+    return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,224 @@
+"""The QKE forward solve, its adjoint gradient, the raw synthesis with dE/dt and
+its chain rule, and the GPU local search, against the FP64 CPU oracle
+(Sec. II.B and Sec. IV.A of arXiv 1704.08919)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import localsearch as LS
+from paper_1704_08919_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+K = 4
+ARGS = (K, 3, 0.0, 2.0, 20.0)
+
+
+def spec(n):
+    return dict(K=K, order=3, w_min=0.0, w_max=2.0, T=20.0, fluence=1.0, n_steps=n)
+
+
+@pytest.fixture(scope="module")
+def pp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1704_08919_gb300 import build
+    build.build()
+    import paper_1704_08919_gb300 as pp
+    pp.lib()
+    assert pp.sync_status() == pp.PP_OK
+    return pp
+
+
+def params(nc, seed, U=2.0):
+    """nc random parameter vectors with the amplitude weights scaled to fluence U."""
+    lo, hi, _ = inputs.param_bounds(K)
+    rng = np.random.default_rng(seed)
+    X = lo + rng.random((nc, 4 * K)) * (hi - lo)
+    for x in X:
+        U0, _ = oracle.fluence_raw(x, *ARGS)
+        s = math.sqrt(U / U0)
+        x[:K] *= s
+        x[2 * K:3 * K] *= s
+    return X
+
+
+def dev(x):
+    return torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+
+
+def floor64(n_steps):
+    """Absolute rounding floor of a pair density after n_steps FP64 RK4 steps."""
+    return 64 * 2.0 ** -53 * math.sqrt(n_steps)
+
+
+@pytest.mark.parametrize("n", [150, 203])
+def test_raw_synthesis_and_time_derivative(pp, n):
+    X = params(3, 1)
+    A, E, Ed, U = pp.synth_field_raw(dev(X), spec(n))
+    Ao, Eo, Edo, Uo = oracle.synth_raw(X, *ARGS, n)
+    assert pp.sync_status() == pp.PP_OK
+    for g, o in ((A, Ao), (E, Eo), (Ed, Edo)):
+        assert np.abs(g.cpu().numpy() - o).max() < 1e-12 * np.abs(o).max()
+    assert np.allclose(U.cpu().numpy(), Uo, rtol=1e-13, atol=0)
+
+
+def test_fluence_and_chain_rule(pp):
+    n = 120
+    X = params(3, 2, U=3.0)
+    rng = np.random.default_rng(3)
+    g = rng.normal(size=(3, 6, 2 * n + 1))
+    grad, U, dU = pp.synth_vjp(dev(X), spec(n), dev(g))
+    assert pp.sync_status() == pp.PP_OK
+    grad, U, dU = grad.cpu().numpy(), U.cpu().numpy(), dU.cpu().numpy()
+    for c in range(3):
+        ref = oracle.synth_vjp(X[c], *ARGS, n, g[c, 0:2], g[c, 2:4], g[c, 4:6])
+        assert np.abs(grad[c] - ref).max() < 1e-11 * np.abs(ref).max()
+        Uo, dUo = oracle.fluence_raw(X[c], *ARGS)
+        assert abs(U[c] - Uo) < 1e-13 * Uo
+        assert np.abs(dU[c] - dUo).max() < 1e-12 * np.abs(dUo).max()
+
+
+@pytest.mark.parametrize("n,grid", [(150, inputs.small_grid(17, 9, 3)),
+                                    (203, inputs.small_grid(5, 4, 3, mirror_z=0))])
+def test_qke_forward_matches_oracle(pp, n, grid):
+    X = params(2, 4)
+    A, E, Ed, _ = oracle.synth_raw(X, *ARGS, n)
+    p, w = oracle.grid_modes(grid)
+    dt = 20.0 / n
+    J64, f64 = pp.qke_pair_number(dev(A), dev(E), dev(Ed), dt, grid, "fp64", want_n=True)
+    J32, _ = pp.qke_pair_number(dev(A), dev(E), dev(Ed), dt, grid, "fp32")
+    assert pp.sync_status() == pp.PP_OK
+    f64 = f64.cpu().numpy().reshape(2, -1)
+    for c in range(2):
+        fo = oracle.qke6_modes(A[c], E[c], Ed[c], n, dt, p)
+        assert np.all(np.abs(f64[c] - fo) <= 1e-9 * np.abs(fo) + floor64(n))
+        Jo = float(np.sum(w * fo))
+        assert abs(J64[c].item() / Jo - 1) < 1e-9
+        assert abs(J32[c].item() / Jo - 1) < 1e-4
+
+
+def test_qke_agrees_with_dirac(pp):
+    """The two formalisms give the same pair density (Sec. II.B); at a small step both
+    RK4 discretisations are converged to well below the tolerance."""
+    n = 1600
+    X = params(2, 5)
+    grid = inputs.small_grid(8, 8, 4)
+    Xd = dev(X)
+    A, E, Ed, _ = pp.synth_field_raw(Xd, spec(n))
+    Jq, fq = pp.qke_pair_number(A, E, Ed, 20.0 / n, grid, "fp64", want_n=True)
+    Nd, fd = pp.pair_number(A, 20.0 / n, grid, precision="fp64", scheme="rk4", want_n=True)
+    assert pp.sync_status() == pp.PP_OK
+    assert torch.allclose(Jq, Nd, rtol=1e-6, atol=0)
+    assert (fq - fd).abs().max().item() < 1e-6 * fd.abs().max().item()
+
+
+@pytest.mark.parametrize("n,grid,nc", [(150, inputs.small_grid(17, 9, 3), 2),
+                                       (203, inputs.small_grid(6, 5, 2, mirror_z=0), 3),
+                                       (9, inputs.small_grid(3, 3, 1), 1)])
+def test_sample_gradient_matches_oracle(pp, n, grid, nc):
+    X = params(nc, 6)
+    A, E, Ed, _ = oracle.synth_raw(X, *ARGS, n)
+    p, w = oracle.grid_modes(grid)
+    dt = 20.0 / n
+    J, g = pp.qke_sample_gradient(dev(A), dev(E), dev(Ed), dt, grid, "fp64")
+    J32, g32 = pp.qke_sample_gradient(dev(A), dev(E), dev(Ed), dt, grid, "fp32")
+    assert pp.sync_status() == pp.PP_OK
+    g, g32 = g.cpu().numpy(), g32.cpu().numpy()
+    for c in range(nc):
+        Jo, _, gA, gE, gEd = oracle.qke6_grad(A[c], E[c], Ed[c], n, dt, p, w)
+        ref = np.concatenate([gA, gE, gEd])
+        scale = np.abs(ref).max()
+        assert abs(J[c].item() / Jo - 1) < 1e-9
+        assert np.abs(g[c] - ref).max() < 1e-9 * scale
+        assert abs(J32[c].item() / Jo - 1) < 1e-4
+        assert np.linalg.norm(g32[c] - ref) < 1e-3 * np.linalg.norm(ref)
+
+
+def test_parameter_gradient_matches_oracle(pp):
+    n = 160
+    grid = inputs.small_grid(6, 6, 3)
+    X = params(3, 7)
+    J, gJ, U, dU = pp.qke_gradient(dev(X), spec(n), grid, "fp64")
+    J0, none, _, _ = pp.qke_gradient(dev(X), spec(n), grid, "fp64", want_grad=False)
+    assert pp.sync_status() == pp.PP_OK
+    assert torch.allclose(J, J0, rtol=1e-13, atol=0)
+    for c in range(3):
+        o = oracle.al_objective(X[c], spec(n), grid, 2.0, 0.0, 1.0)
+        assert abs(J[c].item() / o["J"] - 1) < 1e-9
+        assert np.abs(gJ[c].cpu().numpy() - o["gJ"]).max() < 1e-9 * np.abs(o["gJ"]).max()
+        assert np.abs(dU[c].cpu().numpy() + o["gC"]).max() < 1e-12 * np.abs(o["gC"]).max()
+        assert abs(U[c].item() - (2.0 - o["C"])) < 1e-12
+
+
+def test_directional_derivative_at_full_size(pp):
+    """At the de-batch solver size (grid 64 x 64 x 32, 8192 steps, K = 8) the oracle
+    cannot form the whole gradient; the property checked is the directional
+    derivative: (J(x + h v) - J(x - h v)) / 2h = grad J . v."""
+    cfg = inputs.DE_BATCH
+    sp = dict(inputs.field_spec(cfg), fluence=1.0)
+    Kf = cfg["K"]
+    lo, hi, _ = inputs.param_bounds(Kf)
+    rng = np.random.default_rng(8)
+    x = lo + rng.random(4 * Kf) * (hi - lo)
+    Xd = dev(x[None, :])
+    _, _, U, _ = pp.qke_gradient(Xd, sp, cfg["grid"], "fp64", want_grad=False)
+    s = math.sqrt(2.0 / U.item())
+    x[:Kf] *= s
+    x[2 * Kf:3 * Kf] *= s
+    v = rng.normal(size=4 * Kf)
+    v /= np.linalg.norm(v)
+    h = 1e-4
+    X3 = dev(np.stack([x, x + h * v, x - h * v]))
+    J, gJ, _, _ = pp.qke_gradient(X3[:1].contiguous(), sp, cfg["grid"], "fp64")
+    Jp, _, _, _ = pp.qke_gradient(X3[1:].contiguous(), sp, cfg["grid"], "fp64", want_grad=False)
+    assert pp.sync_status() == pp.PP_OK
+    fd = (Jp[0].item() - Jp[1].item()) / (2 * h)
+    an = float(gJ[0].cpu().numpy() @ v)
+    assert abs(fd - an) < 1e-5 * np.abs(gJ[0].cpu().numpy()).sum()
+    # f at sampled modes against the oracle's forward solve at this size
+    A, E, Ed, _ = pp.synth_field_raw(X3[:1].contiguous(), sp)
+    _, f = pp.qke_pair_number(A, E, Ed, sp["T"] / sp["n_steps"], cfg["grid"], "fp64", want_n=True)
+    modes = inputs.strided_modes(cfg["grid"], 24, seed=3)
+    pts = inputs.grid_points(cfg["grid"])[modes]
+    fo = oracle.qke6_modes(A[0].cpu().numpy(), E[0].cpu().numpy(), Ed[0].cpu().numpy(),
+                           sp["n_steps"], sp["T"] / sp["n_steps"], pts)
+    fg = f[0].cpu().numpy().reshape(-1)[modes]
+    assert np.all(np.abs(fg - fo) <= 1e-9 * np.abs(fo) + floor64(sp["n_steps"]))
+
+
+def test_local_search_matches_oracle(pp):
+    """The GPU local search and the oracle's (same algorithm, FP64 objective from the
+    oracle) reach the same constrained maximum from the same starts."""
+    n = 100
+    grid = inputs.small_grid(4, 4, 2)
+    starts = params(2, 9, U=1.5)
+    kw = dict(mu0=1.0, xi=0.5, outer=8, max_iter=60, gtol=1e-6, ctol=1e-7)
+    r = pp.local_search(starts, spec(n), grid, 2.0, precision="fp64", **kw)
+    assert pp.sync_status() == pp.PP_OK
+    for i in range(2):
+        def obj(z):
+            o = oracle.al_objective(z, spec(n), grid, 2.0, 0.0, 1.0)
+            return o["J"], o["gJ"], o["C"], o["gC"]
+        o = LS.augmented_lagrangian(obj, starts[i], **kw)
+        assert r["status"][i] == 0 and abs(r["C"][i]) <= 1e-7
+        assert abs(r["J"][i] / o["J"] - 1) < 1e-5
+        J0 = oracle.al_objective(starts[i], spec(n), grid, 2.0, 0.0, 1.0)["J"]
+        assert r["J"][i] > J0
+
+
+def test_rejects_bad_arguments(pp):
+    X = dev(params(1, 10))
+    with pytest.raises(pp.PPError):
+        pp.qke_gradient(X, dict(spec(10), order=0), inputs.small_grid(2, 2, 1))
+    with pytest.raises(pp.PPError):
+        pp.qke_gradient(X, spec(10), inputs.small_grid(0, 2, 1))
+    with pytest.raises(pp.PPError):
+        pp.local_search(params(1, 10), spec(10), inputs.small_grid(2, 2, 1), -1.0)
+    A = torch.zeros((1, 2, 21), dtype=torch.float64, device="cuda")
+    with pytest.raises(pp.PPError):
+        pp.qke_pair_number(A, A, A, 0.0, inputs.small_grid(2, 2, 1))
+    assert pp.sync_status() == pp.PP_OK
