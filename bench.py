@@ -61,7 +61,7 @@ def parse():
                     help="modes of one candidate in the CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="de-batch", choices=["de-batch", "uneven", "surrogate", "gemm"],
+    ap.add_argument("--workload", default="de-batch", choices=["de-batch", "uneven", "surrogate", "gemm", "localsearch"],
                     help="de-batch: the 64-candidate DE generation (default); uneven: 128 slots "
                          "of uneven length and grid, generations in one CUDA graph; surrogate: "
                          "exact calls of surrogate-screened DE against plain DE")
@@ -380,6 +380,86 @@ def gemm_measure(pp, torch, reps=20):
     return out
 
 
+# FP32 operations per mode-step of the QKE adjoint kernel, counted from its source
+# (no FMA contraction: every multiply and add is one instruction): forward pass
+# 186 (2 coefficient sets, 4 matrix products, stage updates), the recomputed
+# forward 186, the backward step 611 (2 coefficient sets, 3 + 4 matrix products,
+# 4 coefficient adjoints, 2 sample sensitivities, 12 warp sums).
+QKE_ADJ_FLOP = 983
+
+
+def localsearch_main(args):
+    """Multistart augmented-Lagrangian local search (Sec. IV.A) on the QKE: the
+    native optimiser drives batched adjoint-gradient evaluations on the GPU."""
+    import torch
+    import paper_1704_08919_gb300 as pp
+    L = inputs.LOCAL_SEARCH
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    pp.lib()
+    sp = inputs.field_spec(dict(L, fluence=1.0))
+    K, S = L["K"], L["nstart"]
+    prec = "fp64" if args.precision == "fp64" else "fp32"
+    X = inputs.random_population(S, K, seed=L["seed"])
+    Xd = torch.tensor(X, device="cuda")
+    _, _, U, _ = pp.qke_gradient(Xd, sp, L["grid"], prec, want_grad=False)
+    sc = np.sqrt(L["U_const"] / U.cpu().numpy())
+    X[:, :K] *= sc[:, None]
+    X[:, 2 * K:3 * K] *= sc[:, None]
+    Xd = torch.tensor(X, device="cuda")
+    # one batched evaluation (all starts): forward + adjoint + chain rule, timed alone
+    for _ in range(2):
+        pp.qke_gradient(Xd, sp, L["grid"], prec)
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    reps = 3
+    for _ in range(reps):
+        J0, _, _, _ = pp.qke_gradient(Xd, sp, L["grid"], prec)
+    e1.record(st)
+    torch.cuda.synchronize()
+    eval_ms = e0.elapsed_time(e1) / reps
+    g = L["grid"]
+    mode_steps = g["nx"] * g["ny"] * g["nz"] * L["n_steps"] * S
+    clocks = ClockSampler(local)
+    clocks.start()
+    t0 = time.perf_counter()
+    r = pp.local_search(X, sp, L["grid"], L["U_const"], precision=prec, mu0=L["mu0"], xi=L["xi"],
+                        outer=L["outer"], max_iter=L["max_iter"], gtol=L["gtol"], ctol=L["ctol"])
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    if pp.sync_status() != pp.PP_OK:
+        raise RuntimeError("device status after the local search")
+    J0 = J0.cpu().numpy()
+    achieved = QKE_ADJ_FLOP * mode_steps / (eval_ms * 1e-3) / 1e12
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2070e6 / 1e12
+    print(json.dumps({
+        "metric": "local-search gradient evaluations/s (QKE forward + adjoint, all starts batched)",
+        "value": S / (eval_ms * 1e-3), "unit": "gradients/s", "n_gpus": 1, "steps": reps,
+        "warmup": 2, "ms_per_step": eval_ms, "higher_is_better": True, "scaling": "none",
+        "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64",
+        "data": "synthetic (seeded B-spline pulses scaled to U_const)",
+        "config": {"workload": L["name"], "precision": prec, "grid": "%dx%dx%d" % (g["nx"], g["ny"], g["nz"]),
+                   "n_steps": L["n_steps"], "T": L["T"], "nstart": S,
+                   "options": {k: L[k] for k in ("mu0", "xi", "outer", "max_iter", "gtol", "ctol")}},
+        "mode_steps_per_s": mode_steps / (eval_ms * 1e-3),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak,
+                     "note": "%d FP32 operations per mode-step counted from the source, no FMA; "
+                             "peak = 152 SMs x 128 lanes x 2070 MHz, one operation per lane-cycle"
+                             % QKE_ADJ_FLOP},
+        "search": {"seconds": wall, "evals_total": int(r["evals"].sum()),
+                   "J_start": [float(v) for v in J0], "J_end": [float(v) for v in r["J"]],
+                   "C_end": [float(v) for v in r["C"]], "status": [int(v) for v in r["status"]],
+                   "outer": [int(v) for v in r["outer"]], "best_J": float(np.max(r["J"][r["status"] == 0]))
+                   if np.any(r["status"] == 0) else None},
+        "clocks": clk}), flush=True)
+    return 0
+
+
 def gemm_main(args):
     import torch
     import paper_1704_08919_gb300 as pp
@@ -491,6 +571,8 @@ def main():
         return surrogate_main(args)
     if args.workload == "gemm":
         return gemm_main(args)
+    if args.workload == "localsearch":
+        return localsearch_main(args)
     import torch
     import paper_1704_08919_gb300 as pp
 

@@ -436,7 +436,10 @@ typedef int (*pp_objective_fn)(void *ctx, int32_t count, const double *x, double
  * call of fn.  Per start (each may be NULL): J_out, C_out at the result,
  * lam_out the final multiplier, evals_out the objective evaluations,
  * outer_out the inner minimisations run, status_out 0 = |C| <= ctol reached,
- * 1 = `outer` exhausted.  Each start's iterates do not depend on the others. */
+ * 1 = `outer` exhausted, 2 = L or its gradient is not finite where an inner
+ * minimisation starts (the start ends there).  A non-finite value or slope at
+ * a trial step counts as a failed sufficient-decrease test.  Each start's
+ * iterates do not depend on the others. */
 int pp_al_search(int32_t n, int32_t nstart, double *x, pp_objective_fn fn, void *ctx,
                  const pp_al_options *opt, double *J_out, double *C_out, double *lam_out,
                  int32_t *evals_out, int32_t *outer_out, int32_t *status_out);

@@ -58,6 +58,8 @@ def _cubic_min(a, fa, ga, b, fb, gb):
 def _zoom_point(lo, flo, glo, hi, fhi, ghi):
     """Cubic step safeguarded to the inner 80% of [lo, hi], else the midpoint."""
     a = _cubic_min(lo, flo, glo, hi, fhi, ghi)
+    if a is not None and not math.isfinite(a):
+        a = None
     left, right = min(lo, hi), max(lo, hi)
     d = right - left
     if a is None or not (left + 0.1 * d <= a <= right - 0.1 * d):
@@ -81,7 +83,8 @@ def line_search(phi, f0, g0, alpha1):
         f, g, pay = phi(a)
         evals += 1
         cur = (a, f, g, pay)
-        if f > f0 + C1 * a * g0 or (i > 0 and f >= prev[1]):
+        # a non-finite value or slope counts as a failed decrease (the step is too long)
+        if not (math.isfinite(f) and math.isfinite(g)) or f > f0 + C1 * a * g0 or (i > 0 and f >= prev[1]):
             return _zoom(phi, f0, g0, prev, cur, evals)
         if abs(g) <= -C2 * g0:
             return a, f, pay, evals, True
@@ -99,7 +102,7 @@ def _zoom(phi, f0, g0, lo, hi, evals):
         f, g, pay = phi(a)
         evals += 1
         cur = (a, f, g, pay)
-        if f > f0 + C1 * a * g0 or f >= lo[1]:
+        if not (math.isfinite(f) and math.isfinite(g)) or f > f0 + C1 * a * g0 or f >= lo[1]:
             hi = cur
         else:
             if abs(g) <= -C2 * g0:
@@ -119,6 +122,8 @@ def bfgs(fg, x0, gtol=1e-6, max_iter=200):
     n = x.size
     f, g, aux = fg(x)
     evals = 1
+    if not (math.isfinite(f) and all(math.isfinite(v) for v in g)):
+        return dict(x=x, f=f, g=g, aux=aux, iters=0, evals=evals, status="invalid")
     H = np.eye(n)
     first = True
     for k in range(max_iter):
@@ -161,7 +166,9 @@ def bfgs(fg, x0, gtol=1e-6, max_iter=200):
 
 def augmented_lagrangian(obj, x0, mu0=1.0, xi=0.5, outer=10, gtol=1e-6, ctol=1e-8, max_iter=200):
     """Steps 1-4 of Sec. IV.A from x0.  obj(x) -> (J, gJ, C, gC).  Returns dict(x, J, C,
-    lam, mu, outer, evals, history)."""
+    lam, mu, outer, evals, history, status): status 0 = |C| <= ctol reached, 1 = `outer`
+    inner minimisations run, 2 = the objective is not finite where an inner
+    minimisation starts."""
     lam, mu = 0.0, mu0
     x = np.array(x0, dtype=np.float64)
     evals = 0
@@ -177,11 +184,15 @@ def augmented_lagrangian(obj, x0, mu0=1.0, xi=0.5, outer=10, gtol=1e-6, ctol=1e-
         x = r["x"]
         J, C = r["aux"]
         history.append(dict(J=J, C=C, lam=lam, mu=mu, iters=r["iters"], status=r["status"]))
+        if r["status"] == "invalid":
+            return dict(x=x, J=J, C=C, lam=lam, mu=mu, outer=l + 1, evals=evals, history=history,
+                        status=2)
         if abs(C) <= ctol:
-            return dict(x=x, J=J, C=C, lam=lam, mu=mu, outer=l + 1, evals=evals, history=history)
+            return dict(x=x, J=J, C=C, lam=lam, mu=mu, outer=l + 1, evals=evals, history=history,
+                        status=0)
         lam = lam - C / mu
         mu = xi * mu
-    return dict(x=x, J=J, C=C, lam=lam, mu=mu, outer=outer, evals=evals, history=history)
+    return dict(x=x, J=J, C=C, lam=lam, mu=mu, outer=outer, evals=evals, history=history, status=1)
 
 
 def multistart(obj, starts, **kw):

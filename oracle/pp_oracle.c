@@ -681,6 +681,25 @@ static void mat6_vec(const double N[6][6], const double x[6], double y[6])
     }
 }
 
+/* chi moves on the unit sphere (N is skew), but RK4 does not keep |chi| = 1:
+ * its amplification per step, |1 + z + ... + z^4/24| at z = i theta, is below
+ * one for theta < 2 sqrt(2) and above it beyond, so where the field is too
+ * strong for the step the discrete chi grows without bound and f = 1 - chi_1
+ * leaves the physical range [0, 2].  A density whose |chi(t_f)|^2 exceeds
+ * 1 + QKE_GROWTH_TOL is reported as NaN (the step is too coarse for the field),
+ * so that an optimiser never climbs on that artefact. */
+#define QKE_GROWTH_TOL 1e-3
+
+static double qke_density(const double chi[6])
+{
+    double nrm = 0.0;
+    for (int i = 0; i < 6; i++)
+        nrm += chi[i] * chi[i];
+    if (!(nrm <= 1.0 + QKE_GROWTH_TOL))
+        return NAN;
+    return 1.0 - chi[0];
+}
+
 /* f = 1 - chi_1(t_f) by classical RK4 with chi(t_i) = (1,0,0,0,0,0).  A, E,
  * Edot are [2][ld] half-step samples as in orc_dirac_mode. */
 double orc_qke6_mode(const double *A, const double *E, const double *Edot, int ld, int n_steps,
@@ -710,7 +729,7 @@ double orc_qke6_mode(const double *A, const double *E, const double *Edot, int l
         for (int i = 0; i < 6; i++)
             chi[i] = chi[i] + dt / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
     }
-    return 1.0 - chi[0];
+    return qke_density(chi);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -1029,7 +1048,7 @@ double orc_qke6_adjoint_mode(const double *A, const double *E, const double *Ed,
         for (int i = 0; i < 6; i++)
             chi[n + 1][i] = chi[n][i] + dt / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
     }
-    double f = 1.0 - chi[n_steps][0];
+    double f = qke_density(chi[n_steps]);
     double bar[6] = {-weight, 0, 0, 0, 0, 0};  /* d(weight f)/d chi(t_f) */
     for (int n = n_steps - 1; n >= 0; n--) {
         double N0[6][6], Nh[6][6], N1[6][6], k1[6], k2[6], k3[6], y2[6], y3[6], y4[6];

@@ -15,6 +15,9 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libpp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# Sources whose kernels may contract multiply-adds: their results are compared with
+# the oracle within tolerances, not bit for bit across launch configurations.
+FUSED_OK = {"pp_qke.cu"}
 
 
 def nvcc():
@@ -52,7 +55,10 @@ def build(force=False, verbose_ptxas=False):
         src, obj = pair
         if not force and not verbose_ptxas and not _stale(obj, [src] + headers):
             return ""
-        r = subprocess.run([nvcc(), "-c", src, "-o", obj] + flags, capture_output=True, text=True)
+        f = flags
+        if os.path.basename(src) in FUSED_OK:
+            f = [("-fmad=true" if x == "-fmad=false" else x) for x in flags]
+        r = subprocess.run([nvcc(), "-c", src, "-o", obj] + f, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed on %s:\n%s%s" % (src, r.stdout, r.stderr))
         return r.stdout + r.stderr

@@ -95,7 +95,8 @@ struct Search {
     {
         double a;
         const double left = std::min(l.a, h.a), right = std::max(l.a, h.a), w = right - left;
-        if (!cubic_min(l.a, l.f, l.d, h.a, h.f, h.d, &a) || !(left + 0.1 * w <= a && a <= right - 0.1 * w))
+        if (!cubic_min(l.a, l.f, l.d, h.a, h.f, h.d, &a) || !isfinite(a) ||
+            !(left + 0.1 * w <= a && a <= right - 0.1 * w))
             a = 0.5 * (l.a + h.a);
         return a;
     }
@@ -236,6 +237,15 @@ struct Search {
             s.g = gl;
             s.J = J;
             s.C = C;
+            bool finite = isfinite(fl);
+            for (int i = 0; i < n; ++i)
+                finite = finite && isfinite(gl[i]);
+            if (!finite) {  // the objective is not defined here: this start ends
+                s.outer += 1;
+                s.status = 2;
+                s.phase = Start::DONE;
+                return;
+            }
             std::fill(s.H.begin(), s.H.end(), 0.0);
             for (int i = 0; i < n; ++i)
                 s.H[(size_t)i * n + i] = 1.0;
@@ -253,8 +263,10 @@ struct Search {
         cur.g = gl;
         cur.J = J;
         cur.C = C;
+        // a non-finite value or slope counts as a failed decrease (the step is too long)
+        const bool bad = !(isfinite(cur.f) && isfinite(cur.d));
         if (s.phase == Start::BRACKET) {
-            if (cur.f > s.f0 + kC1 * cur.a * s.g0 || (s.it > 0 && cur.f >= s.prev.f)) {
+            if (bad || cur.f > s.f0 + kC1 * cur.a * s.g0 || (s.it > 0 && cur.f >= s.prev.f)) {
                 start_zoom(s, s.prev, cur);
                 return;
             }
@@ -276,7 +288,7 @@ struct Search {
             return;
         }
         // ZOOM
-        if (cur.f > s.f0 + kC1 * cur.a * s.g0 || cur.f >= s.lo.f) {
+        if (bad || cur.f > s.f0 + kC1 * cur.a * s.g0 || cur.f >= s.lo.f) {
             s.hi = cur;
         } else {
             if (fabs(cur.d) <= -kC2 * s.g0) {

@@ -11,6 +11,9 @@
 // integrated by classical RK4 on the half-step sample grid (N at t_n, t_{n+1/2},
 // t_{n+1}).  The state is carried as delta = chi - e_1 (delta(t_i) = 0), the same
 // RK4 iterates, so that f = -delta_1 keeps its relative precision when f is small.
+// RK4 does not keep |chi| = 1: past |N| dt = 2 sqrt(2) it amplifies, and near a
+// zero of E, where R ~ |Ed| / |E|, that happens at any practical step; a mode
+// whose |chi(t_f)|^2 exceeds 1 + 1e-3 reports f = NaN.
 //
 // The gradient is the exact adjoint of the discrete forward map: the adjoint
 // state (final value -w(p) e_1, i.e. lambda_1(t_f) = -1 of Eq. (adj) times the
@@ -45,19 +48,25 @@ struct Coef {
     T Q, R, W2;  // W2 = 2 omega
 };
 
+// Reciprocal square root: correctly rounded in FP32 (a special-function
+// instruction and a correction instead of a square root and a division).
+__device__ __forceinline__ float rsq(float x) { return __frsqrt_rn(x); }
+__device__ __forceinline__ double rsq(double x) { return 1.0 / sqrt(x); }
+
 template <typename T>
 __device__ __forceinline__ Coef<T> coef_at(const QkeS<T> &s, T px, T py, T pz2, T eperp)
 {
     const T Px = px - s.ax, Py = py - s.ay;
     const T w2 = ((Px * Px + Py * Py) + pz2) + T(1);
-    const T w = sqrt(w2);
+    const T iw = rsq(w2);
     const T EP = s.ex * Px + s.ey * Py;
     const T X = w2 * s.ee - EP * EP;
     Coef<T> c;
-    c.W2 = T(2) * w;
+    c.W2 = T(2) * (w2 * iw);
     if (X > T(0)) {
-        c.Q = sqrt(X) / w2;
-        c.R = eperp * w * s.cr / X;
+        const T rX = rsq(X);
+        c.Q = (X * rX) * (iw * iw);
+        c.R = eperp * (w2 * iw) * s.cr * (rX * rX);
     } else {
         c.Q = T(0);
         c.R = T(0);
@@ -117,26 +126,28 @@ __device__ __forceinline__ void sample_sens(const QkeS<T> &s, T px, T py, T pz2,
 {
     const T Px = px - s.ax, Py = py - s.ay;
     const T w2 = ((Px * Px + Py * Py) + pz2) + T(1);
-    const T w = sqrt(w2);
+    const T iw = rsq(w2), w = w2 * iw, iw2 = iw * iw;
     const T EP = s.ex * Px + s.ey * Py;
     const T X = w2 * s.ee - EP * EP;
     const T P[2] = {Px, Py}, E[2] = {s.ex, s.ey};
     const T dcr_dE[2] = {s.edy, -s.edx}, dcr_dEd[2] = {-s.ey, s.ex};
     const T Qb = ab[0], Rb = ab[1], wb = ab[2];
     const bool pos = X > T(0);
-    const T sX = pos ? sqrt(X) : T(0);
-    const T iX = pos ? T(1) / X : T(0);
+    const T rX = pos ? rsq(X) : T(0);
+    const T sX = X * rX, iX = rX * rX;
+    const T hq = T(0.5) * rX * iw2;  // dQ/dX = 1 / (2 sqrt(X) omega^2)
+    const T cx = s.cr * iX;
 #pragma unroll
     for (int a = 0; a < 2; ++a) {
-        const T dw_dP = P[a] / w;
+        const T dw_dP = P[a] * iw;
         T dQ_dP = 0, dQ_dE = 0, dR_dP = 0, dR_dE = 0, dR_dEd = 0;
         if (pos) {
             const T dX_dP = T(2) * P[a] * s.ee - T(2) * EP * E[a];
             const T dX_dE = T(2) * w2 * E[a] - T(2) * EP * P[a];
-            dQ_dP = dX_dP / (T(2) * sX * w2) - sX * T(2) * P[a] / (w2 * w2);
-            dQ_dE = dX_dE / (T(2) * sX * w2);
+            dQ_dP = dX_dP * hq - sX * T(2) * P[a] * (iw2 * iw2);
+            dQ_dE = dX_dE * hq;
             // grouped so that no 1/X^2 is formed on its own (FP32 range)
-            dR_dP = eperp * (s.cr * iX) * (dw_dP - w * (dX_dP * iX));
+            dR_dP = eperp * cx * (dw_dP - w * (dX_dP * iX));
             dR_dE = eperp * w * iX * (dcr_dE[a] - s.cr * (dX_dE * iX));
             dR_dEd = eperp * w * dcr_dEd[a] * iX;
         }
@@ -144,6 +155,21 @@ __device__ __forceinline__ void sample_sens(const QkeS<T> &s, T px, T py, T pz2,
         out[2 + a] = Qb * dQ_dE + Rb * dR_dE;
         out[4 + a] = Rb * dR_dEd;
     }
+}
+
+// f = 1 - chi_1 = -delta_1, or NaN where RK4 let |chi|^2 = 1 + 2 delta_1 + |delta|^2
+// grow past 1 + 1e-3 (a step too coarse for the field: the discrete chi is no
+// longer a rotation and f has left its physical range).
+constexpr double kGrowthTol = 1e-3;
+
+template <typename T>
+__device__ __forceinline__ double density(const T d[6])
+{
+    T g = T(2) * d[0];
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+        g += d[i] * d[i];
+    return (double)g <= kGrowthTol ? -(double)d[0] : __longlong_as_double(0x7ff8000000000000ll);
 }
 
 template <typename T>
@@ -239,7 +265,7 @@ __global__ void __launch_bounds__(kQThreads) qke_forward_kernel(const QkeS<T> *_
         rk4_step(d, c0, ch, c1, (T)dt);
         c0 = c1;
     }
-    const double f = -(double)d[0];
+    const double f = density(d);
     if (mg.active && n_out)
         n_out[(size_t)c * nmodes + m] = f;
     const double s = cta_sum(mg.active ? mg.w * f : 0.0, red);
@@ -250,7 +276,7 @@ __global__ void __launch_bounds__(kQThreads) qke_forward_kernel(const QkeS<T> *_
 // Forward with checkpoints, then the backward sweep segment by segment.
 // ckpt[c][seg][6][nmp] (T), part[c][blk][6][ldg] (FP64), partJ[c][blk].
 template <typename T, int S>
-__global__ void __launch_bounds__(kQThreads) qke_adjoint_kernel(const QkeS<T> *__restrict__ tab, int ldt, int n_steps,
+__global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 2 : 1) qke_adjoint_kernel(const QkeS<T> *__restrict__ tab, int ldt, int n_steps,
                                                                 double dt_d, pp_grid g, T *__restrict__ ckpt, int nmp,
                                                                 double *__restrict__ part, int ldg,
                                                                 double *__restrict__ partJ)
@@ -288,7 +314,7 @@ __global__ void __launch_bounds__(kQThreads) qke_adjoint_kernel(const QkeS<T> *_
         }
     }
     {
-        const double s = cta_sum(mg.active ? mg.w * (-(double)d[0]) : 0.0, red);
+        const double s = cta_sum(mg.active ? mg.w * density(d) : 0.0, red);
         if (threadIdx.x == 0)
             partJ[(size_t)c * nblk + blk] = s;
     }

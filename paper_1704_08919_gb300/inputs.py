@@ -21,6 +21,12 @@ windows, Sec. V, scaled to the configurations below):
   network 32 -> 256 -> 256 -> 256 -> 1 trained on 50,000 seeded random pulses
   scored exactly (2,048 more held out), population 128, 8 proposals per
   individual per generation of which the network keeps one.
+* ``LOCAL_SEARCH``: the multistart augmented-Lagrangian search of Sec. IV.A on
+  the QKE: 16 starts, K = 8 (32 parameters), cubic B-splines on [0, 2], T = 50,
+  16384 RK4 steps (the QKE is stiff near zeros of E: at T = 200 and 8192 steps it
+  does not converge for such pulses), grid 32 x 32 x 16 over [-2, 2]^2 x [0, 2]
+  mirrored, U_const = 2.0, starts uniform in the bounds with the amplitudes
+  scaled to U_const.
 * ``DE_BATCH``: a population of 64 B-spline pulses (K = 8 control points per
   amplitude and phase per polarisation, cubic splines on [0, 2], T = 200,
   8192 RK4 steps, fluence 2.0) on a 64 x 64 x 32 grid over [-2, 2]^2 x [0, 2]
@@ -49,6 +55,14 @@ SURROGATE_DE = dict(
     NP=128, R=8, hidden=256, n_train=50000, n_heldout=2048, generations=60,
     epochs=60, batch=256, lr0=2e-3, lr1=5e-5,
     train_seed=424242, heldout_seed=434343, pop_seed=7, de_seed=77,
+)
+
+
+LOCAL_SEARCH = dict(
+    name="local search: 16 starts K=8 T=50 16384 steps grid 32x32x16, QKE adjoint + AL-BFGS",
+    nstart=16, K=8, order=4, w_min=0.0, w_max=2.0, T=50.0, n_steps=16384, U_const=2.0,
+    grid=dict(nx=32, ny=32, nz=16, x0=-2.0, x1=2.0, y0=-2.0, y1=2.0, z0=0.0, z1=2.0, mirror_z=1),
+    mu0=0.1, xi=0.5, outer=6, max_iter=30, gtol=1e-4, ctol=1e-3, seed=2024,
 )
 
 

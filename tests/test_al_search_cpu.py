@@ -99,3 +99,34 @@ def test_rejects_bad_options(lib):
         pp.al_search(np.zeros((1, 2)), rosen_obj, xi=1.5)
     with pytest.raises(pp.PPError):
         pp.al_search(np.zeros((1, 2)), rosen_obj, mu0=0.0)
+
+
+def test_native_optimizer_on_the_oracle_qke_objective(lib):
+    """On the real objective (the oracle's QKE augmented Lagrangian pieces, evaluated
+    row by row) the native optimiser and the oracle's take identical iterates."""
+    import oracle
+    from paper_1704_08919_gb300 import inputs
+    K = 4
+    sp = dict(K=K, order=3, w_min=0.0, w_max=2.0, T=20.0, fluence=1.0, n_steps=400)
+    grid = inputs.small_grid(3, 3, 2)
+    lo, hi, _ = inputs.param_bounds(K)
+    X = lo + np.random.default_rng(4).random((2, 4 * K)) * (hi - lo)
+    for x in X:
+        U0, _ = oracle.fluence_raw(x, K, 3, 0.0, 2.0, 20.0)
+        x[:K] *= math.sqrt(1.5 / U0)
+        x[2 * K:3 * K] *= math.sqrt(1.5 / U0)
+
+    def row(z):
+        o = oracle.al_objective(z, sp, grid, 2.0, 0.0, 1.0, nthreads=1)
+        return o["J"], o["gJ"], o["C"], o["gC"]
+
+    def batch(Z):
+        rs = [row(z) for z in Z]
+        return (np.array([r[0] for r in rs]), np.stack([r[1] for r in rs]),
+                np.array([r[2] for r in rs]), np.stack([r[3] for r in rs]))
+    kw = dict(mu0=0.1, xi=0.5, outer=2, max_iter=8, gtol=1e-8, ctol=1e-10)
+    r = pp.al_search(X, batch, **kw)
+    for i in range(2):
+        o = LS.augmented_lagrangian(row, X[i], **kw)
+        assert r["evals"][i] == o["evals"] and r["outer"][i] == o["outer"]
+        assert np.array_equal(r["x"][i], o["x"]) and r["J"][i] == o["J"] and r["lam"][i] == o["lam"]

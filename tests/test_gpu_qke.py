@@ -82,8 +82,10 @@ def test_fluence_and_chain_rule(pp):
         assert np.abs(dU[c] - dUo).max() < 1e-12 * np.abs(dUo).max()
 
 
-@pytest.mark.parametrize("n,grid", [(150, inputs.small_grid(17, 9, 3)),
-                                    (203, inputs.small_grid(5, 4, 3, mirror_z=0))])
+# Step counts resolve these fields (no mode is rejected for RK4 growth) and are
+# ragged against the checkpoint segments of the adjoint (4 and 8 steps).
+@pytest.mark.parametrize("n,grid", [(2003, inputs.small_grid(17, 9, 3)),
+                                    (2050, inputs.small_grid(5, 4, 3, mirror_z=0))])
 def test_qke_forward_matches_oracle(pp, n, grid):
     X = params(2, 4)
     A, E, Ed, _ = oracle.synth_raw(X, *ARGS, n)
@@ -95,6 +97,7 @@ def test_qke_forward_matches_oracle(pp, n, grid):
     f64 = f64.cpu().numpy().reshape(2, -1)
     for c in range(2):
         fo = oracle.qke6_modes(A[c], E[c], Ed[c], n, dt, p)
+        assert np.all(np.isfinite(fo))
         assert np.all(np.abs(f64[c] - fo) <= 1e-9 * np.abs(fo) + floor64(n))
         Jo = float(np.sum(w * fo))
         assert abs(J64[c].item() / Jo - 1) < 1e-9
@@ -102,25 +105,27 @@ def test_qke_forward_matches_oracle(pp, n, grid):
 
 
 def test_qke_agrees_with_dirac(pp):
-    """The two formalisms give the same pair density (Sec. II.B); at a small step both
-    RK4 discretisations are converged to well below the tolerance."""
-    n = 1600
-    X = params(2, 5)
-    grid = inputs.small_grid(8, 8, 4)
-    Xd = dev(X)
-    A, E, Ed, _ = pp.synth_field_raw(Xd, spec(n))
-    Jq, fq = pp.qke_pair_number(A, E, Ed, 20.0 / n, grid, "fp64", want_n=True)
-    Nd, fd = pp.pair_number(A, 20.0 / n, grid, precision="fp64", scheme="rk4", want_n=True)
+    """The two formalisms give the same pair density (Sec. II.B).  On the rotating
+    Gaussian, R = eps_perp omega (E x Ed)/X stays bounded (E x Ed = |E|^2 w), so
+    RK4 on the QKE converges as fast as on the Dirac equation; near a zero of a
+    general field R spikes and the QKE needs far smaller steps (see the oracle)."""
+    g = inputs.ROTATING_GAUSSIAN
+    ns = 8000
+    dt = (g["t1"] - g["t0"]) / ns
+    A, E, Ed = oracle.gaussian_rotating_field(g["E0"] * 3, g["w"], g["tau"], g["t0"], dt / 2, 2 * ns + 1)
+    grid = inputs.small_grid(8, 8, 4, ext=1.2)
+    Jq, fq = pp.qke_pair_number(dev(A[None]), dev(E[None]), dev(Ed[None]), dt, grid, "fp64", want_n=True)
+    Nd, fd = pp.pair_number(dev(A[None]), dt, grid, precision="fp64", scheme="rk4", want_n=True)
     assert pp.sync_status() == pp.PP_OK
-    assert torch.allclose(Jq, Nd, rtol=1e-6, atol=0)
+    assert abs(Jq.item() / Nd.item() - 1) < 1e-6
     assert (fq - fd).abs().max().item() < 1e-6 * fd.abs().max().item()
 
 
-@pytest.mark.parametrize("n,grid,nc", [(150, inputs.small_grid(17, 9, 3), 2),
-                                       (203, inputs.small_grid(6, 5, 2, mirror_z=0), 3),
-                                       (9, inputs.small_grid(3, 3, 1), 1)])
-def test_sample_gradient_matches_oracle(pp, n, grid, nc):
-    X = params(nc, 6)
+@pytest.mark.parametrize("n,grid,nc,U", [(2003, inputs.small_grid(17, 9, 3), 2, 2.0),
+                                         (2050, inputs.small_grid(6, 5, 2, mirror_z=0), 3, 2.0),
+                                         (65, inputs.small_grid(3, 3, 1), 1, 0.02)])
+def test_sample_gradient_matches_oracle(pp, n, grid, nc, U):
+    X = params(nc, 6, U=U)
     A, E, Ed, _ = oracle.synth_raw(X, *ARGS, n)
     p, w = oracle.grid_modes(grid)
     dt = 20.0 / n
@@ -139,7 +144,7 @@ def test_sample_gradient_matches_oracle(pp, n, grid, nc):
 
 
 def test_parameter_gradient_matches_oracle(pp):
-    n = 160
+    n = 2000
     grid = inputs.small_grid(6, 6, 3)
     X = params(3, 7)
     J, gJ, U, dU = pp.qke_gradient(dev(X), spec(n), grid, "fp64")
@@ -155,11 +160,11 @@ def test_parameter_gradient_matches_oracle(pp):
 
 
 def test_directional_derivative_at_full_size(pp):
-    """At the de-batch solver size (grid 64 x 64 x 32, 8192 steps, K = 8) the oracle
+    """At the local-search size (grid 32 x 32 x 16, 16384 steps, K = 8) the oracle
     cannot form the whole gradient; the property checked is the directional
     derivative: (J(x + h v) - J(x - h v)) / 2h = grad J . v."""
-    cfg = inputs.DE_BATCH
-    sp = dict(inputs.field_spec(cfg), fluence=1.0)
+    cfg = inputs.LOCAL_SEARCH
+    sp = dict(inputs.field_spec(dict(cfg, fluence=1.0)))
     Kf = cfg["K"]
     lo, hi, _ = inputs.param_bounds(Kf)
     rng = np.random.default_rng(8)
@@ -171,14 +176,14 @@ def test_directional_derivative_at_full_size(pp):
     x[2 * Kf:3 * Kf] *= s
     v = rng.normal(size=4 * Kf)
     v /= np.linalg.norm(v)
-    h = 1e-4
+    h = 1e-5
     X3 = dev(np.stack([x, x + h * v, x - h * v]))
     J, gJ, _, _ = pp.qke_gradient(X3[:1].contiguous(), sp, cfg["grid"], "fp64")
     Jp, _, _, _ = pp.qke_gradient(X3[1:].contiguous(), sp, cfg["grid"], "fp64", want_grad=False)
     assert pp.sync_status() == pp.PP_OK
     fd = (Jp[0].item() - Jp[1].item()) / (2 * h)
     an = float(gJ[0].cpu().numpy() @ v)
-    assert abs(fd - an) < 1e-5 * np.abs(gJ[0].cpu().numpy()).sum()
+    assert abs(fd - an) < 1e-5 * np.abs(gJ[0].cpu().numpy()).sum(), (fd, an)
     # f at sampled modes against the oracle's forward solve at this size
     A, E, Ed, _ = pp.synth_field_raw(X3[:1].contiguous(), sp)
     _, f = pp.qke_pair_number(A, E, Ed, sp["T"] / sp["n_steps"], cfg["grid"], "fp64", want_n=True)
@@ -190,24 +195,62 @@ def test_directional_derivative_at_full_size(pp):
     assert np.all(np.abs(fg - fo) <= 1e-9 * np.abs(fo) + floor64(sp["n_steps"]))
 
 
-def test_local_search_matches_oracle(pp):
+def _qke_obj(n, grid):
+    def obj(z):
+        o = oracle.al_objective(z, spec(n), grid, 2.0, 0.0, 1.0)
+        return o["J"], o["gJ"], o["C"], o["gC"]
+    return obj
+
+
+def test_local_search_first_iterates_match_oracle(pp):
     """The GPU local search and the oracle's (same algorithm, FP64 objective from the
-    oracle) reach the same constrained maximum from the same starts."""
-    n = 100
+    oracle) take the same first BFGS iterates from the same starts: the objectives
+    differ only by rounding, which cannot flip a line-search decision this early."""
+    n = 2000
     grid = inputs.small_grid(4, 4, 2)
-    starts = params(2, 9, U=1.5)
-    kw = dict(mu0=1.0, xi=0.5, outer=8, max_iter=60, gtol=1e-6, ctol=1e-7)
+    starts = params(3, 9, U=1.5)
+    kw = dict(mu0=0.1, xi=0.5, outer=1, max_iter=3, gtol=1e-12, ctol=1e-12)
     r = pp.local_search(starts, spec(n), grid, 2.0, precision="fp64", **kw)
     assert pp.sync_status() == pp.PP_OK
-    for i in range(2):
-        def obj(z):
-            o = oracle.al_objective(z, spec(n), grid, 2.0, 0.0, 1.0)
-            return o["J"], o["gJ"], o["C"], o["gC"]
-        o = LS.augmented_lagrangian(obj, starts[i], **kw)
-        assert r["status"][i] == 0 and abs(r["C"][i]) <= 1e-7
-        assert abs(r["J"][i] / o["J"] - 1) < 1e-5
-        J0 = oracle.al_objective(starts[i], spec(n), grid, 2.0, 0.0, 1.0)["J"]
-        assert r["J"][i] > J0
+    for i in range(3):
+        o = LS.augmented_lagrangian(_qke_obj(n, grid), starts[i], **kw)
+        assert r["evals"][i] == o["evals"]
+        assert np.abs(r["x"][i] - o["x"]).max() < 1e-7 * np.abs(o["x"]).max()
+        assert abs(r["J"][i] / o["J"] - 1) < 1e-8
+
+
+def test_local_search_improves_and_holds_the_fluence(pp):
+    n = 2000
+    grid = inputs.small_grid(4, 4, 2)
+    starts = params(4, 10, U=2.0)  # start 1 has rejected modes: J is NaN there
+    J0 = [oracle.al_objective(x, spec(n), grid, 2.0, 0.0, 1.0)["J"] for x in starts]
+    r = pp.local_search(starts, spec(n), grid, 2.0, precision="fp32", mu0=0.1, xi=0.5, outer=6,
+                        max_iter=30, gtol=1e-4, ctol=1e-3)
+    assert pp.sync_status() == pp.PP_OK
+    ok = np.isfinite(r["J"])
+    assert ok.sum() >= 3
+    assert np.all(r["status"][~ok] == 2) and np.all(np.isnan(np.array(J0)[~ok]))
+    assert np.all(r["J"][ok] > np.array(J0)[ok])
+    assert np.all(np.abs(r["C"][ok]) < 0.05 * 2.0)
+    # the result's J by the oracle agrees with the GPU's FP32 value
+    for i in np.nonzero(ok)[0]:
+        Jo = oracle.al_objective(r["x"][i], spec(n), grid, 2.0, 0.0, 1.0)["J"]
+        assert abs(r["J"][i] / Jo - 1) < 1e-3
+
+
+def test_rk4_growth_is_rejected_like_the_oracle(pp):
+    """A field far too strong for the step: the oracle and the GPU (both precisions)
+    report NaN for the same modes; J is NaN."""
+    n = 40
+    X = params(1, 5) * np.r_[[30.0] * K, [1.0] * K, [30.0] * K, [1.0] * K]
+    A, E, Ed, _ = oracle.synth_raw(X, *ARGS, n)
+    grid = inputs.small_grid(3, 3, 2)
+    p, _ = oracle.grid_modes(grid)
+    fo = oracle.qke6_modes(A[0], E[0], Ed[0], n, 20.0 / n, p)
+    J, f = pp.qke_pair_number(dev(A), dev(E), dev(Ed), 20.0 / n, grid, "fp64", want_n=True)
+    assert pp.sync_status() != pp.PP_ERR_CUDA
+    assert np.isnan(fo).any() and np.array_equal(np.isnan(f.cpu().numpy().reshape(-1)), np.isnan(fo))
+    assert math.isnan(J.item())
 
 
 def test_rejects_bad_arguments(pp):
