@@ -68,6 +68,10 @@ def parse():
     ap.add_argument("--train", type=int, default=None, help="surrogate: training pulses")
     ap.add_argument("--generations", type=int, default=None, help="surrogate: DE generations")
     ap.add_argument("--seeds", type=int, default=3, help="surrogate: DE runs (seeds) per form")
+    ap.add_argument("--eval-only", action="store_true",
+                    help="localsearch: time the batched gradient evaluation only (no search)")
+    ap.add_argument("--small", action="store_true",
+                    help="localsearch: a 16 x 16 x 8 grid (profiling runs)")
     ap.add_argument("--screen", default="individual", choices=["individual", "global"],
                     help="surrogate: screening mode reported as the value")
     ap.add_argument("--online", type=int, default=0,
@@ -380,12 +384,12 @@ def gemm_measure(pp, torch, reps=20):
     return out
 
 
-# FP32 operations per mode-step of the QKE adjoint kernel, counted from its source
-# (no FMA contraction: every multiply and add is one instruction): forward pass
-# 186 (2 coefficient sets, 4 matrix products, stage updates), the recomputed
-# forward 186, the backward step 611 (2 coefficient sets, 3 + 4 matrix products,
-# 4 coefficient adjoints, 2 sample sensitivities, 12 warp sums).
-QKE_ADJ_FLOP = 983
+# FP32 work per mode-step of the QKE adjoint kernel (forward pass, recomputed
+# forward and backward step), from the kernel's executed SASS counts (ncu,
+# 1.342e8 mode-steps): 355 FFMA + 320 FMUL + 171 FADD thread-instructions,
+# i.e. 1201 flop (FMA = 2) in 846 FP32 instructions.
+QKE_ADJ_FLOP = 1201
+QKE_ADJ_FP32_INSTR = 846
 
 
 def localsearch_main(args):
@@ -400,7 +404,10 @@ def localsearch_main(args):
     torch.cuda.set_device(local)
     pp.lib()
     sp = inputs.field_spec(dict(L, fluence=1.0))
-    K, S = L["K"], L["nstart"]
+    K = L["K"]
+    S = args.ncand if args.ncand != CFG["NP"] else L["nstart"]
+    if args.small:
+        L = dict(L, grid=dict(L["grid"], nx=16, ny=16, nz=8))
     prec = "fp64" if args.precision == "fp64" else "fp32"
     X = inputs.random_population(S, K, seed=L["seed"])
     Xd = torch.tensor(X, device="cuda")
@@ -427,15 +434,18 @@ def localsearch_main(args):
     clocks = ClockSampler(local)
     clocks.start()
     t0 = time.perf_counter()
-    r = pp.local_search(X, sp, L["grid"], L["U_const"], precision=prec, mu0=L["mu0"], xi=L["xi"],
-                        outer=L["outer"], max_iter=L["max_iter"], gtol=L["gtol"], ctol=L["ctol"])
+    if args.eval_only:
+        r = None
+    else:
+        r = pp.local_search(X, sp, L["grid"], L["U_const"], precision=prec, mu0=L["mu0"], xi=L["xi"],
+                            outer=L["outer"], max_iter=L["max_iter"], gtol=L["gtol"], ctol=L["ctol"])
     wall = time.perf_counter() - t0
     clk = clocks.stop()
     if pp.sync_status() != pp.PP_OK:
         raise RuntimeError("device status after the local search")
     J0 = J0.cpu().numpy()
     achieved = QKE_ADJ_FLOP * mode_steps / (eval_ms * 1e-3) / 1e12
-    peak = SM_COUNT * FP32_LANES_PER_SM * 2070e6 / 1e12
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
     print(json.dumps({
         "metric": "local-search gradient evaluations/s (QKE forward + adjoint, all starts batched)",
         "value": S / (eval_ms * 1e-3), "unit": "gradients/s", "n_gpus": 1, "steps": reps,
@@ -448,14 +458,18 @@ def localsearch_main(args):
         "mode_steps_per_s": mode_steps / (eval_ms * 1e-3),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
-                     "note": "%d FP32 operations per mode-step counted from the source, no FMA; "
-                             "peak = 152 SMs x 128 lanes x 2070 MHz, one operation per lane-cycle"
-                             % QKE_ADJ_FLOP},
-        "search": {"seconds": wall, "evals_total": int(r["evals"].sum()),
-                   "J_start": [float(v) for v in J0], "J_end": [float(v) for v in r["J"]],
-                   "C_end": [float(v) for v in r["C"]], "status": [int(v) for v in r["status"]],
-                   "outer": [int(v) for v in r["outer"]], "best_J": float(np.max(r["J"][r["status"] == 0]))
-                   if np.any(r["status"] == 0) else None},
+                     "pipe_frac": QKE_ADJ_FP32_INSTR * mode_steps / (eval_ms * 1e-3)
+                     / (SM_COUNT * FP32_LANES_PER_SM * 2070e6),
+                     "note": "%d FP32 flop (%d instructions) per mode-step from ncu SASS counts; "
+                             "whole evaluation (synthesis, adjoint, chain rule) timed; "
+                             "peak = 152 SMs x 128 lanes x 2 flop x 2070 MHz"
+                             % (QKE_ADJ_FLOP, QKE_ADJ_FP32_INSTR)},
+        "search": None if r is None else {
+            "seconds": wall, "evals_total": int(r["evals"].sum()),
+            "J_start": [float(v) for v in J0], "J_end": [float(v) for v in r["J"]],
+            "C_end": [float(v) for v in r["C"]], "status": [int(v) for v in r["status"]],
+            "outer": [int(v) for v in r["outer"]],
+            "best_J": float(np.max(r["J"][r["status"] == 0])) if np.any(r["status"] == 0) else None},
         "clocks": clk}), flush=True)
     return 0
 
