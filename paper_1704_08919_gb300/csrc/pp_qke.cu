@@ -250,7 +250,9 @@ __global__ void __launch_bounds__(kQThreads) qke_forward_kernel(const QkeS<T> *_
                                                                 double dt, pp_grid g, double *__restrict__ n_out,
                                                                 double *__restrict__ part)
 {
+    constexpr int kTile = 32;  // steps per staged tile
     __shared__ double red[kQWarps];
+    __shared__ QkeS<T> seg[2 * kTile + 1];
     const int c = blockIdx.y, blk = blockIdx.x;
     const int nmodes = g.nx * g.ny * g.nz;
     const int m = blk * kQThreads + threadIdx.x;
@@ -259,11 +261,18 @@ __global__ void __launch_bounds__(kQThreads) qke_forward_kernel(const QkeS<T> *_
     const QkeS<T> *tr = tab + (size_t)c * ldt;
     T d[6] = {0, 0, 0, 0, 0, 0};
     Coef<T> c0 = coef_at(tr[0], px, py, pz2, eperp);
-    for (int n = 0; n < n_steps; ++n) {
-        const Coef<T> ch = coef_at(tr[2 * n + 1], px, py, pz2, eperp);
-        const Coef<T> c1 = coef_at(tr[2 * n + 2], px, py, pz2, eperp);
-        rk4_step(d, c0, ch, c1, (T)dt);
-        c0 = c1;
+    for (int n0 = 0; n0 < n_steps; n0 += kTile) {
+        const int cnt = min(kTile, n_steps - n0);
+        __syncthreads();
+        if (threadIdx.x < 2 * cnt + 1)
+            seg[threadIdx.x] = tr[2 * n0 + threadIdx.x];
+        __syncthreads();
+        for (int q = 0; q < cnt; ++q) {
+            const Coef<T> ch = coef_at(seg[2 * q + 1], px, py, pz2, eperp);
+            const Coef<T> c1 = coef_at(seg[2 * q + 2], px, py, pz2, eperp);
+            rk4_step(d, c0, ch, c1, (T)dt);
+            c0 = c1;
+        }
     }
     const double f = density(d);
     if (mg.active && n_out)
@@ -283,6 +292,7 @@ __global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 2 : 1) qke_adjoint
 {
     __shared__ double red[kQWarps];
     __shared__ double sb[kQWarps][2 * S][6];
+    __shared__ QkeS<T> seg[2 * S + 1];  // the samples of the current segment (broadcast reads)
     const int c = blockIdx.y, blk = blockIdx.x, nblk = gridDim.x;
     const int m = blk * kQThreads + threadIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -293,6 +303,12 @@ __global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 2 : 1) qke_adjoint
     const int nseg = (n_steps + S - 1) / S;
     const int mm = min(m, nmp - 1);  // inactive threads store into a valid slot they own alone
     T *ck = ckpt + (size_t)c * nseg * 6 * nmp;
+    auto stage = [&](int n0, int cnt) {  // samples 2 n0 .. 2 (n0 + cnt) into shared memory
+        __syncthreads();
+        if (threadIdx.x < 2 * cnt + 1)
+            seg[threadIdx.x] = tr[2 * n0 + threadIdx.x];
+        __syncthreads();
+    };
 
     // ---- phase A: forward, keeping the state at the start of every segment
     T d[6] = {0, 0, 0, 0, 0, 0};
@@ -304,10 +320,10 @@ __global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 2 : 1) qke_adjoint
                 for (int i = 0; i < 6; ++i)
                     ck[((size_t)s * 6 + i) * nmp + mm] = d[i];
             const int n0 = s * S, cnt = min(S, n_steps - n0);
+            stage(n0, cnt);
             for (int q = 0; q < cnt; ++q) {
-                const int n = n0 + q;
-                const Coef<T> ch = coef_at(tr[2 * n + 1], px, py, pz2, eperp);
-                const Coef<T> c1 = coef_at(tr[2 * n + 2], px, py, pz2, eperp);
+                const Coef<T> ch = coef_at(seg[2 * q + 1], px, py, pz2, eperp);
+                const Coef<T> c1 = coef_at(seg[2 * q + 2], px, py, pz2, eperp);
                 rk4_step(d, c0, ch, c1, dt);
                 c0 = c1;
             }
@@ -330,17 +346,17 @@ __global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 2 : 1) qke_adjoint
 #pragma unroll
         for (int i = 0; i < 6; ++i)
             d[i] = mg.active ? ck[((size_t)s * 6 + i) * nmp + mm] : T(0);
+        stage(n0, cnt);
         {
-            Coef<T> c0 = coef_at(tr[2 * n0], px, py, pz2, eperp);
+            Coef<T> c0 = coef_at(seg[0], px, py, pz2, eperp);
 #pragma unroll
             for (int q = 0; q < S; ++q) {
                 if (q < cnt) {
 #pragma unroll
                     for (int i = 0; i < 6; ++i)
                         st[q][i] = d[i];
-                    const int n = n0 + q;
-                    const Coef<T> ch = coef_at(tr[2 * n + 1], px, py, pz2, eperp);
-                    const Coef<T> cn = coef_at(tr[2 * n + 2], px, py, pz2, eperp);
+                    const Coef<T> ch = coef_at(seg[2 * q + 1], px, py, pz2, eperp);
+                    const Coef<T> cn = coef_at(seg[2 * q + 2], px, py, pz2, eperp);
                     rk4_step(d, c0, ch, cn, dt);
                     c0 = cn;
                 }
@@ -349,8 +365,7 @@ __global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 2 : 1) qke_adjoint
 #pragma unroll
         for (int q = S - 1; q >= 0; --q) {
             if (q < cnt) {
-                const int n = n0 + q;
-                const QkeS<T> e0 = tr[2 * n], eh = tr[2 * n + 1], e1 = tr[2 * n + 2];
+                const QkeS<T> e0 = seg[2 * q], eh = seg[2 * q + 1], e1 = seg[2 * q + 2];
                 const Coef<T> c0 = coef_at(e0, px, py, pz2, eperp);
                 const Coef<T> ch = coef_at(eh, px, py, pz2, eperp);
                 const T *x = st[q];
