@@ -22,7 +22,7 @@
 // S_Q, S_R, S_W are the adjoints of Q, R, omega -- the inner product
 // <chi, grad N lambda> of Eq. (grad) taken stage by stage.  The forward states
 // are kept at every S-th step (checkpoints in HBM) and recomputed a segment at a
-// time into registers for the backward sweep.  Each sample's six sensitivities
+// time into per-thread shared-memory slots for the backward sweep.  Each sample's six sensitivities
 // are summed over the CTA's modes (warp shuffles, then warps in fixed order) into
 // a per-CTA row; a second kernel sums the rows in fixed order.
 #include <math.h>
@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(kQThreads) qke_forward_kernel(const QkeS<T> *_
 // Forward with checkpoints, then the backward sweep segment by segment.
 // ckpt[c][seg][6][nmp] (T), part[c][blk][6][ldg] (FP64), partJ[c][blk].
 template <typename T, int S>
-__global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 2 : 1) qke_adjoint_kernel(const QkeS<T> *__restrict__ tab, int ldt, int n_steps,
+__global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 3 : 1) qke_adjoint_kernel(const QkeS<T> *__restrict__ tab, int ldt, int n_steps,
                                                                 double dt_d, pp_grid g, T *__restrict__ ckpt, int nmp,
                                                                 double *__restrict__ part, int ldg,
                                                                 double *__restrict__ partJ)
@@ -293,6 +293,9 @@ __global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 2 : 1) qke_adjoint
     __shared__ double red[kQWarps];
     __shared__ double sb[kQWarps][2 * S][6];
     __shared__ QkeS<T> seg[2 * S + 1];  // the samples of the current segment (broadcast reads)
+    // the segment's recomputed states, one slot per thread: sst[(q * 6 + i) * kQThreads + tid]
+    extern __shared__ __align__(16) unsigned char qke_dyn[];
+    T *sst = reinterpret_cast<T *>(qke_dyn);
     const int c = blockIdx.y, blk = blockIdx.x, nblk = gridDim.x;
     const int m = blk * kQThreads + threadIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -342,33 +345,33 @@ __global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 2 : 1) qke_adjoint
     Coef<T> c1 = coef_at(tr[2 * n_steps], px, py, pz2, eperp);
     for (int s = nseg - 1; s >= 0; --s) {
         const int n0 = s * S, cnt = min(S, n_steps - n0);
-        T st[S][6];
 #pragma unroll
         for (int i = 0; i < 6; ++i)
             d[i] = mg.active ? ck[((size_t)s * 6 + i) * nmp + mm] : T(0);
         stage(n0, cnt);
         {
             Coef<T> c0 = coef_at(seg[0], px, py, pz2, eperp);
+#pragma unroll 1
+            for (int q = 0; q < cnt; ++q) {
 #pragma unroll
-            for (int q = 0; q < S; ++q) {
-                if (q < cnt) {
-#pragma unroll
-                    for (int i = 0; i < 6; ++i)
-                        st[q][i] = d[i];
-                    const Coef<T> ch = coef_at(seg[2 * q + 1], px, py, pz2, eperp);
-                    const Coef<T> cn = coef_at(seg[2 * q + 2], px, py, pz2, eperp);
-                    rk4_step(d, c0, ch, cn, dt);
-                    c0 = cn;
-                }
+                for (int i = 0; i < 6; ++i)
+                    sst[(q * 6 + i) * kQThreads + threadIdx.x] = d[i];
+                const Coef<T> ch = coef_at(seg[2 * q + 1], px, py, pz2, eperp);
+                const Coef<T> cn = coef_at(seg[2 * q + 2], px, py, pz2, eperp);
+                rk4_step(d, c0, ch, cn, dt);
+                c0 = cn;
             }
         }
-#pragma unroll
-        for (int q = S - 1; q >= 0; --q) {
-            if (q < cnt) {
+#pragma unroll 1
+        for (int q = cnt - 1; q >= 0; --q) {
+            {
                 const QkeS<T> e0 = seg[2 * q], eh = seg[2 * q + 1], e1 = seg[2 * q + 2];
                 const Coef<T> c0 = coef_at(e0, px, py, pz2, eperp);
                 const Coef<T> ch = coef_at(eh, px, py, pz2, eperp);
-                const T *x = st[q];
+                T x[6];
+#pragma unroll
+                for (int i = 0; i < 6; ++i)
+                    x[i] = sst[(q * 6 + i) * kQThreads + threadIdx.x];
                 T k1[6], k2[6], k3[6], y2[6], y3[6], y4[6];
                 nmul(c0, x, T(1), k1);
 #pragma unroll
@@ -556,9 +559,14 @@ int gradient(const double *A, const double *E, const double *Ed, int ncand, int 
         rc = pp::scratch(pp::SCR_QKE_X, sizeof(double) * (size_t)nblk * chunk, &pj);
     if (rc)
         return rc;
+    const size_t dyn = sizeof(T) * S * 6 * kQThreads;
+    cudaError_t ea = cudaFuncSetAttribute(qke_adjoint_kernel<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)dyn);
+    if (ea != cudaSuccess)
+        return pp::cuda_fail(ea, "QKE adjoint shared memory");
     for (int c0 = 0; c0 < ncand; c0 += chunk) {
         const int nc = std::min(chunk, ncand - c0);
-        qke_adjoint_kernel<T, S><<<dim3(nblk, nc), kQThreads, 0, st>>>(
+        qke_adjoint_kernel<T, S><<<dim3(nblk, nc), kQThreads, dyn, st>>>(
             (const QkeS<T> *)tab + (size_t)c0 * ldt, ldt, n_steps, dt, *g, (T *)ck, nmodes, (double *)part, ldg,
             (double *)pj);
         sum_blocks_kernel<<<dim3(nbk(6ll * ldg), nc), 256, 0, st>>>((const double *)part, nblk, 6ll * ldg,
