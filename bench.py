@@ -61,7 +61,7 @@ def parse():
                     help="modes of one candidate in the CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="de-batch", choices=["de-batch", "uneven", "surrogate", "gemm", "localsearch"],
+    ap.add_argument("--workload", default="de-batch", choices=["de-batch", "uneven", "surrogate", "gemm", "localsearch", "large"],
                     help="de-batch: the 64-candidate DE generation (default); uneven: 128 slots "
                          "of uneven length and grid, generations in one CUDA graph; surrogate: "
                          "exact calls of surrogate-screened DE against plain DE")
@@ -474,6 +474,92 @@ def localsearch_main(args):
     return 0
 
 
+def large_main(args):
+    """The large-scale configuration: population 1024, K = 16, T = 400 (20000 steps),
+    grid 128 x 128 x 64, surrogate-screened DE.  Scores the initial population, fits
+    the network on those exact evaluations (the refit that would recur every 20
+    generations), runs --steps full generations (default 2) and extrapolates the
+    wall-clock of the configured 200 generations."""
+    import torch
+    import paper_1704_08919_gb300 as pp
+    from paper_1704_08919_gb300 import screening as scr
+    Lg = inputs.LARGE_SCALE
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    pp.lib()
+    spec, grid = inputs.field_spec(Lg), Lg["grid"]
+    K, D, NP, R = Lg["K"], 4 * Lg["K"], Lg["NP"], Lg["R"]
+    G = args.steps
+    prec, sch = args.precision, args.scheme
+    lo, hi, per = (torch.tensor(x, device="cuda") for x in inputs.param_bounds(K))
+    pop = torch.tensor(inputs.random_population(NP, K, seed=Lg["pop_seed"]), device="cuda")
+    dt = spec["T"] / spec["n_steps"]
+    modes = grid["nx"] * grid["ny"] * grid["nz"]
+    clocks = ClockSampler(local)
+    clocks.start()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    A, _, _ = pp.synth_field(pop, spec)
+    fit, _ = pp.pair_number(A, dt, grid, precision=prec, scheme=sch)
+    e1.record(st)
+    torch.cuda.synchronize()
+    init_ms = e0.elapsed_time(e1)
+    del A
+    lt = scr.LogTarget(fit)
+    net = pp.Surrogate(D, 256, max_batch=R * NP)
+    net.init(5)
+    X = pp.mlp_features(pop, lo, hi)
+    t = lt.targets(pp, fit)
+    t0 = time.perf_counter()
+    net.fit(X, t, 256, 200, 2e-3, 5e-5)
+    torch.cuda.synchronize()
+    fit_s = time.perf_counter() - t0
+    trial = torch.empty_like(pop)
+    tfit = torch.empty_like(fit)
+    best = [fit.max().item()]
+    gen_ms = []
+    for g in range(G):
+        e0.record(st)
+        pp.de_screened_step(pop, fit, spec, grid, lo, hi, per, Lg["F"], Lg["CR"], Lg["de_seed"], g, R, net,
+                            precision=prec, scheme=sch, trial_out=trial, trial_fit_out=tfit)
+        e1.record(st)
+        torch.cuda.synchronize()
+        gen_ms.append(e0.elapsed_time(e1))
+        best.append(fit.max().item())
+    clk = clocks.stop()
+    if pp.sync_status() != pp.PP_OK:
+        raise RuntimeError("device status after the large-scale run")
+    # accuracy: two scored trials of the last generation, this path against FP64 RK4
+    idx = [0, 1]
+    Ac, _, _ = pp.synth_field(trial[idx].contiguous(), spec)
+    N64, _ = pp.pair_number(Ac, dt, grid, precision="fp64", scheme="rk4")
+    rel = float((tfit[idx] / N64 - 1).abs().max().item())
+    ms = statistics.mean(gen_ms)
+    print(json.dumps({
+        "metric": "candidate pulses scored/s (large-scale configuration, screened DE)",
+        "value": NP / (ms * 1e-3), "unit": "candidates/s", "n_gpus": 1, "steps": G, "warmup": 0,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "none", "vs_baseline": None,
+        "dtype": "f32" if prec != "fp64" else "f64", "data": "synthetic (seeded B-spline pulses)",
+        "config": {"workload": Lg["name"], "precision": prec, "scheme": sch, "NP": NP, "K": K,
+                   "T": Lg["T"], "n_steps": Lg["n_steps"], "grid": "128x128x64 over [-2.5,2.5]^2 x [0,2.5]",
+                   "R": R, "generations_run": G, "generations_configured": Lg["generations"]},
+        "mode_steps_per_s": NP * modes * Lg["n_steps"] / (ms * 1e-3),
+        "generation_ms": gen_ms, "initial_population_ms": init_ms, "surrogate_fit_s": fit_s,
+        "best_N": best, "n_rel_err_vs_fp64_rk4_max": rel,
+        "extrapolated_hours_for_configured_generations":
+            (init_ms + ms * Lg["generations"]) / 3.6e6
+            + fit_s * (Lg["generations"] // Lg["refit_every"]) / 3600.0,
+        "note": "%d of %d generations run; the rest extrapolated from their mean time (the network "
+                "refits every %d generations, at the measured fit time)"
+                % (G, Lg["generations"], Lg["refit_every"]),
+        "clocks": clk}), flush=True)
+    return 0
+
+
 def gemm_main(args):
     import torch
     import paper_1704_08919_gb300 as pp
@@ -587,6 +673,8 @@ def main():
         return gemm_main(args)
     if args.workload == "localsearch":
         return localsearch_main(args)
+    if args.workload == "large":
+        return large_main(args)
     import torch
     import paper_1704_08919_gb300 as pp
 

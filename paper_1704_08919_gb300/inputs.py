@@ -27,6 +27,11 @@ windows, Sec. V, scaled to the configurations below):
   does not converge for such pulses), grid 32 x 32 x 16 over [-2, 2]^2 x [0, 2]
   mirrored, U_const = 2.0, starts uniform in the bounds with the amplitudes
   scaled to U_const.
+* ``LARGE_SCALE``: population 1024, K = 16 (64 parameters), cubic B-splines on
+  [0, 2], T = 400, 20000 steps, fluence 2.0, grid 128 x 128 x 64 over
+  [-2.5, 2.5]^2 x [0, 2.5] mirrored, DE F = 0.8, CR = 0.9, surrogate-screened
+  (8 proposals per individual) with the network refitted every 20 generations on
+  the pulses scored so far.
 * ``DE_BATCH``: a population of 64 B-spline pulses (K = 8 control points per
   amplitude and phase per polarisation, cubic splines on [0, 2], T = 200,
   8192 RK4 steps, fluence 2.0) on a 64 x 64 x 32 grid over [-2, 2]^2 x [0, 2]
@@ -63,6 +68,14 @@ LOCAL_SEARCH = dict(
     nstart=16, K=8, order=4, w_min=0.0, w_max=2.0, T=50.0, n_steps=16384, U_const=2.0,
     grid=dict(nx=32, ny=32, nz=16, x0=-2.0, x1=2.0, y0=-2.0, y1=2.0, z0=0.0, z1=2.0, mirror_z=1),
     mu0=0.1, xi=0.5, outer=6, max_iter=30, gtol=1e-4, ctol=1e-3, seed=2024,
+)
+
+
+LARGE_SCALE = dict(
+    name="large-scale: pop 1024 K=16 T=400 20000 steps grid 128x128x64, screened DE (R=8)",
+    NP=1024, K=16, order=4, w_min=0.0, w_max=2.0, T=400.0, fluence=2.0, n_steps=20000,
+    F=0.8, CR=0.9, R=8, generations=200, refit_every=20, pop_seed=31, de_seed=310,
+    grid=dict(nx=128, ny=128, nz=64, x0=-2.5, x1=2.5, y0=-2.5, y1=2.5, z0=0.0, z1=2.5, mirror_z=1),
 )
 
 
