@@ -16,10 +16,10 @@
 // descriptor's leading-dimension offset) and the row groups 1024 B apart (its
 // stride offset).
 //
-// One CTA of 128 threads computes 128 rows x N columns (N <= 256): warp 0
-// allocates N TMEM columns, thread 0 issues 4 MMAs (K = 16 each) per 64-wide
-// K chunk while the next chunk's tiles are copied (two stages), each warp then
-// reads its 32 TMEM lanes with tcgen05.ld and writes its rows of D.
+// One CTA of 128 threads computes a 128 x 128 block of D (the last column block
+// may be narrower): warp 0 allocates its TMEM columns, thread 0 issues 4 MMAs
+// (K = 16 each) per 64-wide K chunk from a 3-stage ring of bulk copies, each warp
+// then reads its 32 TMEM lanes with tcgen05.ld and writes its rows of D.
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -107,34 +107,40 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
         v[i] = __uint_as_float(r[i]);
 }
 
-// Shared-memory plan: 2 stages x (A tile 16 KiB + B tiles up to 2 x 16 KiB), barriers.
-constexpr int kStageBytes = kTileBytes * 3;
-constexpr int kSmemBytes = 2 * kStageBytes + 1024 + 64;
+// Shared-memory plan: a ring of kStages stages x (A tile 16 KiB + B tile 16 KiB) and
+// the barriers; two CTAs fit on an SM.
+constexpr int kStages = 3;
+constexpr int kBN = 128;                      // columns per CTA (one packed B tile)
+constexpr int kStageBytes = 2 * kTileBytes;
+constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 128;
 
-__global__ void __launch_bounds__(128, 1)
+// One CTA: rows [128 mt, 128 mt + 128) x columns [128 nt, 128 nt + nc), nc = min(128, N - 128 nt).
+// Thread 0 keeps kStages chunks in flight: after issuing chunk ch's MMAs it waits for
+// chunk ch-1's MMAs to finish reading their stage and refills that stage with chunk
+// ch-1+kStages, so the tensor pipe always has the next chunk queued.
+__global__ void __launch_bounds__(128, 2)
     gemm_bf16_kernel(const uint8_t *__restrict__ A, const uint8_t *__restrict__ B, float *__restrict__ D,
                      int M, int N, int K, int ldd, long long wait_limit, unsigned int *__restrict__ status)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t *full = (uint64_t *)(smem + 2 * kStageBytes);  // [2] copies landed
-    uint64_t *done = full + 2;                              // [2] MMAs of a stage finished
-    uint32_t *s_taddr = (uint32_t *)(done + 2);
+    uint64_t *full = (uint64_t *)(smem + kStages * kStageBytes);  // [kStages] copies landed
+    uint64_t *done = full + kStages;                              // [kStages] MMAs of a stage finished
+    uint32_t *s_taddr = (uint32_t *)(done + kStages);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int mt = blockIdx.x;              // row tile
+    const int mt = blockIdx.x, nt = blockIdx.y;
+    const int nc = min(kBN, N - nt * kBN);  // a multiple of 16 in [16, 128]
     const int nchunks = K / kKC;
-    const int ntiles_b = (N + kBM - 1) / kBM;
-    const int kchunks_total = K / kKC;      // packed chunks per row tile
-    const uint32_t ncols = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
+    const uint32_t ncols = nc <= 32 ? 32 : (nc <= 64 ? 64 : 128);
 
     if (warp == 0)
         tmem_alloc(s_taddr, ncols);
     if (tid == 0) {
-        mbar_init(&full[0], 1);
-        mbar_init(&full[1], 1);
-        mbar_init(&done[0], 1);
-        mbar_init(&done[1], 1);
+        for (int i = 0; i < kStages; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&done[i], 1);
+        }
         mbar_fence_init();
     }
     tc_fence_before();
@@ -142,28 +148,25 @@ __global__ void __launch_bounds__(128, 1)
     tc_fence_after();
     const uint32_t taddr = *s_taddr;
 
-    const uint32_t stage_bytes = (uint32_t)kTileBytes * (1 + ntiles_b);
-    int last_issue[2] = {-1, -1}, last_commit[2] = {-1, -1};  // thread 0's bookkeeping
+    int last_issue[kStages], last_commit[kStages];  // thread 0's bookkeeping for the drain
+    for (int i = 0; i < kStages; ++i)
+        last_issue[i] = last_commit[i] = -1;
     auto issue_copy = [&](int ch, int st) {
         uint8_t *sa = smem + st * kStageBytes;
         last_issue[st] = ch;
-        mbar_arrive_expect_tx(&full[st], stage_bytes);
-        bulk_copy_g2s(sa, A + ((size_t)mt * kchunks_total + ch) * kTileBytes, kTileBytes, &full[st]);
-        for (int t = 0; t < ntiles_b; ++t)
-            bulk_copy_g2s(sa + (size_t)(1 + t) * kTileBytes, B + ((size_t)t * kchunks_total + ch) * kTileBytes,
-                          kTileBytes, &full[st]);
+        mbar_arrive_expect_tx(&full[st], 2u * kTileBytes);
+        bulk_copy_g2s(sa, A + ((size_t)mt * nchunks + ch) * kTileBytes, kTileBytes, &full[st]);
+        bulk_copy_g2s(sa + kTileBytes, B + ((size_t)nt * nchunks + ch) * kTileBytes, kTileBytes, &full[st]);
     };
 
     bool ok = true;
     if (tid == 0) {
-        const uint32_t idesc = instr_desc(kBM, N);
-        issue_copy(0, 0);
-        if (nchunks > 1)
-            issue_copy(1, 1);
+        const uint32_t idesc = instr_desc(kBM, nc);
+        for (int ch = 0; ch < kStages && ch < nchunks; ++ch)
+            issue_copy(ch, ch);
         for (int ch = 0; ch < nchunks && ok; ++ch) {
-            const int st = ch & 1;
-            const uint32_t par = (ch >> 1) & 1;
-            if (!mbar_wait_bounded(&full[st], par, wait_limit)) {
+            const int st = ch % kStages;
+            if (!mbar_wait_bounded(&full[st], (ch / kStages) & 1, wait_limit)) {
                 ok = false;
                 break;
             }
@@ -178,28 +181,29 @@ __global__ void __launch_bounds__(128, 1)
             }
             mma_commit(&done[st]);
             last_commit[st] = ch;
-            if (ch + 2 < nchunks) {
-                // the stage is reused: wait until its MMAs have read it
-                if (!mbar_wait_bounded(&done[st], par, wait_limit)) {
+            const int prev = ch - 1;
+            if (prev >= 0 && prev + kStages < nchunks) {
+                const int pst = prev % kStages;
+                if (!mbar_wait_bounded(&done[pst], (prev / kStages) & 1, wait_limit)) {
                     ok = false;
                     break;
                 }
-                issue_copy(ch + 2, st);
+                issue_copy(prev + kStages, pst);
             }
         }
         if (ok) {
-            // last stage's completion covers every earlier MMA
+            // the last commit covers every earlier MMA of this thread
             const int last = nchunks - 1;
-            ok = mbar_wait_bounded(&done[last & 1], (last >> 1) & 1, wait_limit);
+            ok = mbar_wait_bounded(&done[last % kStages], (last / kStages) & 1, wait_limit);
         }
         if (!ok) {
             pp_flag(status, PP_FLAG_TIMEOUT);
             // drain (bounded) every copy issued and every MMA committed before TMEM is freed
-            for (int st = 0; st < 2; ++st) {
+            for (int st = 0; st < kStages; ++st) {
                 if (last_issue[st] >= 0)
-                    mbar_wait_bounded(&full[st], (last_issue[st] >> 1) & 1, 1ll << 24);
+                    mbar_wait_bounded(&full[st], (last_issue[st] / kStages) & 1, 1ll << 24);
                 if (last_commit[st] >= 0)
-                    mbar_wait_bounded(&done[st], (last_commit[st] >> 1) & 1, 1ll << 24);
+                    mbar_wait_bounded(&done[st], (last_commit[st] / kStages) & 1, 1ll << 24);
             }
         }
     }
@@ -207,14 +211,14 @@ __global__ void __launch_bounds__(128, 1)
     tc_fence_after();
     if (ok) {
         const int row = mt * kBM + warp * 32 + lane;
-        for (int c0 = 0; c0 < N; c0 += 16) {
+        float *drow = D + (size_t)row * ldd + (size_t)nt * kBN;
+        for (int c0 = 0; c0 < nc; c0 += 16) {
             float v[16];
             tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
             if (row < M) {
 #pragma unroll
                 for (int i = 0; i < 16; ++i)
-                    if (c0 + i < N)
-                        D[(size_t)row * ldd + c0 + i] = v[i];
+                    drow[c0 + i] = v[i];
             }
         }
     }
@@ -264,8 +268,8 @@ int launch_gemm_bf16(const void *A, const void *B, float *D, int M, int N, int K
     unsigned int *status = status_word();
     if (!status)
         return fail(PP_ERR_CUDA, "status word unavailable");
-    gemm_bf16_kernel<<<M / kBM, 128, kSmemBytes, stream>>>((const uint8_t *)A, (const uint8_t *)B, D, M, N, K,
-                                                           ldd, (long long)wait_limit(), status);
+    gemm_bf16_kernel<<<dim3(M / kBM, (N + kBN - 1) / kBN), 128, kSmemBytes, stream>>>(
+        (const uint8_t *)A, (const uint8_t *)B, D, M, N, K, ldd, (long long)wait_limit(), status);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? PP_OK : cuda_fail(e, "GEMM launch");
 }
