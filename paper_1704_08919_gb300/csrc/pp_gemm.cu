@@ -124,6 +124,7 @@ __global__ void __launch_bounds__(128, 2)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const bool vec = ((uintptr_t)D % 16 == 0) && (ldd % 4 == 0);
     uint64_t *full = (uint64_t *)(smem + kStages * kStageBytes);  // [kStages] copies landed
     uint64_t *done = full + kStages;                              // [kStages] MMAs of a stage finished
     uint32_t *s_taddr = (uint32_t *)(done + kStages);
@@ -216,9 +217,16 @@ __global__ void __launch_bounds__(128, 2)
             float v[16];
             tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
             if (row < M) {
+                if (vec) {  // 16-byte stores: a thread's 16 columns are 64 contiguous bytes
+                    float4 *d4 = reinterpret_cast<float4 *>(drow + c0);
 #pragma unroll
-                for (int i = 0; i < 16; ++i)
-                    drow[c0 + i] = v[i];
+                    for (int i = 0; i < 4; ++i)
+                        d4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        drow[c0 + i] = v[i];
+                }
             }
         }
     }
