@@ -64,13 +64,14 @@ def parse():
                     help="modes of one candidate in the CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="de-batch", choices=["de-batch", "uneven", "surrogate", "gemm", "localsearch", "large"],
+    ap.add_argument("--workload", default="de-batch", choices=["de-batch", "uneven", "surrogate", "gemm", "localsearch", "large",
+                             "single"],
                     help="de-batch: the 64-candidate DE generation (default); uneven: 128 slots "
                          "of uneven length and grid, generations in one CUDA graph; surrogate: "
                          "exact calls of surrogate-screened DE against plain DE")
     ap.add_argument("--train", type=int, default=None, help="surrogate: training pulses")
     ap.add_argument("--generations", type=int, default=None, help="surrogate: DE generations")
-    ap.add_argument("--seeds", type=int, default=3, help="surrogate: DE runs (seeds) per form")
+    ap.add_argument("--seeds", type=int, default=5, help="surrogate: DE runs (seeds) per form")
     ap.add_argument("--eval-only", action="store_true",
                     help="localsearch: time the batched gradient evaluation only (no search)")
     ap.add_argument("--small", action="store_true",
@@ -184,16 +185,16 @@ class ClockSampler:
 # ----------------------------------------------------------------------------- oracle legs
 
 
-def oracle_sample(A_host, cand, nmodes, seed=0):
+def oracle_sample(A_host, cand, nmodes, seed=0, nthreads=0):
     """The FP64 CPU oracle on `nmodes` strided modes of one candidate: (seconds, n, idx, cores)."""
     import oracle
     idx = inputs.strided_modes(CFG["grid"], nmodes, seed=seed)
     pts = inputs.grid_points(CFG["grid"])[idx]
     dt = CFG["T"] / CFG["n_steps"]
     t0 = time.perf_counter()
-    n = oracle.dirac_modes(A_host[cand], CFG["n_steps"], dt, pts)
+    n = oracle.dirac_modes(A_host[cand], CFG["n_steps"], dt, pts, nthreads=nthreads)
     el = time.perf_counter() - t0
-    return el, n, idx, oracle.num_threads(0)
+    return el, n, idx, oracle.num_threads(nthreads)
 
 
 def reference_main(args):
@@ -563,6 +564,62 @@ def large_main(args):
     return 0
 
 
+def single_main(args):
+    """The plain FP64 single-field solve (the rotating Gaussian of the parity case):
+    GPU FP64 RK4 on all 16384 modes, timed, and the FP64 oracle on all of them."""
+    import torch
+    import oracle
+    import paper_1704_08919_gb300 as pp
+    g = inputs.ROTATING_GAUSSIAN
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    pp.lib()
+    ns = g["n_steps"]
+    dt = (g["t1"] - g["t0"]) / ns
+    A, _, _ = oracle.gaussian_rotating_field(g["E0"], g["w"], g["tau"], g["t0"], dt / 2, 2 * ns + 1)
+    Ad = torch.tensor(A[None], device="cuda")
+    for _ in range(args.warmup):
+        pp.pair_number(Ad, dt, g["grid"], precision="fp64", scheme="rk4")
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(args.steps):
+        N, n = pp.pair_number(Ad, dt, g["grid"], precision="fp64", scheme="rk4", want_n=True)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    if pp.sync_status() != pp.PP_OK:
+        raise RuntimeError("device status")
+    t0 = time.perf_counter()
+    No, no = oracle.pair_number(A[None], ns, dt, g["grid"])
+    cpu_s = time.perf_counter() - t0
+    gr = g["grid"]
+    modes = gr["nx"] * gr["ny"] * gr["nz"]
+    nn = n.cpu().numpy().reshape(-1)
+    nov = no.reshape(-1)
+    big = nov >= 1e-6 * nov.max()
+    rel_N = abs(N.item() / No[0] - 1)
+    flop = WORK[("fp64", "rk4")][0]
+    achieved = flop * modes * ns / (ms * 1e-3) / 1e12
+    print(json.dumps({
+        "metric": "single-field FP64 solve time (rotating Gaussian, 16384 modes x 4000 RK4 steps)",
+        "value": ms, "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": False, "scaling": "none", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic (analytic field)", "config": {"workload": g["name"]},
+        "mode_steps_per_s": modes * ns / (ms * 1e-3),
+        "N": N.item(), "N_oracle": float(No[0]), "N_rel_err_vs_oracle": rel_N,
+        "n_max_rel_err_vs_oracle_where_n_ge_1e-6_max": float(np.abs(nn[big] / nov[big] - 1).max()),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
+                     "frac": achieved / 1.25, "note": "%d FP64 flop per mode-step; nominal GB300 FP64 "
+                     "peak (no measured FP64 peak)" % flop},
+        "cpu_baseline": {"value": cpu_s * 1e3, "unit": "ms", "cores": oracle.num_threads(0),
+                         "kind": "oracle", "sample": "the whole solve (all 16384 modes)"}}), flush=True)
+    return 0
+
+
 def gemm_main(args):
     import torch
     import paper_1704_08919_gb300 as pp
@@ -678,6 +735,8 @@ def main():
         return localsearch_main(args)
     if args.workload == "large":
         return large_main(args)
+    if args.workload == "single":
+        return single_main(args)
     import torch
     import paper_1704_08919_gb300 as pp
 
@@ -854,6 +913,11 @@ def main():
                              args.cpu_modes, CFG["n_steps"], el),
                "mode_steps_per_s": cpu_mode_steps,
                "gpu_fp64_vs_oracle_max_rel_n": float(np.abs(n_gpu[big] / n_or[big] - 1).max())}
+        el1, _, _, _ = oracle_sample(A_host, 0, 256, seed=1, nthreads=1)
+        cpu["one_core"] = {"mode_steps_per_s": 256 * CFG["n_steps"] / el1,
+                           "value": 256 * CFG["n_steps"] / el1 / units_per_candidate(),
+                           "sample": "256 strided modes x %d steps on one thread (%.2f s)" % (
+                               CFG["n_steps"], el1)}
 
     if rel_err > 1e-4:
         raise RuntimeError("N error %.3e vs FP64 RK4 exceeds 1e-4: no valid measurement" % rel_err)
