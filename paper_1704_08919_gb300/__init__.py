@@ -244,6 +244,25 @@ def pair_number(A, dt, grid, precision="fp32", n_steps=None, want_n=False, strea
     return N, n
 
 
+def pair_number_static(A, dt, grid, precision="fp32", n_steps=None, want_n=False, stream=None,
+                       N_out=None, scheme="rk4"):
+    """pp_pair_number_static: pair_number with no device allocation (fixed static scratch)."""
+    import torch
+    g = _grid(grid)
+    ncand, _, ld = A.shape
+    N = N_out if N_out is not None else torch.empty(ncand, dtype=torch.float64, device=A.device)
+    n = (torch.empty((ncand, g.nz, g.ny, g.nx), dtype=torch.float64, device=A.device)
+         if want_n else None)
+    ns = None
+    if n_steps is not None:
+        arr = (ctypes.c_int32 * ncand)(*[int(x) for x in n_steps])
+        ns = ctypes.cast(arr, ctypes.c_void_p)
+    _check(lib().pp_pair_number_static(_ptr(A), ncand, ld, ns, float(dt), ctypes.byref(g),
+                                       PRECISIONS[precision], SCHEMES[scheme], _ptr(N), _ptr(n),
+                                       _stream(stream)))
+    return N, n
+
+
 def tune_pair_number(A, dt, grid, precision="fp32", scheme="magnus4", n_steps=None, stream=None):
     """pp_tune_pair_number: time every launch configuration on these inputs, remember the
     fastest for this workload shape.  Returns (chosen index, per-configuration ms, N)."""

@@ -89,6 +89,42 @@ def test_host_validation_rejects_bad_arguments(pp):
     assert rc == pp.PP_ERR_NOT_IMPLEMENTED
 
 
+def test_host_validation_of_the_extension_entry_points(pp):
+    """Screening, surrogate, QKE and local-search entry points reject bad arguments
+    on the host, before any device work."""
+    L = pp.lib()
+    P = ctypes.c_void_p(8)
+    spec = pp.FieldSpec(8, 4, 0.0, 2.0, 50.0, 1.0, 100, 0)
+    grid = pp.Grid(4, 4, 2, -1, 1, -1, 1, 0, 1, 1)
+    rc = L.pp_qke_pair_number(P, P, P, 1, 201, 100, 0.0, ctypes.byref(grid), 0, P, None, None)
+    assert rc == pp.PP_ERR_INVALID_ARG and b"dt" in L.pp_last_error()
+    rc = L.pp_qke_pair_number(P, P, P, 1, 200, 100, 0.5, ctypes.byref(grid), 0, P, None, None)
+    assert rc == pp.PP_ERR_INVALID_ARG and b"ld" in L.pp_last_error()
+    rc = L.pp_qke_pair_number(P, P, P, 1, 201, 100, 0.5, ctypes.byref(grid), 5, P, None, None)
+    assert rc == pp.PP_ERR_INVALID_ARG and b"precision" in L.pp_last_error()
+    rc = L.pp_qke_sample_gradient(P, P, P, 1, 201, 100, 0.5, ctypes.byref(grid), 0, P, P, 150, None)
+    assert rc == pp.PP_ERR_INVALID_ARG and b"ldg" in L.pp_last_error()
+    bad = pp.FieldSpec(8, 0, 0.0, 2.0, 50.0, 1.0, 100, 0)
+    rc = L.pp_qke_gradient(P, 1, ctypes.byref(bad), ctypes.byref(grid), 0, P, P, None, None, None)
+    assert rc == pp.PP_ERR_INVALID_ARG and b"order" in L.pp_last_error()
+    rc = L.pp_synth_field_raw(P, 1, ctypes.byref(spec), P, None, None, 150, None, None)
+    assert rc == pp.PP_ERR_INVALID_ARG and b"ld" in L.pp_last_error()
+    opt = pp.ALOptions(1.0, 0.5, 3, 10, 1e-6, 1e-6)
+    x = (ctypes.c_double * 32)()
+    rc = L.pp_local_search(x, 1, ctypes.byref(spec), ctypes.byref(grid), 0, -2.0, ctypes.byref(opt),
+                           None, None, None, None, None, None, None)
+    assert rc == pp.PP_ERR_INVALID_ARG and b"U_const" in L.pp_last_error()
+    rc = L.pp_de_screened_step(P, P, 16, ctypes.byref(spec), ctypes.byref(grid), 0, 1, P, P, None,
+                               0.8, 0.9, 1, 0, 8, 0, None, None, None, None, None, None)
+    assert rc == pp.PP_ERR_INVALID_ARG and b"mlp" in L.pp_last_error()
+    rc = L.pp_mlp_fit(None, P, P, 10, 4, 1, 1e-3, 1e-4, None, None)
+    assert rc == pp.PP_ERR_INVALID_ARG
+    rc = L.pp_mlp_log_targets(P, 4, 0.0, 0.0, 1.0, P, None)
+    assert rc == pp.PP_ERR_INVALID_ARG and b"floor" in L.pp_last_error()
+    rc = L.pp_gemm_bf16(P, P, P, 100, 64, 64, 64, None)
+    assert rc == pp.PP_ERR_INVALID_ARG
+
+
 def test_product_package_does_not_import_the_oracle():
     pkg = os.path.join(ROOT, "paper_1704_08919_gb300")
     for dirpath, _, files in os.walk(pkg):
