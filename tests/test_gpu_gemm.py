@@ -62,3 +62,26 @@ def test_gemm_rejects_bad_shapes(pp):
         pp.gemm_bf16(A, A, 128, 24, 64)
     with pytest.raises(pp.PPError):
         pp.gemm_bf16(A, A, 128, 16, 48)
+
+
+def test_gemm_bounded_wait_gives_up_cleanly(pp):
+    """With the copies switched off no stage ever fills: the issuing thread's
+    bounded wait gives up, the kernel records PP_ERR_TIMEOUT, frees its TMEM and
+    returns; the next GEMM works."""
+    A = torch.randn(256, 128).cuda()
+    B = torch.randn(64, 128).cuda()
+    Ap, _, _ = pp.pack_bf16(A)
+    Bp, _, _ = pp.pack_bf16(B)
+    old = pp.set_wait_limit(2000)
+    pp.set_skip_copies(1)
+    try:
+        pp.gemm_bf16(Ap, Bp, 256, 64, 128)
+        st = pp.sync_status()
+    finally:
+        pp.set_skip_copies(0)
+        pp.set_wait_limit(old)
+    assert st == pp.PP_ERR_TIMEOUT
+    D = pp.gemm_bf16(Ap, Bp, 256, 64, 128)
+    assert pp.sync_status() == pp.PP_OK
+    ref = (bf16(A.cpu()) @ bf16(B.cpu()).T).numpy()
+    assert np.abs(D.cpu().double().numpy() - ref).max() < 1e-3 * np.abs(ref).max()

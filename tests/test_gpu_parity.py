@@ -314,6 +314,63 @@ def test_de_batch_full_size_sampled_modes(pp):
         assert n_excess(ng, no, cfg["n_steps"]) <= 1.0
 
 
+def test_large_scale_size_sampled_modes(pp):
+    """The large-scale configuration's size (K = 16, T = 400, 20000 steps, grid
+    128 x 128 x 64 over [-2.5, 2.5]^2 x [0, 2.5]) for one candidate: FP64 RK4 on the
+    GPU against the oracle on sampled modes (including the largest), and the timed
+    FP32 Magnus path against FP64 on N."""
+    cfg = inputs.LARGE_SCALE
+    spec = inputs.field_spec(cfg)
+    params = inputs.random_population(1, cfg["K"], seed=cfg["pop_seed"])
+    A, _, _ = pp.synth_field(torch.tensor(params, device=DEV), spec)
+    dt = cfg["T"] / cfg["n_steps"]
+    N64, n64 = pp.pair_number(A, dt, cfg["grid"], precision="fp64", scheme="rk4", want_n=True)
+    N32, _ = pp.pair_number(A, dt, cfg["grid"], precision="fp32fast", scheme="magnus4")
+    assert pp.sync_status() == pp.PP_OK
+    assert abs(N32.item() / N64.item() - 1) < 1e-4
+    n64 = n64[0].cpu().numpy().ravel()
+    idx = inputs.strided_modes(cfg["grid"], 16, seed=4)
+    idx = np.unique(np.concatenate([idx, [int(np.argmax(n64))]]))
+    no = oracle.dirac_modes(A[0].cpu().numpy(), cfg["n_steps"], dt, inputs.grid_points(cfg["grid"])[idx])
+    assert n_excess(n64[idx], no, cfg["n_steps"]) <= 1.0
+
+
+def test_uneven_batch_full_size(pp):
+    """The uneven-batch workload at full size (128 slots, 2500..20000 steps, grids
+    32..96 by peak-field quintile) in the timed path (FP32-fast Magnus): three slots
+    (shortest, longest, finest grid) against FP64 RK4 through the uniform path, and
+    sampled modes of the longest against the oracle."""
+    U = inputs.UNEVEN_BATCH
+    steps = inputs.uneven_steps(U, 1)
+    specs = inputs.uneven_specs(U, steps)
+    pop = torch.tensor(inputs.random_population(U["NP"], U["K"], seed=1), device=DEV)
+    peaks = []
+    for c, sp in enumerate(specs):
+        _, E, _ = pp.synth_field(pop[c:c + 1].contiguous(), sp, want_E=True)
+        peaks.append(torch.sqrt(E[0, 0] ** 2 + E[0, 1] ** 2).max().item())
+    grids = inputs.grids_by_rank(U, peaks)
+    b = pp.Batch(specs, grids, U["dt"], precision="fp32fast", scheme="magnus4")
+    A = b.synth(pop)
+    N, _ = b.pair_number(A)
+    assert pp.sync_status() == pp.PP_OK
+    sizes = [g["nx"] * g["ny"] * g["nz"] for g in grids]
+    picks = sorted({int(np.argmin(steps)), int(np.argmax(steps)), int(np.argmax(sizes))})
+    for c in picks:
+        ns = int(steps[c])
+        Ac = A[c:c + 1, :, :2 * ns + 1].contiguous()
+        N64, n64 = pp.pair_number(Ac, U["dt"], grids[c], precision="fp64", scheme="rk4",
+                                  want_n=c == int(np.argmax(steps)))
+        assert pp.sync_status() == pp.PP_OK
+        assert abs(N[c].item() / N64.item() - 1) < 1e-4, c
+        if n64 is not None:
+            nn = n64[0].cpu().numpy().ravel()
+            idx = inputs.strided_modes(grids[c], 12, seed=c)
+            idx = np.unique(np.concatenate([idx, [int(np.argmax(nn))]]))
+            no = oracle.dirac_modes(Ac[0].cpu().numpy(), ns, U["dt"], inputs.grid_points(grids[c])[idx])
+            assert n_excess(nn[idx], no, ns) <= 1.0
+    b.close()
+
+
 @pytest.mark.parametrize("scheme", ["magnus4", "split2"])
 def test_unitary_schemes_on_the_rotating_gaussian(pp, gauss_ref, scheme):
     g, ns, dt, A, No_rk4, _ = gauss_ref
