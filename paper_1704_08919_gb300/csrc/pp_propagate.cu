@@ -275,7 +275,7 @@ struct PolicySlot {
 
 const PolicySlot &policy_slot(int precision, int scheme)
 {
-    static const ConfigTable<ScalarPolicy<double, false>, false> d_rk4;
+    static const ConfigTable<ScalarPolicy<double, false>, true> d_rk4;  // tunable: small FP64 grids
     static const ConfigTable<MagnusPolicy<double, false>, false> d_mag;
     static const ConfigTable<SplitPolicy<double, false>, false> d_spl;
     static const ConfigTable<PackedPolicy<true>, true> f_rk4;
@@ -286,7 +286,7 @@ const PolicySlot &policy_slot(int precision, int scheme)
     static const ConfigTable<SplitPolicy<float, false>, true> x_spl;
     // defaults from timing the 64-candidate workload on GB300 (see the tuner)
     static const PolicySlot slots[3][3] = {
-        {{d_rk4.run_fn, d_rk4.static_fn, false, 0}, {d_mag.run_fn, d_mag.static_fn, false, 0},
+        {{d_rk4.run_fn, d_rk4.static_fn, true, 0}, {d_mag.run_fn, d_mag.static_fn, false, 0},
          {d_spl.run_fn, d_spl.static_fn, false, 0}},
         {{f_rk4.run_fn, f_rk4.static_fn, true, 0}, {f_mag.run_fn, f_mag.static_fn, true, 2},
          {f_spl.run_fn, f_spl.static_fn, true, 0}},
