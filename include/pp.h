@@ -20,9 +20,13 @@
  *    non-finite result, a zero-fluence pulse) are recorded in a device status
  *    word and returned by pp_sync_status().
  *  - The library keeps a private per-device scratch area (the per-step field
- *    table of pp_pair_number and the per-block partial sums).  It grows on
- *    demand with cudaMalloc after a device synchronisation; call an entry point
- *    once with the largest sizes before capturing it in a CUDA graph.
+ *    table of pp_pair_number, the per-block partial sums, the QKE checkpoints,
+ *    the screening buffers).  It grows on demand with cudaMalloc after a device
+ *    synchronisation; call an entry point once with the largest sizes before
+ *    capturing it in a CUDA graph.  Because the scratch is per device, work that
+ *    uses it must be ordered on one stream per device at a time (two streams
+ *    running such calls concurrently would share it).  pp_pair_number_static,
+ *    a pp_batch and a pp_mlp use buffers of their own.
  *  - Calls are thread-compatible: concurrent calls on different host threads
  *    must use different devices.
  */
