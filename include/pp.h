@@ -25,8 +25,9 @@
  *    synchronisation; call an entry point once with the largest sizes before
  *    capturing it in a CUDA graph.  Because the scratch is per device, work that
  *    uses it must be ordered on one stream per device at a time (two streams
- *    running such calls concurrently would share it).  pp_pair_number_static,
- *    a pp_batch and a pp_mlp use buffers of their own.
+ *    running such calls concurrently would share it).  pp_pair_number_static
+ *    uses a fixed device array of its own, also one per device, so the same
+ *    ordering applies to it; a pp_batch and a pp_mlp own their buffers.
  *  - Calls are thread-compatible: concurrent calls on different host threads
  *    must use different devices.
  */
