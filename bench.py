@@ -222,7 +222,10 @@ def reference_main(args):
         "value": cand_per_s, "unit": "candidates/s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000.0 * CFG["NP"] / cand_per_s,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (seeded B-spline pulses)", "config": workload_config("fp64", None, "rk4"),
+        "data": "synthetic (seeded B-spline pulses)",
+        # the same workload as the library arm; this arm computes it in FP64 RK4 (the oracle)
+        "config": workload_config(args.precision, None, args.scheme),
+        "arm_precision": "fp64", "arm_scheme": "rk4",
         "impl": "reference", "mode_steps_per_s": 1.0 / per_mode_step,
         "cpu_baseline": {"value": cand_per_s, "unit": "candidates/s", "cores": cores,
                          "kind": "oracle", "sample": sample},
