@@ -5,9 +5,9 @@ trained on exact solver evaluations of seeded random pulses, then screens each
 DE generation: every individual gets R DE/rand/1/bin proposals, the network
 keeps NP of the R NP (each individual's best-ranked one, or the NP best-ranked
 overall), and only those are scored by the exact solver (pp_de_screened_step),
-so a generation costs NP exact evaluations as plain DE does.  The exact solver stays the judge: selection only ever compares exact
-pair numbers.  Optionally the network is refitted online on the trials the
-exact solver scored.
+so a generation costs NP exact evaluations as plain DE does.  The exact solver
+decides: selection only ever compares exact pair numbers.  Optionally the
+network is refitted online on the trials the exact solver scored.
 
 Everything here is orchestration: device memory comes from PyTorch, every
 computation is a call into the library.
