@@ -74,6 +74,43 @@ __device__ __forceinline__ Coef<T> coef_at(const QkeS<T> &s, T px, T py, T pz2, 
     return c;
 }
 
+// The mode-dependent quantities of one sample that both the coefficients and
+// their derivatives need.
+template <typename T>
+struct Basics {
+    T Px, Py, w2, iw, EP, X, rX;  // rX = 1/sqrt(X) where X > 0, else 0
+};
+
+template <typename T>
+__device__ __forceinline__ Basics<T> basics(const QkeS<T> &s, T px, T py, T pz2)
+{
+    Basics<T> b;
+    b.Px = px - s.ax;
+    b.Py = py - s.ay;
+    b.w2 = ((b.Px * b.Px + b.Py * b.Py) + pz2) + T(1);
+    b.iw = rsq(b.w2);
+    b.EP = s.ex * b.Px + s.ey * b.Py;
+    b.X = b.w2 * s.ee - b.EP * b.EP;
+    b.rX = b.X > T(0) ? rsq(b.X) : T(0);
+    return b;
+}
+
+// the same values as coef_at, from precomputed basics
+template <typename T>
+__device__ __forceinline__ Coef<T> coef_from(const Basics<T> &b, const QkeS<T> &s, T eperp)
+{
+    Coef<T> c;
+    c.W2 = T(2) * (b.w2 * b.iw);
+    if (b.X > T(0)) {
+        c.Q = (b.X * b.rX) * (b.iw * b.iw);
+        c.R = eperp * (b.w2 * b.iw) * s.cr * (b.rX * b.rX);
+    } else {
+        c.Q = T(0);
+        c.R = T(0);
+    }
+    return c;
+}
+
 // out = N (one e_1 + v)
 template <typename T>
 __device__ __forceinline__ void nmul(const Coef<T> &c, const T v[6], T one, T out[6])
@@ -170,6 +207,56 @@ __device__ __forceinline__ double density(const T d[6])
     for (int i = 0; i < 6; ++i)
         g += d[i] * d[i];
     return (double)g <= kGrowthTol ? -(double)d[0] : __longlong_as_double(0x7ff8000000000000ll);
+}
+
+// the same values as sample_sens, from precomputed basics
+template <typename T>
+__device__ __forceinline__ void sens_from(const Basics<T> &b, const QkeS<T> &s, T eperp, const T ab[3], T out[6])
+{
+    const T w = b.w2 * b.iw, iw2 = b.iw * b.iw;
+    const T P[2] = {b.Px, b.Py}, E[2] = {s.ex, s.ey};
+    const T dcr_dE[2] = {s.edy, -s.edx}, dcr_dEd[2] = {-s.ey, s.ex};
+    const T Qb = ab[0], Rb = ab[1], wb = ab[2];
+    const bool pos = b.X > T(0);
+    const T sX = b.X * b.rX, iX = b.rX * b.rX;
+    const T hq = T(0.5) * b.rX * iw2;
+    const T cx = s.cr * iX;
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        const T dw_dP = P[a] * b.iw;
+        T dQ_dP = 0, dQ_dE = 0, dR_dP = 0, dR_dE = 0, dR_dEd = 0;
+        if (pos) {
+            const T dX_dP = T(2) * P[a] * s.ee - T(2) * b.EP * E[a];
+            const T dX_dE = T(2) * b.w2 * E[a] - T(2) * b.EP * P[a];
+            dQ_dP = dX_dP * hq - sX * T(2) * P[a] * (iw2 * iw2);
+            dQ_dE = dX_dE * hq;
+            dR_dP = eperp * cx * (dw_dP - w * (dX_dP * iX));
+            dR_dE = eperp * w * iX * (dcr_dE[a] - s.cr * (dX_dE * iX));
+            dR_dEd = eperp * w * dcr_dEd[a] * iX;
+        }
+        out[a] = -((Qb * dQ_dP + Rb * dR_dP) + wb * dw_dP);
+        out[2 + a] = Qb * dQ_dE + Rb * dR_dE;
+        out[4 + a] = Rb * dR_dEd;
+    }
+}
+
+// Sums v[0..15] over the warp by halving exchanges (16 shuffles instead of 80):
+// afterwards lanes L and L^1 hold the total of value (L >> 1) & 15.
+template <typename T>
+__device__ __forceinline__ T warp_sum16(T v[16], int lane)
+{
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int o = 16 >> r, w = 8 >> r;
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < w; ++i) {
+            const T send = up ? v[i] : v[i + w];
+            const T keep = up ? v[i + w] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
 template <typename T>
@@ -366,8 +453,9 @@ __global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 3 : 1) qke_adjoint
         for (int q = cnt - 1; q >= 0; --q) {
             {
                 const QkeS<T> e0 = seg[2 * q], eh = seg[2 * q + 1], e1 = seg[2 * q + 2];
+                const Basics<T> bh = basics(eh, px, py, pz2);
                 const Coef<T> c0 = coef_at(e0, px, py, pz2, eperp);
-                const Coef<T> ch = coef_at(eh, px, py, pz2, eperp);
+                const Coef<T> ch = coef_from(bh, eh, eperp);
                 T x[6];
 #pragma unroll
                 for (int i = 0; i < 6; ++i)
@@ -423,22 +511,17 @@ __global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 3 : 1) qke_adjoint
 #pragma unroll
                 for (int i = 0; i < 6; ++i)
                     bar[i] = xb[i] - yb[i];
-                // emit samples 2n+2 (slot 2q+1) and 2n+1 (slot 2q)
-                T o[6];
-                sample_sens(e1, px, py, pz2, eperp, pend, o);
+                // emit samples 2n+2 (values 0..5, slot 2q+1) and 2n+1 (values 6..11, slot 2q)
+                T o[16];
+                sens_from(basics(e1, px, py, pz2), e1, eperp, pend, o);
+                sens_from(bh, eh, eperp, hacc, o + 6);
 #pragma unroll
-                for (int i = 0; i < 6; ++i) {
-                    const T v = warp_sum(o[i]);
-                    if (lane == 0)
-                        sb[warp][2 * q + 1][i] = (double)v;
-                }
-                sample_sens(eh, px, py, pz2, eperp, hacc, o);
-#pragma unroll
-                for (int i = 0; i < 6; ++i) {
-                    const T v = warp_sum(o[i]);
-                    if (lane == 0)
-                        sb[warp][2 * q][i] = (double)v;
-                }
+                for (int i = 12; i < 16; ++i)
+                    o[i] = T(0);
+                const T tot = warp_sum16(o, lane);
+                const int vi = (lane >> 1) & 15;
+                if ((lane & 1) == 0 && vi < 12)
+                    sb[warp][vi < 6 ? 2 * q + 1 : 2 * q][vi < 6 ? vi : vi - 6] = (double)tot;
 #pragma unroll
                 for (int i = 0; i < 3; ++i)
                     pend[i] = nacc[i];
