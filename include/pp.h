@@ -70,8 +70,9 @@ typedef enum {
  *             H_1) + dt^2/12 [H_0, H_1]: unitary; the fourth-order scheme the
  *             paper's outlook (Sec. V.C.2) calls for.
  *  PP_SPLIT2  second-order Strang split operator, the paper's own integrator
- *             (Sec. II.A): constant part beta + alpha_z p_z, field part
- *             alpha_x P_x + alpha_y P_y at t_n + dt/2; unitary. */
+ *             (Sec. II.A): free part alpha.p + beta (two half steps), coupling
+ *             -alpha.A(t_n + dt/2) (one full step), each factor an exact
+ *             exponential; unitary. */
 typedef enum { PP_RK4 = 0, PP_MAGNUS4 = 1, PP_SPLIT2 = 2 } pp_scheme;
 
 /* Pulse model of Sec. III of the paper.
@@ -82,7 +83,13 @@ typedef enum { PP_RK4 = 0, PP_MAGNUS4 = 1, PP_SPLIT2 = 2 } pp_scheme;
  *  fluence  U_const of Eq. (energy): every pulse is rescaled to int E^2 dt = U_const.
  *  n_steps  RK4 steps over [-T/2, T/2] (dt = T / n_steps); the potential is
  *           sampled on the half-step grid, 2 n_steps + 1 samples.
- *  envelope 0 only (g(t) = 1, DC removed so A(-T/2) = A(T/2) = 0).            */
+ *  envelope 0: g(t) = 1 (DC removed, so A(-T/2) = A(T/2) = 0 with A(-T/2) = 0 as
+ *           the gauge); 1: the Hann envelope of Eq. (hann), g(t) = cos^2(pi t / T),
+ *           with A of Eq. (vector_potential) in the paper's gauge A(T/2) = 0
+ *           (A(-T/2) is then in general not 0) and the fluence of the enveloped
+ *           field.  envelope = 1 is accepted by pp_synth_field, pp_synth_field_raw
+ *           and pp_de_step / pp_de_screened_step; pp_batch_*, pp_synth_vjp,
+ *           pp_qke_gradient and pp_local_search return PP_ERR_NOT_IMPLEMENTED for it. */
 typedef struct {
     int32_t K;
     int32_t order;

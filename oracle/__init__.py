@@ -53,6 +53,8 @@ def lib():
         L.orc_de_propose.argtypes = [_pd, _i, _i, _pd, _pd, _pu8, _d, _d, _u64, _u64, _pd]
         L.orc_de_select.argtypes = [_pd, _pd, _pd, _pd, _i, _i]
         L.orc_num_threads.argtypes = [_i]
+        L.orc_synth_hann.argtypes = [_pd, _i, _i, _i, _d, _d, _d, _d, _i, _i, _i, _pd, _pd, _pd,
+                                     _pd]
         L.orc_synth_raw.argtypes = [_pd, _i, _i, _i, _d, _d, _d, _i, _i, _pd, _pd, _pd, _pd]
         L.orc_fluence_raw.argtypes = [_pd, _i, _i, _d, _d, _d, _pd, _pd]
         L.orc_qke6_adjoint_mode.argtypes = [_pd, _pd, _pd, _i, _i, _d, _pd, _d, _pd, _pd, _pd]
@@ -353,3 +355,18 @@ def al_objective(params, spec, grid, U_const, lam, mu, nthreads=0):
     L = -J - lam * C + C * C / (2.0 * mu)
     grad = -gJ - (lam - C / mu) * gC
     return {"L": L, "grad": grad, "J": J, "C": C, "gJ": gJ, "gC": gC}
+
+
+def synth_hann(params, K, order, wmin, wmax, T, U, n_steps, normalize=True):
+    """(A, E, Edot [c,2,2n+1], scale[c]): Eq. (field) with the Hann envelope of Eq. (hann),
+    A from Eq. (vector_potential) in the gauge A(t_f) = 0; scale = s (normalize) or U_raw."""
+    params = _f64(params).reshape(-1, 4 * K)
+    nc = params.shape[0]
+    ld = 2 * n_steps + 1
+    A, E, Ed = np.zeros((nc, 2, ld)), np.zeros((nc, 2, ld)), np.zeros((nc, 2, ld))
+    s = np.zeros(nc)
+    rc = lib().orc_synth_hann(_p(params), nc, K, order, wmin, wmax, T, U, int(normalize), n_steps,
+                              ld, _p(A), _p(E), _p(Ed), _p(s))
+    if rc:
+        raise ValueError("orc_synth_hann rc=%d" % rc)
+    return A, E, Ed, s

@@ -13,7 +13,9 @@
  *   - B-spline spectral model ............ Sec. III, Eqs. (coeff_basis_E/phi),
  *                                           Cox-de Boor recursion, clamped knots
  *   - multimode field, potential, fluence . Sec. III, Eqs. (field), (energy);
- *                                           DE renormalisation, Sec. IV.B
+ *                                           DE renormalisation, Sec. IV.B;
+ *                                           Hann envelope, Eqs. (hann),
+ *                                           (vector_potential)
  *   - momentum-space Dirac equation ...... Sec. II.A, Eqs. (kin_mom), (free_spin1),
  *                                           (wf_init), (dirac_eq_mom)
  *   - pair density ....................... Sec. II.A, Eq. (pair_prod_homo)
@@ -217,6 +219,95 @@ int orc_synth_field(const double *params, int ncand, int K, int order, double wm
     free(Om);
     free(amp);
     free(ph);
+    return status;
+}
+
+/* ------------------------------------------------------------------------- */
+/* The Hann envelope of Eq. (hann): g(t) = cos^2(Omega_T t), Omega_T = pi / T. */
+/* ------------------------------------------------------------------------- */
+
+/* The antiderivative F of g(t) cos(W t - P) of Eq. (vector_potential),
+ * F = 1/4 [2 sin(W t - P)/W + sin((2 Omega_T - W) t + P)/(2 Omega_T - W)
+ *          + sin((2 Omega_T + W) t - P)/(2 Omega_T + W)],
+ * with the middle term written as (sin(d t + P) - sin P)/d, d = 2 Omega_T - W,
+ * which differs from the paper's by a constant (absorbed by A_{l,0}) and has the
+ * regular limit t cos P at d = 0 (the mode W = 2 Omega_T). */
+static double hann_F(double W, double P, double OT, double t)
+{
+    double d = 2.0 * OT - W;
+    double mid = fabs(d) > 1e-12 * W ? (sin(d * t + P) - sin(P)) / d : t * cos(P);
+    return 0.25 * (2.0 * sin(W * t - P) / W + mid + sin((2.0 * OT + W) * t - P) / (2.0 * OT + W));
+}
+
+/* Field of Eq. (field) with the Hann envelope: E_l = s g(t) sum_j E_{l,j}
+ * cos(Omega_j t - Phi_{l,j}), A_l(t) = s sum_j E_{l,j} [F_{l,j}(t_f) - F_{l,j}(t)] (the paper's
+ * gauge A(t_f) = 0), Ed = dE/dt; on the half-step grid of orc_synth_field.  With
+ * normalize = 1, s = sqrt(U / U_raw), U_raw = int E^2 dt of the unit-scale field over
+ * one period, evaluated by the rectangle rule on the 2 n_steps grid points of the
+ * period (exact: E^2 is a trigonometric polynomial of degree < 2 n_steps); with
+ * normalize = 0, s = 1.  scale[c] (may be NULL) receives s, or U_raw when
+ * normalize = 0.  E and Ed may be NULL. */
+int orc_synth_hann(const double *params, int ncand, int K, int order, double wmin, double wmax,
+                   double T, double U, int normalize, int n_steps, int ld, double *A, double *E,
+                   double *Ed, double *scale)
+{
+    if (ncand < 0 || n_steps < 1 || ld < 2 * n_steps + 1 || !(T > 0) || !A)
+        return ORC_ERR_ARG;
+    int M = orc_mode_range(wmin, wmax, T, NULL);
+    if (M <= 0)
+        return ORC_ERR_ARG;
+    double *Om = malloc(sizeof(double) * M);
+    double *amp = malloc(sizeof(double) * 2 * M);
+    double *ph = malloc(sizeof(double) * 2 * M);
+    int nsamp = 2 * n_steps + 1, status = ORC_OK;
+    double h = T / (2.0 * n_steps), ti = -0.5 * T, tf = 0.5 * T, OT = M_PI / T;
+    double *e1 = malloc(sizeof(double) * nsamp);
+    for (int c = 0; c < ncand && status == ORC_OK; c++) {
+        int rc = orc_spectrum(params + (size_t)c * 4 * K, K, order, wmin, wmax, T, Om, amp, ph);
+        if (rc < 0) {
+            status = -rc;
+            break;
+        }
+        /* fluence of the unit-scale field: rectangle rule over one period */
+        double Uraw = 0.0;
+        for (int l = 0; l < 2; l++)
+            for (int k = 0; k < 2 * n_steps; k++) {
+                double t = ti + (double)k * h, g = cos(OT * t), e = 0.0;
+                g = g * g;
+                for (int m = 0; m < M; m++)
+                    e += amp[l * M + m] * cos(Om[m] * t - ph[l * M + m]);
+                Uraw += (g * e) * (g * e);
+            }
+        Uraw *= h;
+        double s = normalize ? (Uraw > 0.0 ? sqrt(U / Uraw) : 0.0) : 1.0;
+        if (normalize && !(Uraw > 0.0))
+            status = ORC_ERR_DEGENERATE;
+        if (scale)
+            scale[c] = normalize ? s : Uraw;
+        for (int l = 0; l < 2; l++) {
+            double *Ar = A + ((size_t)c * 2 + l) * ld;
+            double *Er = E ? E + ((size_t)c * 2 + l) * ld : NULL;
+            double *Dr = Ed ? Ed + ((size_t)c * 2 + l) * ld : NULL;
+            for (int k = 0; k < nsamp; k++) {
+                double t = ti + (double)k * h;
+                double cg = cos(OT * t), g = cg * cg, gp = -OT * sin(2.0 * OT * t);
+                double a = 0.0, sum_c = 0.0, sum_s = 0.0;
+                for (int m = 0; m < M; m++) {
+                    double Ej = amp[l * M + m], Pj = ph[l * M + m], W = Om[m];
+                    a += Ej * (hann_F(W, Pj, OT, tf) - hann_F(W, Pj, OT, t));
+                    sum_c += Ej * cos(W * t - Pj);
+                    sum_s += Ej * W * sin(W * t - Pj);
+                }
+                Ar[k] = s * a;
+                e1[k] = s * g * sum_c;
+                if (Er)
+                    Er[k] = e1[k];
+                if (Dr)
+                    Dr[k] = s * (gp * sum_c - g * sum_s);
+            }
+        }
+    }
+    free(Om), free(amp), free(ph), free(e1);
     return status;
 }
 

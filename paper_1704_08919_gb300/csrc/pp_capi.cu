@@ -171,8 +171,8 @@ int check_spec(const pp_field_spec *s)
         return fail(PP_ERR_INVALID_ARG, "band must satisfy 0 <= w_min < w_max");
     if (s->n_steps < 1 || s->n_steps > (1 << 28))
         return fail(PP_ERR_INVALID_ARG, "n_steps must be in [1, 2^28]");
-    if (s->envelope != 0)
-        return fail(PP_ERR_NOT_IMPLEMENTED, "only envelope = 0 is implemented");
+    if (s->envelope != 0 && s->envelope != 1)
+        return fail(PP_ERR_NOT_IMPLEMENTED, "envelope must be 0 (none) or 1 (Hann)");
     const double dw = 2.0 * M_PI / s->T;
     int j0 = (int)ceil(s->w_min / dw - 1e-12);
     if (j0 < 1)

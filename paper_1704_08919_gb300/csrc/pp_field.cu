@@ -113,10 +113,85 @@ __global__ void spectrum_kernel(const double *__restrict__ params, int K, int or
     }
 }
 
+// The Hann envelope of Eq. (hann), g(t) = cos^2(pi t / T) = 1/2 + 1/2 cos(dOmega t),
+// keeps the field a trigonometric polynomial on the same harmonic grid: mode j feeds
+// harmonics j and j +- 1 with weights 1/2 and 1/4.  With the (-1)^j phase factor of
+// the stored coefficients, C'_j = C_j / 2 - C_{j-1} / 4 - C_{j+1} / 4 for the
+// harmonics j0 - 1 .. j1 + 1 (Mp = M + 2 of them, starting at j0p = j0 - 1).  A
+// harmonic j = 0 (when j0 = 1) is the DC part of E: D'_0 = 0 and the samples add
+// its potential c0 (t_f - t) (the gauge A(t_f) = 0 of Eq. (vector_potential)).  The
+// fluence is (T/2) sum_{j >= 1} |C'_j|^2 + T c0^2.  Layout as spectrum_kernel, with
+// Mp in place of M.
+__global__ void hann_spectrum_kernel(const double *__restrict__ params, int K, int order, double wmin,
+                                     double wmax, double T, double U, int j0, int M,
+                                     double2 *__restrict__ coef, double *__restrict__ scale_out,
+                                     unsigned int *__restrict__ status, int normalize)
+{
+    __shared__ double red[256];
+    const int c = blockIdx.x, Mp = M + 2, j0p = j0 - 1;
+    const double *prm = params + (size_t)c * 4 * K;
+    const double dw = 2.0 * M_PI / T;
+    // unit-scale C_j of mode j = j0 + m into slot m + 1 of the D region (slots 0 and M+1 zero)
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+        const int j = j0 + m;
+        double B[kMaxK];
+        bspline_basis(K, order, wmin, wmax, (double)j * dw, B);
+        for (int l = 0; l < 2; ++l) {
+            double e = 0.0, ph = 0.0;
+            for (int i = 0; i < K; ++i) {
+                e += prm[(2 * l) * K + i] * B[i];
+                ph += prm[(2 * l + 1) * K + i] * B[i];
+            }
+            double sn, cs;
+            sincos(ph, &sn, &cs);
+            const double sg = (j & 1) ? -1.0 : 1.0;
+            coef[((size_t)c * 2 + l) * 2 * Mp + Mp + m + 1] = make_double2(sg * e * cs, -sg * e * sn);
+        }
+    }
+    if (threadIdx.x < 2) {
+        coef[((size_t)c * 2 + threadIdx.x) * 2 * Mp + Mp] = make_double2(0.0, 0.0);
+        coef[((size_t)c * 2 + threadIdx.x) * 2 * Mp + Mp + M + 1] = make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    double ssq = 0.0;
+    for (int q = threadIdx.x; q < 2 * Mp; q += blockDim.x) {
+        const int l = q / Mp, m = q % Mp;
+        const double2 *u = coef + ((size_t)c * 2 + l) * 2 * Mp + Mp;  // untransformed, slot m = harmonic j0p + m
+        const double2 cm = u[m], cl = m > 0 ? u[m - 1] : make_double2(0.0, 0.0),
+                      cr = m + 1 < Mp ? u[m + 1] : make_double2(0.0, 0.0);
+        const double2 v = make_double2(0.5 * cm.x - 0.25 * cl.x - 0.25 * cr.x, 0.5 * cm.y - 0.25 * cl.y - 0.25 * cr.y);
+        coef[((size_t)c * 2 + l) * 2 * Mp + m] = v;
+        ssq += (j0p + m == 0) ? 2.0 * v.x * v.x : v.x * v.x + v.y * v.y;
+    }
+    red[threadIdx.x] = ssq;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h)
+            red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    const double Uraw = 0.5 * T * red[0];
+    const double s = normalize ? (Uraw > 0.0 ? sqrt(U / Uraw) : 0.0) : 1.0;
+    if (threadIdx.x == 0) {
+        if (normalize && !(Uraw > 0.0))
+            pp_flag(status, PP_FLAG_DEGENERATE);
+        if (scale_out)
+            scale_out[c] = normalize ? s : Uraw;
+    }
+    for (int q = threadIdx.x; q < 2 * Mp; q += blockDim.x) {
+        const int l = q / Mp, m = q % Mp;
+        double2 *cf = coef + ((size_t)c * 2 + l) * 2 * Mp;
+        const double2 v = make_double2(s * cf[m].x, s * cf[m].y);
+        const double W = (double)(j0p + m) * dw;
+        cf[m] = v;
+        cf[Mp + m] = W > 0.0 ? make_double2(v.x / W, v.y / W) : make_double2(0.0, 0.0);
+    }
+}
+
 // Samples: grid (ceil(nsamp / 256), ncand, 2 polarisations).
 __global__ void samples_kernel(const double2 *__restrict__ coef, int M, int j0, int n_steps,
                                int ld, double *__restrict__ A, double *__restrict__ E, double dw,
-                               double *__restrict__ Ed)
+                               double *__restrict__ Ed, double T)
 {
     extern __shared__ double2 sc[];  // [2M]: C then D
     const int c = blockIdx.y, l = blockIdx.z;
@@ -157,7 +232,10 @@ __global__ void samples_kernel(const double2 *__restrict__ coef, int M, int j0, 
     const double Cr = cr * jc - ci * js;
     const double Di = dr * js + di * jc;
     double *Arow = A + ((size_t)c * 2 + l) * ld;
-    Arow[k] = -(Di - d0i);
+    double a = -(Di - d0i);
+    if (j0 == 0)  // DC harmonic (Hann envelope): potential c0 (t_f - t_k)
+        a += sc[0].x * ((double)(2 * n_steps - k) * (T / (2.0 * n_steps)));
+    Arow[k] = a;
     if (E)
         E[((size_t)c * 2 + l) * ld + k] = Cr;
     if (Ed)
@@ -435,8 +513,10 @@ int launch_synth(const double *params, int ncand, const pp_field_spec *spec, int
 {
     int j0;
     const int M = mode_band(spec, &j0);
+    const bool hann = spec->envelope == 1;
+    const int Ms = hann ? M + 2 : M, j0s = hann ? j0 - 1 : j0;  // harmonics actually synthesised
     void *coef = nullptr;
-    int rc = scratch(SCR_COEF, (size_t)ncand * 4 * M * sizeof(double2), &coef);
+    int rc = scratch(SCR_COEF, (size_t)ncand * 4 * Ms * sizeof(double2), &coef);
     if (rc)
         return rc;
     if (ncand == 0)
@@ -444,14 +524,19 @@ int launch_synth(const double *params, int ncand, const pp_field_spec *spec, int
     unsigned int *status = status_word();
     if (!status)
         return fail(PP_ERR_CUDA, "status word unavailable");
-    spectrum_kernel<<<ncand, 128, 0, stream>>>(params, spec->K, spec->order, spec->w_min, spec->w_max,
-                                               spec->T, spec->fluence, j0, M, (double2 *)coef, scale, status,
-                                               normalize);
+    if (hann)
+        hann_spectrum_kernel<<<ncand, 128, 0, stream>>>(params, spec->K, spec->order, spec->w_min, spec->w_max,
+                                                        spec->T, spec->fluence, j0, M, (double2 *)coef, scale,
+                                                        status, normalize);
+    else
+        spectrum_kernel<<<ncand, 128, 0, stream>>>(params, spec->K, spec->order, spec->w_min, spec->w_max,
+                                                   spec->T, spec->fluence, j0, M, (double2 *)coef, scale, status,
+                                                   normalize);
     const int nsamp = 2 * spec->n_steps + 1;
     dim3 g((nsamp + 255) / 256, ncand, 2);
-    samples_kernel<<<g, 256, 2 * M * sizeof(double2), stream>>>((const double2 *)coef, M, j0,
-                                                                spec->n_steps, ld, A, E,
-                                                                2.0 * M_PI / spec->T, Ed);
+    samples_kernel<<<g, 256, 2 * Ms * sizeof(double2), stream>>>((const double2 *)coef, Ms, j0s,
+                                                                 spec->n_steps, ld, A, E,
+                                                                 2.0 * M_PI / spec->T, Ed, spec->T);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return cuda_fail(e, "synthesis kernel launch");
