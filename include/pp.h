@@ -387,6 +387,12 @@ int pp_de_step(double *pop, double *fit, int32_t NP, const pp_field_spec *spec,
  * severe one seen since the last call), or PP_ERR_CUDA if the wait failed. */
 int pp_sync_status(void *stream);
 
+/* Frees the library's scratch on the current device (it only grows otherwise: the
+ * QKE adjoint, for instance, keeps up to ~8 GiB of checkpoints).  Synchronises the
+ * device first; the next call that needs scratch allocates it again.  Do not call
+ * it while a CUDA graph that uses the scratch may still be launched. */
+int pp_release_scratch(void);
+
 /* Test hooks for the bounded device waits (failure detection without a GPU fault).
  * pp_set_wait_limit: iteration limit of every mbarrier wait in the propagation
  *   kernel's main loop (default 1 << 26 polls; 0 restores the default).  Returns

@@ -49,7 +49,7 @@ EXPORTS = ("pp_synth_field", "pp_pair_number", "pp_de_propose", "pp_de_select", 
            "pp_mlp_train_step", "pp_mlp_features", "pp_de_screened_step", "pp_mlp_fit",
            "pp_mlp_log_targets", "pp_mlp_init", "pp_al_search", "pp_synth_field_raw",
            "pp_synth_vjp", "pp_qke_pair_number", "pp_qke_sample_gradient", "pp_qke_gradient",
-           "pp_local_search")
+           "pp_local_search", "pp_release_scratch")
 
 
 class ALOptions(ctypes.Structure):
@@ -516,6 +516,11 @@ def de_step(pop, fit, spec, grid, lo, hi, periodic, F, CR, seed, generation, pre
 def sync_status(stream=None):
     """pp_sync_status: wait for the stream; return (and clear) the device status code."""
     return lib().pp_sync_status(_stream(stream))
+
+
+def release_scratch():
+    """pp_release_scratch: free the library's scratch on the current device."""
+    _check(lib().pp_release_scratch())
 
 
 def profile_begin():

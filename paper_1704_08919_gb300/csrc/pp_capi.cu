@@ -75,6 +75,27 @@ int scratch(int slot, size_t bytes, void **ptr)
     return PP_OK;
 }
 
+int release_scratch()
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices)
+        return fail(PP_ERR_CUDA, "device index %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_mu);
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess)
+        return cuda_fail(e, "scratch release sync");
+    for (int slot = 0; slot < SCR_NSLOTS; ++slot) {
+        if (g_buf[dev][slot])
+            cudaFree(g_buf[dev][slot]);
+        g_buf[dev][slot] = nullptr;
+        g_cap[dev][slot] = 0;
+    }
+    return PP_OK;
+}
+
 unsigned int *status_word()
 {
     static unsigned int *addr[kMaxDevices] = {};
@@ -194,6 +215,12 @@ extern "C" {
 const char *pp_last_error(void) { return t_msg; }
 
 int pp_version(void) { return 100; }
+
+int pp_release_scratch(void)
+{
+    clear_error();
+    return release_scratch();
+}
 
 int64_t pp_set_wait_limit(int64_t limit)
 {

@@ -33,6 +33,7 @@ enum ScratchSlot {
     SCR_VJP, SCR_QKE_TABLE, SCR_QKE_CKPT, SCR_QKE_PART, SCR_QKE_G, SCR_QKE_FIELD, SCR_QKE_X, SCR_NSLOTS
 };
 int scratch(int slot, size_t bytes, void **ptr);
+int release_scratch();  // frees every slot of the current device (after a device synchronisation)
 
 // Argument checks shared by the entry points (pp_capi.cu); they record the message.
 int check_grid(const pp_grid *g);

@@ -466,3 +466,16 @@ def test_invalid_arguments_raise(pp):
     with pytest.raises(pp.PPError) as e:
         pp.pair_number(A, 0.1, inputs.small_grid(2, 2, 2), n_steps=[6])
     assert e.value.code == pp.PP_ERR_INVALID_ARG
+
+
+def test_release_scratch_then_reuse(pp):
+    """pp_release_scratch frees the scratch; the next call allocates it again and
+    gives the same result."""
+    g, ns, dt, A = rotating_gaussian()
+    At = torch.tensor(A[None], device=DEV)
+    grid = inputs.small_grid(8, 8, 2)
+    N1, _ = pp.pair_number(At, dt, grid, precision="fp64")
+    pp.release_scratch()
+    N2, _ = pp.pair_number(At, dt, grid, precision="fp64")
+    assert pp.sync_status() == pp.PP_OK
+    assert torch.equal(N1, N2)
