@@ -55,6 +55,8 @@ def lib():
         L.orc_num_threads.argtypes = [_i]
         L.orc_synth_hann.argtypes = [_pd, _i, _i, _i, _d, _d, _d, _d, _i, _i, _i, _pd, _pd, _pd,
                                      _pd]
+        L.orc_synth_vjp_hann.argtypes = [_pd, _i, _i, _d, _d, _d, _i, _i, _pd, _pd, _pd, _pd, _pd,
+                                         _pd]
         L.orc_synth_raw.argtypes = [_pd, _i, _i, _i, _d, _d, _d, _i, _i, _pd, _pd, _pd, _pd]
         L.orc_fluence_raw.argtypes = [_pd, _i, _i, _d, _d, _d, _pd, _pd]
         L.orc_qke6_adjoint_mode.argtypes = [_pd, _pd, _pd, _i, _i, _d, _pd, _d, _pd, _pd, _pd]
@@ -338,6 +340,19 @@ def grid_modes(grid):
     return p, (WX * WY * WZ).ravel()
 
 
+def synth_vjp_hann(params, K, order, wmin, wmax, T, n_steps, gA, gE, gEd):
+    """(grad[4K], U, dU[4K]): the chain rule and the fluence of the un-normalised
+    Hann-envelope field (Eqs. (hann), (field), (vector_potential))."""
+    params = _f64(params).reshape(4 * K)
+    gA, gE, gEd = (_f64(x).reshape(2, -1) for x in (gA, gE, gEd))
+    grad, dU, U = np.zeros(4 * K), np.zeros(4 * K), np.zeros(1)
+    rc = lib().orc_synth_vjp_hann(_p(params), K, order, wmin, wmax, T, n_steps, gA.shape[1], _p(gA),
+                                  _p(gE), _p(gEd), _p(grad), _p(U), _p(dU))
+    if rc:
+        raise ValueError("orc_synth_vjp_hann rc=%d" % rc)
+    return grad, float(U[0]), dU
+
+
 def al_objective(params, spec, grid, U_const, lam, mu, nthreads=0):
     """The augmented Lagrangian of Sec. IV.A for one parameter vector:
     L = -J - lam C + C^2 / (2 mu), C = U_const - U, with J from the QKE (Eq. (opt_prob)),
@@ -345,11 +360,18 @@ def al_objective(params, spec, grid, U_const, lam, mu, nthreads=0):
     Returns dict(L, grad, J, C, gJ, gC)."""
     K, n = spec["K"], spec["n_steps"]
     args = (K, spec["order"], spec["w_min"], spec["w_max"], spec["T"])
-    A, E, Ed, _ = synth_raw(params, *args, n)
+    hann = spec.get("envelope", 0) == 1
+    if hann:
+        A, E, Ed, _ = synth_hann(params, *args, 1.0, n, normalize=False)
+    else:
+        A, E, Ed, _ = synth_raw(params, *args, n)
     p, w = grid_modes(grid)
     J, _, gA, gE, gEd = qke6_grad(A[0], E[0], Ed[0], n, spec["T"] / n, p, w, nthreads)
-    gJ = synth_vjp(params, *args, n, gA, gE, gEd)
-    U, dU = fluence_raw(params, *args)
+    if hann:
+        gJ, U, dU = synth_vjp_hann(params, *args, n, gA, gE, gEd)
+    else:
+        gJ = synth_vjp(params, *args, n, gA, gE, gEd)
+        U, dU = fluence_raw(params, *args)
     C = U_const - U
     gC = -dU
     L = -J - lam * C + C * C / (2.0 * mu)

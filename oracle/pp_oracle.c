@@ -311,6 +311,96 @@ int orc_synth_hann(const double *params, int ncand, int K, int order, double wmi
     return status;
 }
 
+/* dF/dP of hann_F (P the phase), with the middle term in the same regular form. */
+static double hann_dF_dP(double W, double P, double OT, double t)
+{
+    double d = 2.0 * OT - W;
+    double mid = fabs(d) > 1e-12 * W ? (cos(d * t + P) - cos(P)) / d : -t * sin(P);
+    return 0.25 * (-2.0 * cos(W * t - P) / W + mid - cos((2.0 * OT + W) * t - P) / (2.0 * OT + W));
+}
+
+/* Chain rule of the un-normalised Hann-envelope field (orc_synth_hann with
+ * normalize = 0) for one candidate: gA, gE, gEd = dJ/d(samples) ([2][ld]) ->
+ * grad[4K]; and the fluence U (rectangle rule over one period, as orc_synth_hann)
+ * with dU[4K].  Each output may be NULL.  With theta = W t - P the samples depend
+ * on (E_j, P_j) through A = E_j (F(t_f) - F(t)), E = g E_j cos theta,
+ * Ed = E_j (g' cos theta - g W sin theta). */
+int orc_synth_vjp_hann(const double *params, int K, int order, double wmin, double wmax, double T,
+                       int n_steps, int ld, const double *gA, const double *gE, const double *gEd,
+                       double *grad, double *U_out, double *dU)
+{
+    int M = orc_mode_range(wmin, wmax, T, NULL);
+    if (M <= 0 || n_steps < 1 || ld < 2 * n_steps + 1)
+        return ORC_ERR_ARG;
+    double *Om = malloc(sizeof(double) * M);
+    double *amp = malloc(sizeof(double) * 2 * M);
+    double *ph = malloc(sizeof(double) * 2 * M);
+    double *B = malloc(sizeof(double) * K);
+    double *Ek = malloc(sizeof(double) * 2 * (size_t)(2 * n_steps));
+    int rc = orc_spectrum(params, K, order, wmin, wmax, T, Om, amp, ph);
+    if (rc < 0) {
+        free(Om), free(amp), free(ph), free(B), free(Ek);
+        return -rc;
+    }
+    double h = T / (2.0 * n_steps), ti = -0.5 * T, tf = 0.5 * T, OT = M_PI / T;
+    /* the field on the 2 n_steps points of the period, for the fluence */
+    double U = 0.0;
+    for (int l = 0; l < 2; l++)
+        for (int k = 0; k < 2 * n_steps; k++) {
+            double t = ti + (double)k * h, cg = cos(OT * t), e = 0.0;
+            for (int m = 0; m < M; m++)
+                e += amp[l * M + m] * cos(Om[m] * t - ph[l * M + m]);
+            Ek[l * 2 * n_steps + k] = cg * cg * e;
+            U += Ek[l * 2 * n_steps + k] * Ek[l * 2 * n_steps + k];
+        }
+    U *= h;
+    if (U_out)
+        *U_out = U;
+    if (grad)
+        for (int i = 0; i < 4 * K; i++)
+            grad[i] = 0.0;
+    if (dU)
+        for (int i = 0; i < 4 * K; i++)
+            dU[i] = 0.0;
+    for (int m = 0; m < M; m++) {
+        double W = Om[m];
+        orc_bspline_basis(K, order, wmin, wmax, W, B);
+        for (int l = 0; l < 2; l++) {
+            double Ej = amp[l * M + m], Pj = ph[l * M + m];
+            double dE = 0.0, dP = 0.0, uE = 0.0, uP = 0.0;
+            double Ff = hann_F(W, Pj, OT, tf), Pf = hann_dF_dP(W, Pj, OT, tf);
+            for (int k = 0; k <= 2 * n_steps; k++) {
+                double t = ti + (double)k * h;
+                double cg = cos(OT * t), g = cg * cg, gp = -OT * sin(2.0 * OT * t);
+                double ck = cos(W * t - Pj), sk = sin(W * t - Pj);
+                if (grad) {
+                    double ga = gA[l * ld + k], ge = gE[l * ld + k], gd = gEd[l * ld + k];
+                    dE += ga * (Ff - hann_F(W, Pj, OT, t)) + ge * (g * ck) + gd * (gp * ck - g * W * sk);
+                    dP += ga * (Ej * (Pf - hann_dF_dP(W, Pj, OT, t))) + ge * (g * Ej * sk)
+                          + gd * (Ej * (gp * sk + g * W * ck));
+                }
+                if (dU && k < 2 * n_steps) {
+                    double e = Ek[l * 2 * n_steps + k];
+                    uE += 2.0 * h * e * (g * ck);
+                    uP += 2.0 * h * e * (g * Ej * sk);
+                }
+            }
+            for (int i = 0; i < K; i++) {
+                if (grad) {
+                    grad[2 * l * K + i] += B[i] * dE;
+                    grad[(2 * l + 1) * K + i] += B[i] * dP;
+                }
+                if (dU) {
+                    dU[2 * l * K + i] += B[i] * uE;
+                    dU[(2 * l + 1) * K + i] += B[i] * uP;
+                }
+            }
+        }
+    }
+    free(Om), free(amp), free(ph), free(B), free(Ek);
+    return ORC_OK;
+}
+
 /* ------------------------------------------------------------------------- */
 /* A test field: E(t) = E0 exp(-t^2/tau^2) (cos w t, sin w t, 0), A(t0) = 0,  */
 /* A(t) = -int_{t0}^t E.  The integral has no elementary closed form; it is  */

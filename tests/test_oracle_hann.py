@@ -72,3 +72,44 @@ def test_unit_envelope_limit_is_not_the_hann_field():
     _, E1, _, _ = oracle.synth_hann(x, K, ORDER, 0.0, 2.0, T, 2.0, 1000)
     assert rc == 0
     assert np.abs(E1[0, :, 1000] / E0[0, :, 1000]).max() != pytest.approx(1.0)
+
+
+def test_chain_rule_and_fluence_gradient_by_finite_differences():
+    """synth_vjp_hann is the transpose of the Hann synthesis Jacobian (random sample
+    weights), and dU is the gradient of the fluence."""
+    n = 300
+    x = inputs.random_population(1, K, seed=7)[0] * 0.3
+    rng = np.random.default_rng(2)
+    wA, wE, wD = (rng.normal(size=(2, 2 * n + 1)) for _ in range(3))
+    g, U, dU = oracle.synth_vjp_hann(x, K, ORDER, 0.0, 2.0, T, n, wA, wE, wD)
+
+    def F(z):
+        A, E, Ed, Uz = oracle.synth_hann(z[None], K, ORDER, 0.0, 2.0, T, 1.0, n, normalize=False)
+        return float(np.sum(wA * A[0]) + np.sum(wE * E[0]) + np.sum(wD * Ed[0])), Uz[0]
+    assert abs(F(x)[1] - U) < 1e-13 * U
+    for i in range(4 * K):
+        e = np.zeros_like(x)
+        e[i] = 1e-6
+        (fp, up), (fm, um) = F(x + e), F(x - e)
+        assert abs((fp - fm) / 2e-6 - g[i]) < 1e-7 * np.abs(g).max(), i
+        assert abs((up - um) / 2e-6 - dU[i]) < 1e-7 * max(np.abs(dU).max(), 1e-12), i
+
+
+def test_lagrangian_gradient_with_the_envelope():
+    import math
+    k, n, T2 = 4, 2000, 20.0
+    sp = dict(K=k, order=3, w_min=0.0, w_max=2.0, T=T2, fluence=1.0, n_steps=n, envelope=1)
+    x = inputs.random_population(1, k, seed=6)[0]
+    _, _, _, U0 = oracle.synth_hann(x, k, 3, 0.0, 2.0, T2, 1.0, n, normalize=False)
+    s = math.sqrt(1.5 / U0[0])
+    x[:k] *= s
+    x[2 * k:3 * k] *= s
+    grid = inputs.small_grid(3, 3, 2)
+    r = oracle.al_objective(x, sp, grid, 2.0, 0.3, 0.5)
+    assert abs(r["C"] - 0.5) < 1e-12
+    for i in range(4 * k):
+        e = np.zeros_like(x)
+        e[i] = 1e-5
+        fd = (oracle.al_objective(x + e, sp, grid, 2.0, 0.3, 0.5)["L"]
+              - oracle.al_objective(x - e, sp, grid, 2.0, 0.3, 0.5)["L"]) / 2e-5
+        assert abs(fd - r["grad"][i]) < 1e-7 * np.abs(r["grad"]).max(), i
