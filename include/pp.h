@@ -87,9 +87,10 @@ typedef enum { PP_RK4 = 0, PP_MAGNUS4 = 1, PP_SPLIT2 = 2 } pp_scheme;
  *           the gauge); 1: the Hann envelope of Eq. (hann), g(t) = cos^2(pi t / T),
  *           with A of Eq. (vector_potential) in the paper's gauge A(T/2) = 0
  *           (A(-T/2) is then in general not 0) and the fluence of the enveloped
- *           field.  envelope = 1 is accepted by pp_synth_field, pp_synth_field_raw
- *           and pp_de_step / pp_de_screened_step; pp_batch_*, pp_synth_vjp,
- *           pp_qke_gradient and pp_local_search return PP_ERR_NOT_IMPLEMENTED for it. */
+ *           field.  envelope = 1 is accepted by pp_synth_field, pp_synth_field_raw,
+ *           pp_de_step / pp_de_screened_step, and by the chain rule of pp_synth_vjp,
+ *           pp_qke_gradient and pp_local_search; pp_batch_* return
+ *           PP_ERR_NOT_IMPLEMENTED for it. */
 typedef struct {
     int32_t K;
     int32_t order;
@@ -465,15 +466,18 @@ int pp_al_search(int32_t n, int32_t nstart, double *x, pp_objective_fn fn, void 
 /* ---- The 6-component quantum kinetic equation and its adjoint (Sec. II.B,
  * Eqs. (qke), (matrix); Sec. IV.A, Eqs. (eom2), (adj), (grad)) ----
  *
- * pp_synth_field_raw: the field of Eq. (field) with g = 1 WITHOUT the DE
- *   renormalisation (the local search keeps the fluence through its penalty):
- *   A, E and Ed = dE/dt ([ncand][2][ld] device FP64, half-step grid as in
- *   pp_synth_field; E, Ed and U may be NULL); U[c] = the fluence of Eq.
- *   (energy) over one period, (T/2) sum_{l,j} E_{l,j}^2.  spec->fluence is not used.
- * pp_synth_vjp: the chain rule of that synthesis.  g ([ncand][6][ldg] device)
- *   holds dJ/d(samples) in the order A_x, A_y, E_x, E_y, Ed_x, Ed_y; grad
- *   ([ncand][4K] device) receives dJ/dparams.  U and dU ([ncand][4K]) receive the
- *   fluence and its gradient.  Each output may be NULL (g is read only for grad).
+ * pp_synth_field_raw: the field of Eq. (field) (envelope per spec->envelope)
+ *   WITHOUT the DE renormalisation (the local search keeps the fluence through its
+ *   penalty): A, E and Ed = dE/dt ([ncand][2][ld] device FP64, half-step grid as in
+ *   pp_synth_field; E, Ed and U may be NULL); U[c] = the fluence of Eq. (energy)
+ *   over one period: (T/2) sum_{l,j} E_{l,j}^2 for g = 1, and for the Hann
+ *   envelope (T/2) sum_{l,j>=1} |C'_{l,j}|^2 + T sum_l (C'_{l,0})^2 over the
+ *   enveloped harmonics C'.  spec->fluence is not used.
+ * pp_synth_vjp: the chain rule of that synthesis (both envelopes).  g
+ *   ([ncand][6][ldg] device) holds dJ/d(samples) in the order A_x, A_y, E_x, E_y,
+ *   Ed_x, Ed_y; grad ([ncand][4K] device) receives dJ/dparams.  U and dU
+ *   ([ncand][4K]) receive the fluence and its gradient.  Each output may be NULL
+ *   (g is read only for grad).
  * pp_qke_pair_number: J[c] = sum_p w(p) f(p), f = 1 - chi_1(t_f) by classical
  *   RK4 of the QKE on the half-step grid of (A, E, Ed) ([ncand][2][ld] device),
  *   chi(t_i) = e_1; n_p as in pp_pair_number (may be NULL).  FP64 or FP32 state

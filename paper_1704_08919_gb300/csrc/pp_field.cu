@@ -352,6 +352,158 @@ __global__ void vjp_params_kernel(const double *__restrict__ params, int K, int 
     }
 }
 
+// ---- chain rule of the Hann-envelope synthesis.  The samples are linear in the
+// harmonic coefficients C'_j of hann_spectrum_kernel (s = 1):
+//   E = Re sum_j C'_j z^j,  Ed = Re sum_j i W_j C'_j z^j,
+//   A = -Im sum_{j>=1} C'_j (z^j - 1) / W_j + Re(C'_0) (t_f - t),   z = exp(i pi k / n),
+// so dJ/dC'_j is a sum over samples; the transpose of C'_j = C_j/2 - C_{j-1}/4 -
+// C_{j+1}/4 gives dJ/dC_j, and C_j = (-1)^j E~_j e^{-i Phi_j} gives dJ/dE~_j, dJ/dPhi_j.
+// The fluence (T/2) sum_{j>=1} |C'_j|^2 + T Re(C'_0)^2 goes the same way.
+
+// One block per (harmonic slot, polarisation, candidate): gH = (dJ/dRe C'_j, dJ/dIm C'_j).
+__global__ void __launch_bounds__(kVjpThreads) hann_vjp_harmonics_kernel(
+    double T, int j0p, int n_steps, const double *__restrict__ g, int ldg, double2 *__restrict__ gH)
+{
+    __shared__ double red[2][kVjpThreads];
+    const int m = blockIdx.x, l = blockIdx.y, c = blockIdx.z, Mp = gridDim.x;
+    const int j = j0p + m;
+    const double W = (double)j * (2.0 * M_PI / T), h = T / (2.0 * n_steps);
+    const double *gA = g + ((size_t)c * 6 + l) * ldg;
+    const double *gE = g + ((size_t)c * 6 + 2 + l) * ldg;
+    const double *gD = g + ((size_t)c * 6 + 4 + l) * ldg;
+    const long long two_n = 2ll * n_steps;
+    double gre = 0.0, gim = 0.0;
+    for (int k = threadIdx.x; k <= 2 * n_steps; k += kVjpThreads) {
+        const double ga = gA[k], ge = gE[k], gd = gD[k];
+        if (j == 0) {
+            gre += ga * ((double)(2 * n_steps - k) * h) + ge;
+        } else {
+            double sz, cz;
+            sincospi((double)(((long long)j * k) % two_n) / (double)n_steps, &sz, &cz);
+            gre += ga * (-sz / W) + ge * cz + gd * (-W * sz);
+            gim += ga * (-(cz - 1.0) / W) + ge * (-sz) + gd * (-W * cz);
+        }
+    }
+    red[0][threadIdx.x] = gre;
+    red[1][threadIdx.x] = gim;
+    __syncthreads();
+    for (int hh = kVjpThreads / 2; hh > 0; hh >>= 1) {
+        if (threadIdx.x < hh) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + hh];
+            red[1][threadIdx.x] += red[1][threadIdx.x + hh];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        gH[((size_t)c * 2 + l) * Mp + m] = make_double2(red[0][0], red[1][0]);
+}
+
+// One block per candidate: unit-scale spectrum, the harmonics C', the fluence U,
+// and per mode (dJ/dE~, dJ/dPhi) (if gH is given) and (dU/dE~, dU/dPhi).
+// Work arrays (global, per candidate): cp[2][M+2] padded C, ch[2][M+2] = C'.
+__global__ void hann_vjp_modes_kernel(const double *__restrict__ params, int K, int order, double wmin,
+                                      double wmax, double T, int j0, int M, const double2 *__restrict__ gH,
+                                      double2 *__restrict__ cpad, double2 *__restrict__ chh,
+                                      double2 *__restrict__ eph, double2 *__restrict__ dEP,
+                                      double2 *__restrict__ dUP, double *__restrict__ U_out)
+{
+    __shared__ double red[256];
+    const int c = blockIdx.x, Mp = M + 2, j0p = j0 - 1;
+    const double *prm = params + (size_t)c * 4 * K;
+    const double dw = 2.0 * M_PI / T;
+    double2 *cp = cpad + (size_t)c * 2 * Mp, *hc = chh + (size_t)c * 2 * Mp;
+    double2 *ep = eph + (size_t)c * 2 * M;
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+        const int j = j0 + m;
+        double B[kMaxK];
+        bspline_basis(K, order, wmin, wmax, (double)j * dw, B);
+        for (int l = 0; l < 2; ++l) {
+            double e = 0.0, ph = 0.0;
+            for (int i = 0; i < K; ++i) {
+                e += prm[(2 * l) * K + i] * B[i];
+                ph += prm[(2 * l + 1) * K + i] * B[i];
+            }
+            double sn, cs;
+            sincos(ph, &sn, &cs);
+            const double sg = (j & 1) ? -1.0 : 1.0;
+            cp[l * Mp + m + 1] = make_double2(sg * e * cs, -sg * e * sn);
+            ep[l * M + m] = make_double2(e, ph);
+        }
+    }
+    if (threadIdx.x < 2) {
+        cp[threadIdx.x * Mp] = make_double2(0.0, 0.0);
+        cp[threadIdx.x * Mp + M + 1] = make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    double ssq = 0.0;
+    for (int q = threadIdx.x; q < 2 * Mp; q += blockDim.x) {
+        const int l = q / Mp, m = q % Mp;
+        const double2 *u = cp + l * Mp;
+        const double2 cm = u[m], cl = m > 0 ? u[m - 1] : make_double2(0.0, 0.0),
+                      cr = m + 1 < Mp ? u[m + 1] : make_double2(0.0, 0.0);
+        const double2 v = make_double2(0.5 * cm.x - 0.25 * cl.x - 0.25 * cr.x, 0.5 * cm.y - 0.25 * cl.y - 0.25 * cr.y);
+        hc[q] = v;
+        ssq += (j0p + m == 0) ? 2.0 * v.x * v.x : v.x * v.x + v.y * v.y;
+    }
+    red[threadIdx.x] = ssq;
+    __syncthreads();
+    for (int hh = blockDim.x / 2; hh > 0; hh >>= 1) {
+        if (threadIdx.x < hh)
+            red[threadIdx.x] += red[threadIdx.x + hh];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && U_out)
+        U_out[c] = 0.5 * T * red[0];
+    // dU/dC'_j: T C'_j (j >= 1), 2 T Re C'_0 (j = 0); transposed to the modes
+    for (int q = threadIdx.x; q < 2 * M; q += blockDim.x) {
+        const int l = q / M, m = q % M;
+        auto uH = [&](int s) -> double2 {
+            const double2 v = hc[l * Mp + s];
+            return (j0p + s == 0) ? make_double2(2.0 * T * v.x, 0.0) : make_double2(T * v.x, T * v.y);
+        };
+        const double2 a = uH(m + 1), b = uH(m), d = uH(m + 2);
+        const double ure = 0.5 * a.x - 0.25 * b.x - 0.25 * d.x, uim = 0.5 * a.y - 0.25 * b.y - 0.25 * d.y;
+        const double2 eq = ep[l * M + m];
+        const double sg = ((j0 + m) & 1) ? -1.0 : 1.0;
+        double sn, cs;
+        sincos(eq.y, &sn, &cs);
+        dUP[(size_t)c * 2 * M + q] = make_double2(sg * (ure * cs - uim * sn), sg * eq.x * (-ure * sn - uim * cs));
+        if (gH) {
+            const double2 *gh = gH + ((size_t)c * 2 + l) * Mp;
+            const double gre = 0.5 * gh[m + 1].x - 0.25 * gh[m].x - 0.25 * gh[m + 2].x;
+            const double gim = 0.5 * gh[m + 1].y - 0.25 * gh[m].y - 0.25 * gh[m + 2].y;
+            dEP[(size_t)c * 2 * M + q] = make_double2(sg * (gre * cs - gim * sn), sg * eq.x * (-gre * sn - gim * cs));
+        }
+    }
+}
+
+// B-spline sums of the per-mode derivatives: grad_o and dU_o (U already written).
+__global__ void hann_vjp_params_kernel(int K, int order, double wmin, double wmax, double T, int j0, int M,
+                                       const double2 *__restrict__ dEP, const double2 *__restrict__ dUP,
+                                       double *__restrict__ grad, double *__restrict__ dU)
+{
+    const int c = blockIdx.x;
+    const double dw = 2.0 * M_PI / T;
+    for (int o = threadIdx.x; o < 4 * K; o += blockDim.x) {
+        const int l = o / (2 * K), kind = (o / K) % 2, i = o % K;
+        double acc = 0.0, accU = 0.0;
+        for (int m = 0; m < M; ++m) {
+            double B[kMaxK];
+            bspline_basis(K, order, wmin, wmax, (double)(j0 + m) * dw, B);
+            if (grad) {
+                const double2 v = dEP[((size_t)c * 2 + l) * M + m];
+                acc += B[i] * (kind ? v.y : v.x);
+            }
+            const double2 u = dUP[((size_t)c * 2 + l) * M + m];
+            accU += B[i] * (kind ? u.y : u.x);
+        }
+        if (grad)
+            grad[(size_t)c * 4 * K + o] = acc;
+        if (dU)
+            dU[(size_t)c * 4 * K + o] = accU;
+    }
+}
+
 // ---- batches of candidates with their own pulse length and step count (same K,
 // order, band and fluence): per-candidate spectrum descriptors.
 struct SynthCand {
@@ -554,6 +706,28 @@ int launch_synth_vjp(const double *params, int ncand, const pp_field_spec *spec,
 {
     int j0;
     const int M = mode_band(spec, &j0);
+    if (spec->envelope == 1) {
+        const int Mp = M + 2;
+        // gH, cpad, chh: 2 Mp each; eph, dEP, dUP: 2 M each (per candidate)
+        void *buf = nullptr;
+        int rc = scratch(SCR_VJP, (size_t)ncand * (6 * Mp + 6 * M) * sizeof(double2), &buf);
+        if (rc || ncand == 0)
+            return rc;
+        double2 *gH = (double2 *)buf, *cpad = gH + (size_t)ncand * 2 * Mp, *chh = cpad + (size_t)ncand * 2 * Mp;
+        double2 *eph = chh + (size_t)ncand * 2 * Mp, *dEP = eph + (size_t)ncand * 2 * M,
+                *dUP = dEP + (size_t)ncand * 2 * M;
+        if (grad)
+            hann_vjp_harmonics_kernel<<<dim3(Mp, 2, ncand), kVjpThreads, 0, stream>>>(spec->T, j0 - 1, spec->n_steps,
+                                                                                    g, ldg, gH);
+        hann_vjp_modes_kernel<<<ncand, 128, 0, stream>>>(params, spec->K, spec->order, spec->w_min, spec->w_max,
+                                                         spec->T, j0, M, grad ? gH : nullptr, cpad, chh, eph, dEP,
+                                                         dUP, U);
+        if (grad || dU)
+            hann_vjp_params_kernel<<<ncand, 128, 0, stream>>>(spec->K, spec->order, spec->w_min, spec->w_max,
+                                                              spec->T, j0, M, dEP, dUP, grad, dU);
+        cudaError_t e = cudaGetLastError();
+        return e == cudaSuccess ? PP_OK : cuda_fail(e, "synthesis chain-rule launch");
+    }
     void *dep = nullptr;
     int rc = scratch(SCR_VJP, (size_t)ncand * 2 * M * sizeof(double2), &dep);
     if (rc || ncand == 0)

@@ -807,8 +807,6 @@ int pp_synth_vjp(const double *params, int32_t ncand, const pp_field_spec *spec,
     int rc = check_raw_spec(spec);
     if (rc)
         return rc;
-    if (spec->envelope != 0)
-        return fail(PP_ERR_NOT_IMPLEMENTED, "the chain rule is implemented for envelope = 0");
     if (ncand < 0 || ncand > 65535)
         return fail(PP_ERR_INVALID_ARG, "ncand must be in [0, 65535]");
     if (ncand > 0 && (!params || (grad && !g)))
@@ -863,8 +861,6 @@ int pp_qke_gradient(const double *params, int32_t ncand, const pp_field_spec *sp
 {
     clear_error();
     int rc = check_raw_spec(spec);
-    if (!rc && spec->envelope != 0)
-        rc = fail(PP_ERR_NOT_IMPLEMENTED, "the chain rule is implemented for envelope = 0");
     if (!rc)
         rc = check_grid(grid);
     if (!rc)
@@ -906,8 +902,6 @@ int pp_local_search(double *x, int32_t nstart, const pp_field_spec *spec, const 
 {
     clear_error();
     int rc = check_raw_spec(spec);
-    if (!rc && spec->envelope != 0)
-        rc = fail(PP_ERR_NOT_IMPLEMENTED, "the chain rule is implemented for envelope = 0");
     if (!rc)
         rc = check_grid(grid);
     if (!rc)

@@ -87,10 +87,6 @@ def test_host_validation_rejects_bad_arguments(pp):
     rc = L.pp_synth_field(ctypes.c_void_p(8), 1, ctypes.byref(spec), ctypes.c_void_p(8), 201, None,
                           None, None)
     assert rc == pp.PP_ERR_NOT_IMPLEMENTED
-    hann = pp.FieldSpec(8, 4, 0.0, 2.0, 200.0, 2.0, 100, 1)  # the Hann envelope: no chain rule for it
-    rc = L.pp_synth_vjp(ctypes.c_void_p(8), 1, ctypes.byref(hann), ctypes.c_void_p(8), 201,
-                        ctypes.c_void_p(8), None, None, None)
-    assert rc == pp.PP_ERR_NOT_IMPLEMENTED
 
 
 def test_host_validation_of_the_extension_entry_points(pp):

@@ -86,11 +86,92 @@ def test_de_step_with_the_envelope(pp):
     assert np.abs(tfit.cpu().numpy() / No - 1).max() < 1e-9
 
 
-def test_paths_without_the_envelope_reject_it(pp):
-    x = torch.tensor(inputs.random_population(2, K, seed=1), device=DEV)
+def test_batches_reject_the_envelope(pp):
     with pytest.raises(pp.PPError) as e:
-        pp.qke_gradient(x, spec(100), inputs.small_grid(2, 2, 1))
-    assert e.value.code == pp.PP_ERR_NOT_IMPLEMENTED
-    with pytest.raises(pp.PPError):
         pp.Batch([spec(100), spec(120)], [inputs.small_grid(2, 2, 1)] * 2, T / 100)
+    assert e.value.code == pp.PP_ERR_NOT_IMPLEMENTED
     assert pp.sync_status() == pp.PP_OK
+
+
+# ---- the chain rule through the envelope (the local search's gradient), on the
+# small QKE workload of the local-search tests: K = 4, order 3, T = 20
+KQ, ORDQ, TQ = 4, 3, 20.0
+
+
+def qspec(n):
+    return dict(K=KQ, order=ORDQ, w_min=0.0, w_max=2.0, T=TQ, fluence=1.0, n_steps=n, envelope=1)
+
+
+def qparams(nc, seed, U=1.5):
+    """nc random parameter vectors with the amplitude weights scaled so that the
+    enveloped field has fluence U."""
+    lo, hi, _ = inputs.param_bounds(KQ)
+    rng = np.random.default_rng(seed)
+    X = lo + rng.random((nc, 4 * KQ)) * (hi - lo)
+    _, _, _, U0 = oracle.synth_hann(X, KQ, ORDQ, 0.0, 2.0, TQ, 1.0, 100, normalize=False)
+    for x, u in zip(X, U0):
+        s = np.sqrt(U / u)
+        x[:KQ] *= s
+        x[2 * KQ:3 * KQ] *= s
+    return X
+
+
+def dev(x):
+    return torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device=DEV)
+
+
+@pytest.mark.parametrize("n,wmin", [(300, 0.0), (777, 0.3)])
+def test_chain_rule_matches_oracle(pp, n, wmin):
+    """pp_synth_vjp with the envelope against the oracle's transpose of the closed
+    form, for random sample weights; the fluence and its gradient too."""
+    X = inputs.random_population(3, K, seed=n) * 0.3
+    rng = np.random.default_rng(n)
+    g = rng.normal(size=(3, 6, 2 * n + 1))
+    sp = spec(n, wmin)
+    grad, U, dU = pp.synth_vjp(dev(X), sp, dev(g))
+    assert pp.sync_status() == pp.PP_OK
+    grad, U, dU = grad.cpu().numpy(), U.cpu().numpy(), dU.cpu().numpy()
+    for c in range(3):
+        go, Uo, dUo = oracle.synth_vjp_hann(X[c], K, ORDER, wmin, 2.0, T, n,
+                                            g[c, 0:2], g[c, 2:4], g[c, 4:6])
+        assert np.abs(grad[c] - go).max() < 1e-11 * np.abs(go).max()
+        assert abs(U[c] / Uo - 1) < 1e-13
+        assert np.abs(dU[c] - dUo).max() < 1e-13 * np.abs(dUo).max()
+
+
+def test_parameter_gradient_matches_oracle(pp):
+    n = 2000
+    grid = inputs.small_grid(5, 5, 3)
+    X = qparams(3, 4)
+    J, gJ, U, dU = pp.qke_gradient(dev(X), qspec(n), grid, "fp64")
+    J32, gJ32, _, _ = pp.qke_gradient(dev(X), qspec(n), grid, "fp32")
+    assert pp.sync_status() == pp.PP_OK
+    for c in range(3):
+        o = oracle.al_objective(X[c], qspec(n), grid, 2.0, 0.0, 1.0)
+        assert np.isfinite(o["J"])
+        assert abs(J[c].item() / o["J"] - 1) < 1e-9
+        assert np.abs(gJ[c].cpu().numpy() - o["gJ"]).max() < 1e-9 * np.abs(o["gJ"]).max()
+        assert np.abs(dU[c].cpu().numpy() + o["gC"]).max() < 1e-12 * np.abs(o["gC"]).max()
+        assert abs(U[c].item() - (2.0 - o["C"])) < 1e-12
+        assert abs(J32[c].item() / o["J"] - 1) < 1e-4
+        assert np.linalg.norm(gJ32[c].cpu().numpy() - o["gJ"]) < 1e-3 * np.linalg.norm(o["gJ"])
+
+
+def test_local_search_first_iterates_match_oracle(pp):
+    """The GPU local search over enveloped pulses takes the oracle's first BFGS iterates."""
+    from oracle import localsearch as LS
+    n = 2000
+    grid = inputs.small_grid(4, 4, 2)
+    starts = qparams(2, 9)
+    kw = dict(mu0=0.1, xi=0.5, outer=1, max_iter=3, gtol=1e-12, ctol=1e-12)
+    r = pp.local_search(starts, qspec(n), grid, 2.0, precision="fp64", **kw)
+    assert pp.sync_status() == pp.PP_OK
+
+    def obj(z):
+        o = oracle.al_objective(z, qspec(n), grid, 2.0, 0.0, 1.0)
+        return o["J"], o["gJ"], o["C"], o["gC"]
+    for i in range(2):
+        o = LS.augmented_lagrangian(obj, starts[i], **kw)
+        assert r["evals"][i] == o["evals"]
+        assert np.abs(r["x"][i] - o["x"]).max() < 1e-7 * np.abs(o["x"]).max()
+        assert abs(r["J"][i] / o["J"] - 1) < 1e-8
