@@ -87,10 +87,8 @@ typedef enum { PP_RK4 = 0, PP_MAGNUS4 = 1, PP_SPLIT2 = 2 } pp_scheme;
  *           the gauge); 1: the Hann envelope of Eq. (hann), g(t) = cos^2(pi t / T),
  *           with A of Eq. (vector_potential) in the paper's gauge A(T/2) = 0
  *           (A(-T/2) is then in general not 0) and the fluence of the enveloped
- *           field.  envelope = 1 is accepted by pp_synth_field, pp_synth_field_raw,
- *           pp_de_step / pp_de_screened_step, and by the chain rule of pp_synth_vjp,
- *           pp_qke_gradient and pp_local_search; pp_batch_* return
- *           PP_ERR_NOT_IMPLEMENTED for it. */
+ *           field.  Every entry point that takes a pp_field_spec accepts both;
+ *           other values return PP_ERR_NOT_IMPLEMENTED. */
 typedef struct {
     int32_t K;
     int32_t order;
@@ -123,8 +121,8 @@ typedef struct {
  *  scale  (device) [ncand] the factor s applied to the unit-weight spectrum, or NULL.
  * A zero-fluence candidate produces A = E = 0, s = 0 and sets PP_ERR_DEGENERATE_FIELD
  * in the status word.  Errors: INVALID_ARG (K < order, order < 1 or > 8, K > 64,
- * empty band or more than 1536 modes in it, T <= 0, fluence <= 0, n_steps < 1, ld too
- * small, null A or params). */
+ * empty band or more than 1536 modes in it (1534 with the envelope), T <= 0,
+ * fluence <= 0, n_steps < 1, ld too small, null A or params). */
 int pp_synth_field(const double *params, int32_t ncand, const pp_field_spec *spec, double *A,
                    int32_t ld, double *E, double *scale, void *stream);
 
@@ -176,7 +174,7 @@ void pp_clear_tuning(void);
 
 /* ---- Uneven batches (candidates with their own pulse length, step count and
  * momentum grid) and captured DE loops.  A pp_batch fixes, per population slot
- * c, the pulse model specs[c] (same K, order, band and fluence for all slots;
+ * c, the pulse model specs[c] (same K, order, band, fluence and envelope for all slots;
  * T and n_steps per slot with T / n_steps = dt) and the momentum grid grids[c],
  * plus the precision and scheme.  pp_batch_create allocates every device
  * buffer the batch needs (the step table, partial sums, work lists, potential,

@@ -349,9 +349,11 @@ int pp_batch_create(int32_t ncand, const pp_field_spec *specs, const pp_grid *gr
     for (int c = 0; c < ncand; ++c) {
         const pp_field_spec &s = specs[c];
         if (s.K != specs[0].K || s.order != specs[0].order || s.w_min != specs[0].w_min ||
-            s.w_max != specs[0].w_max || s.fluence != specs[0].fluence || s.envelope != 0)
-            return fail(PP_ERR_INVALID_ARG, "candidate %d: K, order, band, fluence must match candidate 0 "
-                                            "and envelope must be 0", c);
+            s.w_max != specs[0].w_max || s.fluence != specs[0].fluence || s.envelope != specs[0].envelope)
+            return fail(PP_ERR_INVALID_ARG, "candidate %d: K, order, band, fluence and envelope must match "
+                                            "candidate 0", c);
+        if (s.envelope != 0 && s.envelope != 1)
+            return fail(PP_ERR_NOT_IMPLEMENTED, "envelope must be 0 (none) or 1 (Hann)");
         if (s.K < s.order || s.K > 64 || s.order < 1 || s.order > 8 || !(s.T > 0.0) || s.n_steps < 1)
             return fail(PP_ERR_INVALID_ARG, "candidate %d: bad pulse model", c);
         if (fabs(s.T / s.n_steps - dt) > 1e-12 * dt)
@@ -361,8 +363,9 @@ int pp_batch_create(int32_t ncand, const pp_field_spec *specs, const pp_grid *gr
         if (j0 < 1)
             j0 = 1;
         const int j1 = (int)floor(s.w_max / dw + 1e-12);
-        if (j1 < j0 || j1 - j0 + 1 > 1536)
-            return fail(PP_ERR_INVALID_ARG, "candidate %d: 1 to 1536 modes must lie in the band", c);
+        const int max_modes = s.envelope ? 1534 : 1536;
+        if (j1 < j0 || j1 - j0 + 1 > max_modes)
+            return fail(PP_ERR_INVALID_ARG, "candidate %d: 1 to %d modes must lie in the band", c, max_modes);
         const pp_grid &g = grids[c];
         if (g.nx < 1 || g.ny < 1 || g.nz < 1 || (long long)g.nx * g.ny * g.nz > (1ll << 30))
             return fail(PP_ERR_INVALID_ARG, "candidate %d: bad grid sizes", c);

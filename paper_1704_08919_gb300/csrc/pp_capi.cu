@@ -201,8 +201,10 @@ int check_spec(const pp_field_spec *s)
     const int j1 = (int)floor(s->w_max / dw + 1e-12);
     if (j1 < j0)
         return fail(PP_ERR_INVALID_ARG, "no mode j*2pi/T (j >= 1) lies in [w_min, w_max]");
-    if (j1 - j0 + 1 > 1536)
-        return fail(PP_ERR_INVALID_ARG, "more than 1536 modes in the band");
+    // the sample kernels stage 2 (M + 2 with the envelope) coefficients in 48 KB of shared memory
+    const int max_modes = s->envelope ? 1534 : 1536;
+    if (j1 - j0 + 1 > max_modes)
+        return fail(PP_ERR_INVALID_ARG, "more than %d modes in the band", max_modes);
     return PP_OK;
 }
 

@@ -59,16 +59,28 @@ __device__ void bspline_basis(int K, int order, double wmin, double wmax, double
         B[i] = b[i];
 }
 
-// One block per candidate: spectrum at every mode, fluence, scale, and the
-// Horner coefficients coef[c][l][m] = (C, D) for mode j = j0 + m.
-__global__ void spectrum_kernel(const double *__restrict__ params, int K, int order, double wmin,
-                                double wmax, double T, double U, int j0, int M,
-                                double2 *__restrict__ coef, double *__restrict__ scale_out,
-                                unsigned int *__restrict__ status, int normalize)
+// Block-wide sum of one value per thread (blockDim.x a power of two <= 256).
+__device__ double block_sum(double v)
 {
     __shared__ double red[256];
-    const int c = blockIdx.x;
-    const double *prm = params + (size_t)c * 4 * K;
+    __syncthreads();  // red may still be read by a previous call
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h)
+            red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    return red[0];
+}
+
+// One block per candidate: spectrum at every mode, fluence, scale, and the
+// Horner coefficients cf[l][m] = C, cf[l][M + m] = D for mode j = j0 + m
+// (cf: this candidate's 4 M coefficients; scale_out: its scale slot or NULL).
+__device__ void spectrum_block(const double *__restrict__ prm, int K, int order, double wmin, double wmax,
+                               double T, double U, int j0, int M, double2 *__restrict__ cf,
+                               double *__restrict__ scale_out, unsigned int *__restrict__ status, int normalize)
+{
     const double dw = 2.0 * M_PI / T;
     double ssq = 0.0;
     for (int m = threadIdx.x; m < M; m += blockDim.x) {
@@ -87,29 +99,22 @@ __global__ void spectrum_kernel(const double *__restrict__ params, int K, int or
             sincos(ph, &sn, &cs);
             const double sg = (j & 1) ? -1.0 : 1.0;
             // unit-scale C_j = E~ e^{-i Phi} (-1)^j ; the scale is applied below
-            coef[((size_t)c * 2 + l) * 2 * M + m] = make_double2(sg * e * cs, -sg * e * sn);
-            coef[((size_t)c * 2 + l) * 2 * M + M + m] = make_double2(sg * e * cs / W, -sg * e * sn / W);
+            cf[(size_t)l * 2 * M + m] = make_double2(sg * e * cs, -sg * e * sn);
+            cf[(size_t)l * 2 * M + M + m] = make_double2(sg * e * cs / W, -sg * e * sn / W);
         }
     }
-    red[threadIdx.x] = ssq;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s)
-            red[threadIdx.x] += red[threadIdx.x + s];
-        __syncthreads();
-    }
-    const double Uraw = 0.5 * T * red[0];
+    const double Uraw = 0.5 * T * block_sum(ssq);
     // normalize = 0: the un-normalised field (s = 1) and scale_out receives its fluence
     const double s = normalize ? (Uraw > 0.0 ? sqrt(U / Uraw) : 0.0) : 1.0;
     if (threadIdx.x == 0) {
         if (normalize && !(Uraw > 0.0))
             pp_flag(status, PP_FLAG_DEGENERATE);
         if (scale_out)
-            scale_out[c] = normalize ? s : Uraw;
+            *scale_out = normalize ? s : Uraw;
     }
     for (int q = threadIdx.x; q < 4 * M; q += blockDim.x) {
-        double2 v = coef[(size_t)c * 4 * M + q];
-        coef[(size_t)c * 4 * M + q] = make_double2(s * v.x, s * v.y);
+        const double2 v = cf[q];
+        cf[q] = make_double2(s * v.x, s * v.y);
     }
 }
 
@@ -120,16 +125,14 @@ __global__ void spectrum_kernel(const double *__restrict__ params, int K, int or
 // harmonics j0 - 1 .. j1 + 1 (Mp = M + 2 of them, starting at j0p = j0 - 1).  A
 // harmonic j = 0 (when j0 = 1) is the DC part of E: D'_0 = 0 and the samples add
 // its potential c0 (t_f - t) (the gauge A(t_f) = 0 of Eq. (vector_potential)).  The
-// fluence is (T/2) sum_{j >= 1} |C'_j|^2 + T c0^2.  Layout as spectrum_kernel, with
-// Mp in place of M.
-__global__ void hann_spectrum_kernel(const double *__restrict__ params, int K, int order, double wmin,
-                                     double wmax, double T, double U, int j0, int M,
-                                     double2 *__restrict__ coef, double *__restrict__ scale_out,
-                                     unsigned int *__restrict__ status, int normalize)
+// fluence is (T/2) sum_{j >= 1} |C'_j|^2 + T c0^2.  Layout as spectrum_block, with
+// Mp in place of M (cf: 4 Mp coefficients).
+__device__ void hann_spectrum_block(const double *__restrict__ prm, int K, int order, double wmin, double wmax,
+                                    double T, double U, int j0, int M, double2 *__restrict__ cf,
+                                    double *__restrict__ scale_out, unsigned int *__restrict__ status,
+                                    int normalize)
 {
-    __shared__ double red[256];
-    const int c = blockIdx.x, Mp = M + 2, j0p = j0 - 1;
-    const double *prm = params + (size_t)c * 4 * K;
+    const int Mp = M + 2, j0p = j0 - 1;
     const double dw = 2.0 * M_PI / T;
     // unit-scale C_j of mode j = j0 + m into slot m + 1 of the D region (slots 0 and M+1 zero)
     for (int m = threadIdx.x; m < M; m += blockDim.x) {
@@ -145,47 +148,61 @@ __global__ void hann_spectrum_kernel(const double *__restrict__ params, int K, i
             double sn, cs;
             sincos(ph, &sn, &cs);
             const double sg = (j & 1) ? -1.0 : 1.0;
-            coef[((size_t)c * 2 + l) * 2 * Mp + Mp + m + 1] = make_double2(sg * e * cs, -sg * e * sn);
+            cf[(size_t)l * 2 * Mp + Mp + m + 1] = make_double2(sg * e * cs, -sg * e * sn);
         }
     }
     if (threadIdx.x < 2) {
-        coef[((size_t)c * 2 + threadIdx.x) * 2 * Mp + Mp] = make_double2(0.0, 0.0);
-        coef[((size_t)c * 2 + threadIdx.x) * 2 * Mp + Mp + M + 1] = make_double2(0.0, 0.0);
+        cf[(size_t)threadIdx.x * 2 * Mp + Mp] = make_double2(0.0, 0.0);
+        cf[(size_t)threadIdx.x * 2 * Mp + Mp + M + 1] = make_double2(0.0, 0.0);
     }
     __syncthreads();
     double ssq = 0.0;
     for (int q = threadIdx.x; q < 2 * Mp; q += blockDim.x) {
         const int l = q / Mp, m = q % Mp;
-        const double2 *u = coef + ((size_t)c * 2 + l) * 2 * Mp + Mp;  // untransformed, slot m = harmonic j0p + m
+        const double2 *u = cf + (size_t)l * 2 * Mp + Mp;  // untransformed, slot m = harmonic j0p + m
         const double2 cm = u[m], cl = m > 0 ? u[m - 1] : make_double2(0.0, 0.0),
                       cr = m + 1 < Mp ? u[m + 1] : make_double2(0.0, 0.0);
         const double2 v = make_double2(0.5 * cm.x - 0.25 * cl.x - 0.25 * cr.x, 0.5 * cm.y - 0.25 * cl.y - 0.25 * cr.y);
-        coef[((size_t)c * 2 + l) * 2 * Mp + m] = v;
+        cf[(size_t)l * 2 * Mp + m] = v;
         ssq += (j0p + m == 0) ? 2.0 * v.x * v.x : v.x * v.x + v.y * v.y;
     }
-    red[threadIdx.x] = ssq;
-    __syncthreads();
-    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-        if (threadIdx.x < h)
-            red[threadIdx.x] += red[threadIdx.x + h];
-        __syncthreads();
-    }
-    const double Uraw = 0.5 * T * red[0];
+    // block_sum's barriers also order the C' writes above before the reads below
+    const double Uraw = 0.5 * T * block_sum(ssq);
     const double s = normalize ? (Uraw > 0.0 ? sqrt(U / Uraw) : 0.0) : 1.0;
     if (threadIdx.x == 0) {
         if (normalize && !(Uraw > 0.0))
             pp_flag(status, PP_FLAG_DEGENERATE);
         if (scale_out)
-            scale_out[c] = normalize ? s : Uraw;
+            *scale_out = normalize ? s : Uraw;
     }
     for (int q = threadIdx.x; q < 2 * Mp; q += blockDim.x) {
         const int l = q / Mp, m = q % Mp;
-        double2 *cf = coef + ((size_t)c * 2 + l) * 2 * Mp;
-        const double2 v = make_double2(s * cf[m].x, s * cf[m].y);
+        double2 *c = cf + (size_t)l * 2 * Mp;
+        const double2 v = make_double2(s * c[m].x, s * c[m].y);
         const double W = (double)(j0p + m) * dw;
-        cf[m] = v;
-        cf[Mp + m] = W > 0.0 ? make_double2(v.x / W, v.y / W) : make_double2(0.0, 0.0);
+        c[m] = v;
+        c[Mp + m] = W > 0.0 ? make_double2(v.x / W, v.y / W) : make_double2(0.0, 0.0);
     }
+}
+
+__global__ void spectrum_kernel(const double *__restrict__ params, int K, int order, double wmin,
+                                double wmax, double T, double U, int j0, int M,
+                                double2 *__restrict__ coef, double *__restrict__ scale_out,
+                                unsigned int *__restrict__ status, int normalize)
+{
+    const int c = blockIdx.x;
+    spectrum_block(params + (size_t)c * 4 * K, K, order, wmin, wmax, T, U, j0, M, coef + (size_t)c * 4 * M,
+                   scale_out ? scale_out + c : nullptr, status, normalize);
+}
+
+__global__ void hann_spectrum_kernel(const double *__restrict__ params, int K, int order, double wmin,
+                                     double wmax, double T, double U, int j0, int M,
+                                     double2 *__restrict__ coef, double *__restrict__ scale_out,
+                                     unsigned int *__restrict__ status, int normalize)
+{
+    const int c = blockIdx.x;
+    hann_spectrum_block(params + (size_t)c * 4 * K, K, order, wmin, wmax, T, U, j0, M,
+                        coef + (size_t)c * 4 * (M + 2), scale_out ? scale_out + c : nullptr, status, normalize);
 }
 
 // Samples: grid (ceil(nsamp / 256), ncand, 2 polarisations).
@@ -508,7 +525,11 @@ __global__ void hann_vjp_params_kernel(int K, int order, double wmin, double wma
 // order, band and fluence): per-candidate spectrum descriptors.
 struct SynthCand {
     double T;
-    int n_steps, j0, M;
+    int n_steps;
+    int j0, M;    // harmonic band of the samples (the mode band widened by one each side
+                  // with the Hann envelope)
+    int j0m, Mm;  // mode band of the spectrum
+    int env;      // 0: g = 1, 1: Hann
     long long coef_off;  // into the coefficient buffer, 4 M double2 per candidate
 };
 
@@ -516,47 +537,13 @@ __global__ void spectrum_batch_kernel(const double *__restrict__ params, int K, 
                                       double wmax, double U, const SynthCand *__restrict__ sc,
                                       double2 *__restrict__ coef, unsigned int *__restrict__ status)
 {
-    __shared__ double red[256];
     const int c = blockIdx.x;
     const SynthCand d = sc[c];
     const double *prm = params + (size_t)c * 4 * K;
-    const double dw = 2.0 * M_PI / d.T;
-    double2 *cf = coef + d.coef_off;
-    double ssq = 0.0;
-    for (int m = threadIdx.x; m < d.M; m += blockDim.x) {
-        const int j = d.j0 + m;
-        const double W = (double)j * dw;
-        double B[kMaxK];
-        bspline_basis(K, order, wmin, wmax, W, B);
-        for (int l = 0; l < 2; ++l) {
-            double e = 0.0, ph = 0.0;
-            for (int i = 0; i < K; ++i) {
-                e += prm[(2 * l) * K + i] * B[i];
-                ph += prm[(2 * l + 1) * K + i] * B[i];
-            }
-            ssq += e * e;
-            double sn, cs;
-            sincos(ph, &sn, &cs);
-            const double sg = (j & 1) ? -1.0 : 1.0;
-            cf[(size_t)l * 2 * d.M + m] = make_double2(sg * e * cs, -sg * e * sn);
-            cf[(size_t)l * 2 * d.M + d.M + m] = make_double2(sg * e * cs / W, -sg * e * sn / W);
-        }
-    }
-    red[threadIdx.x] = ssq;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s)
-            red[threadIdx.x] += red[threadIdx.x + s];
-        __syncthreads();
-    }
-    const double Uraw = 0.5 * d.T * red[0];
-    const double s = Uraw > 0.0 ? sqrt(U / Uraw) : 0.0;
-    if (threadIdx.x == 0 && !(Uraw > 0.0))
-        pp_flag(status, PP_FLAG_DEGENERATE);
-    for (int q = threadIdx.x; q < 4 * d.M; q += blockDim.x) {
-        double2 v = cf[q];
-        cf[q] = make_double2(s * v.x, s * v.y);
-    }
+    if (d.env)
+        hann_spectrum_block(prm, K, order, wmin, wmax, d.T, U, d.j0m, d.Mm, coef + d.coef_off, nullptr, status, 1);
+    else
+        spectrum_block(prm, K, order, wmin, wmax, d.T, U, d.j0m, d.Mm, coef + d.coef_off, nullptr, status, 1);
 }
 
 __global__ void samples_batch_kernel(const double2 *__restrict__ coef, const SynthCand *__restrict__ sc,
@@ -589,7 +576,10 @@ __global__ void samples_batch_kernel(const double2 *__restrict__ coef, const Syn
         d0i += D.y;
     }
     const double Di = dr * js + di * jc;
-    A[((size_t)c * 2 + l) * ld + k] = -(Di - d0i);
+    double a = -(Di - d0i);
+    if (d.j0 == 0)  // DC harmonic of the Hann envelope: potential c0 (t_f - t_k)
+        a += scf[0].x * ((double)(2 * d.n_steps - k) * (d.T / (2.0 * d.n_steps)));
+    A[((size_t)c * 2 + l) * ld + k] = a;
 }
 
 }  // namespace
@@ -609,10 +599,14 @@ int synth_batch_prepare(int ncand, const pp_field_spec *specs, void **d_desc, vo
         if (j0 < 1)
             j0 = 1;
         const int j1 = (int)floor(specs[c].w_max / dw + 1e-12);
+        const int env = specs[c].envelope == 1;
         h[c].T = specs[c].T;
         h[c].n_steps = specs[c].n_steps;
-        h[c].j0 = j0;
-        h[c].M = j1 - j0 + 1;
+        h[c].j0m = j0;
+        h[c].Mm = j1 - j0 + 1;
+        h[c].env = env;
+        h[c].j0 = env ? j0 - 1 : j0;
+        h[c].M = env ? h[c].Mm + 2 : h[c].Mm;
         h[c].coef_off = off;
         off += 4ll * h[c].M;
         mm = h[c].M > mm ? h[c].M : mm;

@@ -184,3 +184,32 @@ def test_batch_rejects_inconsistent_specs(pp):
     assert e.value.code == pp.PP_ERR_INVALID_ARG
     with pytest.raises(pp.PPError):
         pp.Batch(specs()[:3], grids()[:3], DT)
+    sp = specs()
+    sp[3] = dict(sp[3], envelope=1)  # envelopes must match across slots
+    with pytest.raises(pp.PPError) as e:
+        pp.Batch(sp, grids(), DT)
+    assert e.value.code == pp.PP_ERR_INVALID_ARG
+
+
+def test_batch_with_the_hann_envelope(pp):
+    """Slots of different length with the Hann envelope of Eq. (hann): the batch
+    synthesis equals the oracle's closed form, and the batch pair numbers equal the
+    uniform path's bit for bit and the oracle's to 1e-9."""
+    params = inputs.random_population(len(STEPS), K, seed=45)
+    sp = [dict(x, envelope=1) for x in specs()]
+    b = pp.Batch(sp, grids(), DT, precision="fp64", scheme="rk4")
+    A = b.synth(torch.tensor(params, device=DEV))
+    N, _ = b.pair_number(A)
+    assert pp.sync_status() == pp.PP_OK
+    An = A.cpu().numpy()
+    for c, (s, g) in enumerate(zip(sp, grids())):
+        ns = s["n_steps"]
+        Ao, _, _, _ = oracle.synth_hann(params[c:c + 1], K, ORDER, 0.0, 2.0, s["T"], 2.0, ns)
+        assert np.abs(An[c, :, :2 * ns + 1] - Ao[0]).max() < 1e-12 * np.abs(Ao).max()
+        Nu, _ = pp.pair_number(A[c:c + 1, :, :2 * ns + 1].contiguous(), DT, g, precision="fp64",
+                               scheme="rk4")
+        assert torch.equal(N[c:c + 1], Nu)
+        if c < 2:
+            No, _ = oracle.pair_number(Ao, ns, DT, g)
+            assert abs(N[c].item() / No[0] - 1) < 1e-9
+    b.close()

@@ -86,13 +86,6 @@ def test_de_step_with_the_envelope(pp):
     assert np.abs(tfit.cpu().numpy() / No - 1).max() < 1e-9
 
 
-def test_batches_reject_the_envelope(pp):
-    with pytest.raises(pp.PPError) as e:
-        pp.Batch([spec(100), spec(120)], [inputs.small_grid(2, 2, 1)] * 2, T / 100)
-    assert e.value.code == pp.PP_ERR_NOT_IMPLEMENTED
-    assert pp.sync_status() == pp.PP_OK
-
-
 # ---- the chain rule through the envelope (the local search's gradient), on the
 # small QKE workload of the local-search tests: K = 4, order 3, T = 20
 KQ, ORDQ, TQ = 4, 3, 20.0
