@@ -16,10 +16,22 @@
 // descriptor's leading-dimension offset) and the row groups 1024 B apart (its
 // stride offset).
 //
-// One CTA of 128 threads computes a 128 x 128 block of D (the last column block
-// may be narrower): warp 0 allocates its TMEM columns, thread 0 issues 4 MMAs
-// (K = 16 each) per 64-wide K chunk from a 3-stage ring of bulk copies, each warp
-// then reads its 32 TMEM lanes with tcgen05.ld and writes its rows of D.
+// Persistent, warp-specialised kernel: one CTA per SM (at most one per 128-row
+// tile of D) walks the tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...; each tile
+// is the full width of D (N <= 256), so every A tile crosses from L2 once.
+//   warp 0      producer: lane 0 streams the A tile and the one or two B tiles of
+//               every 64-wide K chunk into a kStages ring with bulk copies;
+//   warp 1      owns TMEM (two 256-column FP32 accumulators) and issues: lane 0
+//               issues 4 MMAs (K = 16 each) per chunk into the accumulator of the
+//               tile, commits each stage back to the producer and each finished
+//               tile to the epilogue;
+//   warps 2..5  epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (the quadrant
+//               tcgen05.ld allows it), stages 32 x 32 blocks through shared memory
+//               and writes whole row segments of D, then hands the accumulator
+//               back, so the next tile's MMAs overlap this tile's stores.
+// Every wait is bounded; a wait that gives up records PP_ERR_TIMEOUT, and the
+// issuing lanes wait (bounded) for their copies and MMAs in flight before TMEM is
+// freed.
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -107,41 +119,54 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
         v[i] = __uint_as_float(r[i]);
 }
 
-// Shared-memory plan: a ring of kStages stages x (A tile 16 KiB + B tile 16 KiB) and
-// the barriers; two CTAs fit on an SM.
-constexpr int kStages = 3;
-constexpr int kBN = 128;                      // columns per CTA (one packed B tile)
-constexpr int kStageBytes = 2 * kTileBytes;
-constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 128;
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
+                 : "memory");
+}
 
-// One CTA: rows [128 mt, 128 mt + 128) x columns [128 nt, 128 nt + nc), nc = min(128, N - 128 nt).
-// Thread 0 keeps kStages chunks in flight: after issuing chunk ch's MMAs it waits for
-// chunk ch-1's MMAs to finish reading their stage and refills that stage with chunk
-// ch-1+kStages, so the tensor pipe always has the next chunk queued.
-__global__ void __launch_bounds__(128, 2)
+// Shared-memory plan: a ring of kStages stages x (A tile + two B tiles, 48 KiB), the
+// epilogue's staging blocks and the barriers: one CTA per SM.
+constexpr int kStages = 4;
+constexpr int kBN = 256;                      // D columns per tile (all of N)
+constexpr int kStageBytes = 3 * kTileBytes;
+constexpr int kEpiWarps = 4;
+constexpr int kEpiPitch = 33;                 // floats per staged row: conflict-free columns and rows
+constexpr int kEpiBytes = kEpiWarps * 32 * kEpiPitch * 4;
+constexpr int kBarBytes = 256;
+constexpr int kSmemBytes = kStages * kStageBytes + kEpiBytes + kBarBytes + 1024;
+constexpr int kThreads = 64 + 32 * kEpiWarps;
+constexpr uint32_t kTmemCols = 2 * kBN;       // double-buffered accumulator
+
+__global__ void __launch_bounds__(kThreads, 1)
     gemm_bf16_kernel(const uint8_t *__restrict__ A, const uint8_t *__restrict__ B, float *__restrict__ D,
                      int M, int N, int K, int ldd, long long wait_limit, unsigned int *__restrict__ status,
                      int skip_copies)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const bool vec = ((uintptr_t)D % 16 == 0) && (ldd % 4 == 0);
-    uint64_t *full = (uint64_t *)(smem + kStages * kStageBytes);  // [kStages] copies landed
-    uint64_t *done = full + kStages;                              // [kStages] MMAs of a stage finished
-    uint32_t *s_taddr = (uint32_t *)(done + kStages);
+    float *stage_all = (float *)(smem + kStages * kStageBytes);
+    uint64_t *full = (uint64_t *)(smem + kStages * kStageBytes + kEpiBytes);  // [kStages] copies landed
+    uint64_t *empty = full + kStages;                                         // [kStages] stage's MMAs done
+    uint64_t *tfull = empty + kStages;                                        // [2] accumulator complete
+    uint64_t *tempty = tfull + 2;                                             // [2] accumulator read out
+    uint32_t *s_taddr = (uint32_t *)(tempty + 2);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int mt = blockIdx.x, nt = blockIdx.y;
-    const int nc = min(kBN, N - nt * kBN);  // a multiple of 16 in [16, 128]
-    const int nchunks = K / kKC;
-    const uint32_t ncols = nc <= 32 ? 32 : (nc <= 64 ? 64 : 128);
+    const int ntiles = M / kBM, nchunks = K / kKC;
+    const int nb = N > 128 ? 2 : 1;  // packed B row tiles per chunk
+    const uint32_t stage_tx = (uint32_t)(1 + nb) * kTileBytes;
 
-    if (warp == 0)
-        tmem_alloc(s_taddr, ncols);
+    if (warp == 1)
+        tmem_alloc(s_taddr, kTmemCols);
     if (tid == 0) {
         for (int i = 0; i < kStages; ++i) {
             mbar_init(&full[i], 1);
-            mbar_init(&done[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&tfull[i], 1);
+            mbar_init(&tempty[i], kEpiWarps);
         }
         mbar_fence_init();
     }
@@ -150,93 +175,143 @@ __global__ void __launch_bounds__(128, 2)
     tc_fence_after();
     const uint32_t taddr = *s_taddr;
 
-    int last_issue[kStages], last_commit[kStages];  // thread 0's bookkeeping for the drain
-    for (int i = 0; i < kStages; ++i)
-        last_issue[i] = last_commit[i] = -1;
-    auto issue_copy = [&](int ch, int st) {
-        if (skip_copies)  // test hook: nothing is issued, so the first wait gives up
-            return;
-        uint8_t *sa = smem + st * kStageBytes;
-        last_issue[st] = ch;
-        mbar_arrive_expect_tx(&full[st], 2u * kTileBytes);
-        bulk_copy_g2s(sa, A + ((size_t)mt * nchunks + ch) * kTileBytes, kTileBytes, &full[st]);
-        bulk_copy_g2s(sa + kTileBytes, B + ((size_t)nt * nchunks + ch) * kTileBytes, kTileBytes, &full[st]);
-    };
-
     bool ok = true;
-    if (tid == 0) {
-        const uint32_t idesc = instr_desc(kBM, nc);
-        for (int ch = 0; ch < kStages && ch < nchunks; ++ch)
-            issue_copy(ch, ch);
-        for (int ch = 0; ch < nchunks && ok; ++ch) {
-            const int st = ch % kStages;
-            if (!mbar_wait_bounded(&full[st], (ch / kStages) & 1, wait_limit)) {
+    // drain bookkeeping of the issuing lanes: chunks copied, chunks committed and tiles
+    // committed, each in ring order, so the last round of every barrier follows from the count
+    long long n_copied = 0, n_committed = 0;
+    int n_tiles_done = 0;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            long long g = 0;  // chunk counter over all tiles of this CTA
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                for (int ch = 0; ch < nchunks; ++ch, ++g) {
+                    const int st = (int)(g % kStages);
+                    const long long round = g / kStages;
+                    if (round > 0 && !mbar_wait_bounded(&empty[st], (uint32_t)((round - 1) & 1), wait_limit)) {
+                        ok = false;
+                        break;
+                    }
+                    if (skip_copies)  // test hook: nothing is issued, so the consumers' waits give up
+                        continue;
+                    uint8_t *sa = smem + st * kStageBytes;
+                    ++n_copied;
+                    mbar_arrive_expect_tx(&full[st], stage_tx);
+                    bulk_copy_g2s(sa, A + ((size_t)t * nchunks + ch) * kTileBytes, kTileBytes, &full[st]);
+                    for (int j = 0; j < nb; ++j)
+                        bulk_copy_g2s(sa + (1 + j) * kTileBytes, B + ((size_t)j * nchunks + ch) * kTileBytes,
+                                      kTileBytes, &full[st]);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = instr_desc(kBM, N);
+            long long g = 0;
+            int tc = 0;  // tiles of this CTA so far
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tc) {
+                const int buf = tc & 1, use = tc >> 1;
+                if (use > 0 && !mbar_wait_bounded(&tempty[buf], (uint32_t)((use - 1) & 1), wait_limit)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t dtm = taddr + (uint32_t)(buf * kBN);
+                for (int ch = 0; ch < nchunks; ++ch, ++g) {
+                    const int st = (int)(g % kStages);
+                    const long long round = g / kStages;
+                    if (!mbar_wait_bounded(&full[st], (uint32_t)(round & 1), wait_limit)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = smem_u32(smem + st * kStageBytes);
+                    const uint32_t sb = sa + kTileBytes;  // B rows 128..255 follow at +16 KiB (16 row groups)
+#pragma unroll
+                    for (int k = 0; k < kKC / 16; ++k) {
+                        // K = 16 spans two core matrices along K: advance by 2 x 128 B per step
+                        mma_bf16(dtm, smem_desc(sa + k * 256), smem_desc(sb + k * 256), idesc,
+                                 (ch > 0 || k > 0) ? 1u : 0u);
+                    }
+                    mma_commit(&empty[st]);
+                    ++n_committed;
+                }
+                if (!ok)
+                    break;
+                mma_commit(&tfull[buf]);
+                ++n_tiles_done;
+            }
+        }
+    } else {
+        const int quad = warp & 3;  // TMEM lanes 32 quad .. 32 quad + 31
+        float *stg = stage_all + (warp - 2) * 32 * kEpiPitch;
+        const bool vec = ((uintptr_t)D % 16 == 0) && (ldd % 4 == 0);
+        int tc = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tc) {
+            const int buf = tc & 1, use = tc >> 1;
+            const bool got = __all_sync(0xffffffffu, mbar_wait_bounded(&tfull[buf], (uint32_t)(use & 1), wait_limit));
+            if (!got) {
                 ok = false;
                 break;
             }
             tc_fence_after();
-            const uint32_t sa = smem_u32(smem + st * kStageBytes);
-            const uint32_t sb = sa + kTileBytes;
+            const int row0 = t * kBM + quad * 32;
+            const uint32_t tl = taddr + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * kBN);
+            for (int c0 = 0; c0 < N; c0 += 32) {
+                const int w = min(32, N - c0);  // 16 or 32 columns
+                float v[32];
+                tmem_ld16(tl + (uint32_t)c0, v);
+                if (w > 16)
+                    tmem_ld16(tl + (uint32_t)c0 + 16, v + 16);
 #pragma unroll
-            for (int k = 0; k < kKC / 16; ++k) {
-                // K = 16 spans two core matrices along K: advance by 2 x 128 B per step
-                mma_bf16(taddr, smem_desc(sa + k * 256), smem_desc(sb + k * 256), idesc,
-                         (ch > 0 || k > 0) ? 1u : 0u);
-            }
-            mma_commit(&done[st]);
-            last_commit[st] = ch;
-            const int prev = ch - 1;
-            if (prev >= 0 && prev + kStages < nchunks) {
-                const int pst = prev % kStages;
-                if (!mbar_wait_bounded(&done[pst], (prev / kStages) & 1, wait_limit)) {
-                    ok = false;
-                    break;
+                for (int j = 0; j < 32; ++j)
+                    if (j < w)
+                        stg[lane * kEpiPitch + j] = v[j];
+                __syncwarp();
+                // w / 4 lanes per row, 16 bytes each: every store instruction writes whole rows
+                const int lpr = w >> 2, rpi = 32 / lpr;
+                const int cc = (lane % lpr) * 4;
+                for (int r = lane / lpr; r < 32; r += rpi) {
+                    const float *src = stg + r * kEpiPitch + cc;
+                    float *dst = D + (size_t)(row0 + r) * ldd + c0 + cc;
+                    if (vec) {
+                        *reinterpret_cast<float4 *>(dst) = make_float4(src[0], src[1], src[2], src[3]);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            dst[i] = src[i];
+                    }
                 }
-                issue_copy(prev + kStages, pst);
+                __syncwarp();
             }
-        }
-        if (ok) {
-            // the last commit covers every earlier MMA of this thread
-            const int last = nchunks - 1;
-            ok = mbar_wait_bounded(&done[last % kStages], (last / kStages) & 1, wait_limit);
-        }
-        if (!ok) {
-            pp_flag(status, PP_FLAG_TIMEOUT);
-            // drain (bounded) every copy issued and every MMA committed before TMEM is freed
-            for (int st = 0; st < kStages; ++st) {
-                if (last_issue[st] >= 0)
-                    mbar_wait_bounded(&full[st], (last_issue[st] / kStages) & 1, 1ll << 24);
-                if (last_commit[st] >= 0)
-                    mbar_wait_bounded(&done[st], (last_commit[st] / kStages) & 1, 1ll << 24);
-            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive(&tempty[buf]);
         }
     }
+
     ok = __syncthreads_and(ok);
-    tc_fence_after();
-    if (ok) {
-        const int row = mt * kBM + warp * 32 + lane;
-        float *drow = D + (size_t)row * ldd + (size_t)nt * kBN;
-        for (int c0 = 0; c0 < nc; c0 += 16) {
-            float v[16];
-            tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-            if (row < M) {
-                if (vec) {  // 16-byte stores: a thread's 16 columns are 64 contiguous bytes
-                    float4 *d4 = reinterpret_cast<float4 *>(drow + c0);
-#pragma unroll
-                    for (int i = 0; i < 4; ++i)
-                        d4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 16; ++i)
-                        drow[c0 + i] = v[i];
-                }
-            }
+    if (!ok) {
+        // drain (bounded) every copy issued and every MMA committed before TMEM is freed
+        // (stage st last held chunk st + kStages r, r = (n - 1 - st) / kStages, when n > st)
+        if (tid == 0) {
+            pp_flag(status, PP_FLAG_TIMEOUT);
+            for (int st = 0; st < kStages && st < n_copied; ++st)
+                mbar_wait_bounded(&full[st], (uint32_t)(((n_copied - 1 - st) / kStages) & 1), 1ll << 24);
+        }
+        if (tid == 32) {
+            for (int st = 0; st < kStages && st < n_committed; ++st)
+                mbar_wait_bounded(&empty[st], (uint32_t)(((n_committed - 1 - st) / kStages) & 1), 1ll << 24);
+            for (int i = 0; i < 2 && i < n_tiles_done; ++i)
+                mbar_wait_bounded(&tfull[i], (uint32_t)(((n_tiles_done - 1 - i) / 2) & 1), 1ll << 24);
         }
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0)
-        tmem_dealloc(taddr, ncols);
+    tc_fence_after();
+    if (warp == 1)
+        tmem_dealloc(taddr, kTmemCols);
 }
 
 // Packs an FP32 matrix (rows x cols, leading dimension ldx; transposed if trans)
@@ -279,8 +354,18 @@ int launch_gemm_bf16(const void *A, const void *B, float *D, int M, int N, int K
     unsigned int *status = status_word();
     if (!status)
         return fail(PP_ERR_CUDA, "status word unavailable");
-    gemm_bf16_kernel<<<dim3(M / kBM, (N + kBN - 1) / kBN), 128, kSmemBytes, stream>>>(
-        (const uint8_t *)A, (const uint8_t *)B, D, M, N, K, ldd, (long long)wait_limit(), status, skip_copies());
+    static int sms[64] = {};
+    if (dev >= 0 && dev < 64 && sms[dev] == 0) {
+        int n = 0;
+        cudaError_t e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "SM count");
+        sms[dev] = n;
+    }
+    const int ntiles = M / kBM;
+    const int grid = (dev >= 0 && dev < 64 && sms[dev] > 0 && sms[dev] < ntiles) ? sms[dev] : ntiles;
+    gemm_bf16_kernel<<<grid, kThreads, kSmemBytes, stream>>>((const uint8_t *)A, (const uint8_t *)B, D, M, N, K,
+                                                            ldd, (long long)wait_limit(), status, skip_copies());
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? PP_OK : cuda_fail(e, "GEMM launch");
 }
