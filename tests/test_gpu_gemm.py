@@ -42,6 +42,25 @@ def test_gemm_matches_fp64_product_of_bf16_operands(pp, M, N, K):
     assert np.abs(D[:, N:].cpu().numpy()).max() == 0.0 if Np > N else True
 
 
+@pytest.mark.parametrize("M,N,K", [(128 * 400, 256, 128), (128 * 700, 48, 64)])
+def test_gemm_with_more_tiles_than_sms(pp, M, N, K):
+    """More 128-row tiles than SMs: every CTA of the persistent kernel walks several
+    tiles and reuses both TMEM accumulators, so the hand-back between the epilogue
+    and the MMA issuer is exercised."""
+    g = torch.Generator(device="cpu").manual_seed(M + N + K)
+    A = torch.randn(M, K, generator=g).cuda()
+    B = torch.randn(N, K, generator=g).cuda()
+    Ap, _, _ = pp.pack_bf16(A)
+    Bp, _, _ = pp.pack_bf16(B)
+    D = pp.gemm_bf16(Ap, Bp, M, N, K)
+    D2 = pp.gemm_bf16(Ap, Bp, M, N, K)
+    assert pp.sync_status() == pp.PP_OK
+    assert torch.equal(D, D2)
+    ref = (bf16(A.cpu()) @ bf16(B.cpu()).T).numpy()
+    got = D.cpu().double().numpy()
+    assert np.abs(got - ref).max() < 2e-5 * np.abs(ref).max() + 1e-5 * np.sqrt(K)
+
+
 def test_gemm_transposed_packing(pp):
     g = torch.Generator(device="cpu").manual_seed(1)
     X = torch.randn(64, 256, generator=g).cuda()  # stored as (K rows) x (M cols): pack X^T
