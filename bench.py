@@ -393,10 +393,10 @@ def gemm_measure(pp, torch, reps=20):
 
 # FP32 work per mode-step of the QKE adjoint kernel (forward pass, recomputed
 # forward and backward step), from the kernel's executed SASS counts (ncu,
-# 1.342e8 mode-steps): 360 FFMA + 322 FMUL + 128 FADD thread-instructions,
-# i.e. 1169 flop (FMA = 2) in 810 FP32 instructions.
-QKE_ADJ_FLOP = 1169
-QKE_ADJ_FP32_INSTR = 810
+# 1.342e8 mode-steps): 288 FFMA + 296 FMUL + 128 FADD thread-instructions,
+# i.e. 1000 flop (FMA = 2) in 712 FP32 instructions.
+QKE_ADJ_FLOP = 1000
+QKE_ADJ_FP32_INSTR = 712
 
 
 def localsearch_main(args):

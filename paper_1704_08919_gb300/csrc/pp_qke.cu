@@ -48,9 +48,12 @@ struct Coef {
     T Q, R, W2;  // W2 = 2 omega
 };
 
-// Reciprocal square root: correctly rounded in FP32 (a special-function
-// instruction and a correction instead of a square root and a division).
-__device__ __forceinline__ float rsq(float x) { return __frsqrt_rn(x); }
+// Reciprocal square root.  FP32: the special-function unit's approximation
+// (rsqrtf, at most 2 ulp), one instruction instead of a square root and a
+// division; its error is far below the FP32 RK4 rounding of the state.  The
+// forward, recomputed and adjoint sweeps all call this one function, so the
+// recomputed trajectory is the forward one bit for bit.
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsq(double x) { return 1.0 / sqrt(x); }
 
 template <typename T>
