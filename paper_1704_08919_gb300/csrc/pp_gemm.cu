@@ -20,15 +20,18 @@
 // tile of D) walks the tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...; each tile
 // is the full width of D (N <= 256), so every A tile crosses from L2 once.
 //   warp 0      producer: lane 0 streams the A tile and the one or two B tiles of
-//               every 64-wide K chunk into a kStages ring with bulk copies;
+//               every 64-wide K chunk into a ring with bulk copies; when all of B
+//               fits in 128 KiB (K <= 512, or K <= 256 for N > 128) it loads B once
+//               per CTA and the ring carries A alone;
 //   warp 1      owns TMEM (two 256-column FP32 accumulators) and issues: lane 0
 //               issues 4 MMAs (K = 16 each) per chunk into the accumulator of the
 //               tile, commits each stage back to the producer and each finished
 //               tile to the epilogue;
-//   warps 2..5  epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (the quadrant
-//               tcgen05.ld allows it), stages 32 x 32 blocks through shared memory
-//               and writes whole row segments of D, then hands the accumulator
-//               back, so the next tile's MMAs overlap this tile's stores.
+//   warps 2..9  epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (the quadrant
+//               tcgen05.ld allows it) over one half of the columns, stages 32 x 32
+//               blocks through shared memory and writes whole row segments of D,
+//               then hands the accumulator back, so the next tile's MMAs overlap
+//               this tile's stores.
 // Every wait is bounded; a wait that gives up records PP_ERR_TIMEOUT, and the
 // issuing lanes wait (bounded) for their copies and MMAs in flight before TMEM is
 // freed.
@@ -125,37 +128,54 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
                  : "memory");
 }
 
-// Shared-memory plan: a ring of kStages stages x (A tile + two B tiles, 48 KiB), the
-// epilogue's staging blocks and the barriers: one CTA per SM.
-constexpr int kStages = 4;
 constexpr int kBN = 256;                      // D columns per tile (all of N)
-constexpr int kStageBytes = 3 * kTileBytes;
-constexpr int kEpiWarps = 4;
+constexpr int kEpiWarps = 8;                  // two per TMEM lane quadrant, one per column half
 constexpr int kEpiPitch = 33;                 // floats per staged row: conflict-free columns and rows
 constexpr int kEpiBytes = kEpiWarps * 32 * kEpiPitch * 4;
 constexpr int kBarBytes = 256;
-constexpr int kSmemBytes = kStages * kStageBytes + kEpiBytes + kBarBytes + 1024;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr uint32_t kTmemCols = 2 * kBN;       // double-buffered accumulator
+constexpr int kMaxResidentB = 8;              // B tiles kept resident (128 KiB): K <= 512, or K <= 256 for N > 128
 
+// Shared-memory plan, one CTA per SM.  Streaming B (RB = false): a ring of 4 stages x
+// (A tile + two B tiles, 48 KiB).  Resident B (RB = true, when all of B fits): the B
+// tiles of every chunk, loaded once per CTA, then a ring of 4 A tiles.  Both: the
+// epilogue's staging blocks and the barriers.
+template <bool RB>
+struct GemmPlan {
+    static constexpr int stages = 4;
+    static constexpr int stage_bytes = RB ? kTileBytes : 3 * kTileBytes;
+    static constexpr int ring_off = RB ? kMaxResidentB * kTileBytes : 0;
+    static constexpr int epi_off = ring_off + stages * stage_bytes;
+    static constexpr int bar_off = epi_off + kEpiBytes;
+    static constexpr int smem_bytes = bar_off + kBarBytes + 1024;
+    static_assert(smem_bytes <= 232448, "shared memory per CTA");
+};
+
+template <bool RB>
 __global__ void __launch_bounds__(kThreads, 1)
     gemm_bf16_kernel(const uint8_t *__restrict__ A, const uint8_t *__restrict__ B, float *__restrict__ D,
                      int M, int N, int K, int ldd, long long wait_limit, unsigned int *__restrict__ status,
                      int skip_copies)
 {
+    using Plan = GemmPlan<RB>;
+    constexpr int kStages = Plan::stages;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    float *stage_all = (float *)(smem + kStages * kStageBytes);
-    uint64_t *full = (uint64_t *)(smem + kStages * kStageBytes + kEpiBytes);  // [kStages] copies landed
-    uint64_t *empty = full + kStages;                                         // [kStages] stage's MMAs done
-    uint64_t *tfull = empty + kStages;                                        // [2] accumulator complete
-    uint64_t *tempty = tfull + 2;                                             // [2] accumulator read out
-    uint32_t *s_taddr = (uint32_t *)(tempty + 2);
+    uint8_t *bres = smem;                           // resident B: chunk ch's tiles at ch * nb tiles
+    uint8_t *ring = smem + Plan::ring_off;
+    float *stage_all = (float *)(smem + Plan::epi_off);
+    uint64_t *full = (uint64_t *)(smem + Plan::bar_off);  // [kStages] copies landed
+    uint64_t *empty = full + kStages;                     // [kStages] stage's MMAs done
+    uint64_t *tfull = empty + kStages;                    // [2] accumulator complete
+    uint64_t *tempty = tfull + 2;                         // [2] accumulator read out
+    uint64_t *bfull = tempty + 2;                         // resident B landed
+    uint32_t *s_taddr = (uint32_t *)(bfull + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ntiles = M / kBM, nchunks = K / kKC;
     const int nb = N > 128 ? 2 : 1;  // packed B row tiles per chunk
-    const uint32_t stage_tx = (uint32_t)(1 + nb) * kTileBytes;
+    const uint32_t stage_tx = (uint32_t)(RB ? 1 : 1 + nb) * kTileBytes;
 
     if (warp == 1)
         tmem_alloc(s_taddr, kTmemCols);
@@ -168,6 +188,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(&tfull[i], 1);
             mbar_init(&tempty[i], kEpiWarps);
         }
+        mbar_init(bfull, 1);
         mbar_fence_init();
     }
     tc_fence_before();
@@ -180,9 +201,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     // committed, each in ring order, so the last round of every barrier follows from the count
     long long n_copied = 0, n_committed = 0;
     int n_tiles_done = 0;
+    bool b_loaded = false;
 
     if (warp == 0) {
         if (lane == 0) {
+            if (RB && !skip_copies && blockIdx.x < ntiles) {
+                b_loaded = true;
+                mbar_arrive_expect_tx(bfull, (uint32_t)(nchunks * nb) * kTileBytes);
+                for (int ch = 0; ch < nchunks; ++ch)
+                    for (int j = 0; j < nb; ++j)
+                        bulk_copy_g2s(bres + (ch * nb + j) * kTileBytes, B + ((size_t)j * nchunks + ch) * kTileBytes,
+                                      kTileBytes, bfull);
+            }
             long long g = 0;  // chunk counter over all tiles of this CTA
             for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
                 for (int ch = 0; ch < nchunks; ++ch, ++g) {
@@ -194,19 +224,22 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     if (skip_copies)  // test hook: nothing is issued, so the consumers' waits give up
                         continue;
-                    uint8_t *sa = smem + st * kStageBytes;
+                    uint8_t *sa = ring + st * Plan::stage_bytes;
                     ++n_copied;
                     mbar_arrive_expect_tx(&full[st], stage_tx);
                     bulk_copy_g2s(sa, A + ((size_t)t * nchunks + ch) * kTileBytes, kTileBytes, &full[st]);
-                    for (int j = 0; j < nb; ++j)
-                        bulk_copy_g2s(sa + (1 + j) * kTileBytes, B + ((size_t)j * nchunks + ch) * kTileBytes,
-                                      kTileBytes, &full[st]);
+                    if (!RB)
+                        for (int j = 0; j < nb; ++j)
+                            bulk_copy_g2s(sa + (1 + j) * kTileBytes, B + ((size_t)j * nchunks + ch) * kTileBytes,
+                                          kTileBytes, &full[st]);
                 }
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
             const uint32_t idesc = instr_desc(kBM, N);
+            if (RB && blockIdx.x < ntiles && !mbar_wait_bounded(bfull, 0, wait_limit))
+                ok = false;
             long long g = 0;
             int tc = 0;  // tiles of this CTA so far
             for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tc) {
@@ -225,8 +258,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t sa = smem_u32(smem + st * kStageBytes);
-                    const uint32_t sb = sa + kTileBytes;  // B rows 128..255 follow at +16 KiB (16 row groups)
+                    const uint32_t sa = smem_u32(ring + st * Plan::stage_bytes);
+                    // B rows 128..255 follow rows 0..127 at +16 KiB (16 row groups)
+                    const uint32_t sb = RB ? smem_u32(bres + ch * nb * kTileBytes) : sa + kTileBytes;
 #pragma unroll
                     for (int k = 0; k < kKC / 16; ++k) {
                         // K = 16 spans two core matrices along K: advance by 2 x 128 B per step
@@ -243,7 +277,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         }
     } else {
-        const int quad = warp & 3;  // TMEM lanes 32 quad .. 32 quad + 31
+        const int quad = warp & 3;                     // TMEM lanes 32 quad .. 32 quad + 31
+        const int cbeg = ((warp - 2) >> 2) * (kBN / 2);  // this warp's column half
+        const int cend = min(N, cbeg + kBN / 2);
         float *stg = stage_all + (warp - 2) * 32 * kEpiPitch;
         const bool vec = ((uintptr_t)D % 16 == 0) && (ldd % 4 == 0);
         int tc = 0;
@@ -257,8 +293,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_after();
             const int row0 = t * kBM + quad * 32;
             const uint32_t tl = taddr + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * kBN);
-            for (int c0 = 0; c0 < N; c0 += 32) {
-                const int w = min(32, N - c0);  // 16 or 32 columns
+            for (int c0 = cbeg; c0 < cend; c0 += 32) {
+                const int w = min(32, cend - c0);  // 16 or 32 columns
                 float v[32];
                 tmem_ld16(tl + (uint32_t)c0, v);
                 if (w > 16)
@@ -299,6 +335,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             pp_flag(status, PP_FLAG_TIMEOUT);
             for (int st = 0; st < kStages && st < n_copied; ++st)
                 mbar_wait_bounded(&full[st], (uint32_t)(((n_copied - 1 - st) / kStages) & 1), 1ll << 24);
+            if (b_loaded)
+                mbar_wait_bounded(bfull, 0, 1ll << 24);
         }
         if (tid == 32) {
             for (int st = 0; st < kStages && st < n_committed; ++st)
@@ -336,36 +374,41 @@ __global__ void pack_bf16_kernel(const float *__restrict__ X, int rows, int cols
 
 namespace pp {
 
-int gemm_smem_bytes() { return kSmemBytes; }
-
 int launch_gemm_bf16(const void *A, const void *B, float *D, int M, int N, int K, int ldd,
                      cudaStream_t stream)
 {
     static bool attr_set[64] = {};
+    static int sms[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             kSmemBytes);
+        cudaError_t e = cudaFuncSetAttribute(gemm_bf16_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             GemmPlan<false>::smem_bytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(gemm_bf16_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     GemmPlan<true>::smem_bytes);
         if (e != cudaSuccess)
             return cuda_fail(e, "GEMM shared-memory attribute");
+        int n = 0;
+        e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "SM count");
+        sms[dev] = n;
         attr_set[dev] = true;
     }
     unsigned int *status = status_word();
     if (!status)
         return fail(PP_ERR_CUDA, "status word unavailable");
-    static int sms[64] = {};
-    if (dev >= 0 && dev < 64 && sms[dev] == 0) {
-        int n = 0;
-        cudaError_t e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess)
-            return cuda_fail(e, "SM count");
-        sms[dev] = n;
-    }
     const int ntiles = M / kBM;
     const int grid = (dev >= 0 && dev < 64 && sms[dev] > 0 && sms[dev] < ntiles) ? sms[dev] : ntiles;
-    gemm_bf16_kernel<<<grid, kThreads, kSmemBytes, stream>>>((const uint8_t *)A, (const uint8_t *)B, D, M, N, K,
-                                                            ldd, (long long)wait_limit(), status, skip_copies());
+    // B resident in shared memory when all its tiles fit: every CTA then reads B once
+    const bool resident = (K / kKC) * (N > 128 ? 2 : 1) <= kMaxResidentB;
+    if (resident)
+        gemm_bf16_kernel<true><<<grid, kThreads, GemmPlan<true>::smem_bytes, stream>>>(
+            (const uint8_t *)A, (const uint8_t *)B, D, M, N, K, ldd, (long long)wait_limit(), status, skip_copies());
+    else
+        gemm_bf16_kernel<false><<<grid, kThreads, GemmPlan<false>::smem_bytes, stream>>>(
+            (const uint8_t *)A, (const uint8_t *)B, D, M, N, K, ldd, (long long)wait_limit(), status, skip_copies());
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? PP_OK : cuda_fail(e, "GEMM launch");
 }

@@ -42,11 +42,13 @@ def test_gemm_matches_fp64_product_of_bf16_operands(pp, M, N, K):
     assert np.abs(D[:, N:].cpu().numpy()).max() == 0.0 if Np > N else True
 
 
-@pytest.mark.parametrize("M,N,K", [(128 * 400, 256, 128), (128 * 700, 48, 64)])
+@pytest.mark.parametrize("M,N,K", [(128 * 400, 256, 128), (128 * 700, 48, 64), (128 * 300, 256, 640),
+                                   (128 * 320, 112, 576)])
 def test_gemm_with_more_tiles_than_sms(pp, M, N, K):
     """More 128-row tiles than SMs: every CTA of the persistent kernel walks several
     tiles and reuses both TMEM accumulators, so the hand-back between the epilogue
-    and the MMA issuer is exercised."""
+    and the MMA issuer is exercised, with B resident in shared memory (the first two
+    shapes) and streamed with A (the last two: more than 8 B tiles)."""
     g = torch.Generator(device="cpu").manual_seed(M + N + K)
     A = torch.randn(M, K, generator=g).cuda()
     B = torch.randn(N, K, generator=g).cuda()
@@ -83,24 +85,25 @@ def test_gemm_rejects_bad_shapes(pp):
         pp.gemm_bf16(A, A, 128, 16, 48)
 
 
-def test_gemm_bounded_wait_gives_up_cleanly(pp):
-    """With the copies switched off no stage ever fills: the issuing thread's
-    bounded wait gives up, the kernel records PP_ERR_TIMEOUT, frees its TMEM and
-    returns; the next GEMM works."""
-    A = torch.randn(256, 128).cuda()
-    B = torch.randn(64, 128).cuda()
+@pytest.mark.parametrize("K", [128, 1024])  # B resident in shared memory / B streamed with A
+def test_gemm_bounded_wait_gives_up_cleanly(pp, K):
+    """With the copies switched off no stage ever fills: the bounded waits give up,
+    the kernel records PP_ERR_TIMEOUT, frees its TMEM and returns; the next GEMM
+    works."""
+    A = torch.randn(256, K).cuda()
+    B = torch.randn(64, K).cuda()
     Ap, _, _ = pp.pack_bf16(A)
     Bp, _, _ = pp.pack_bf16(B)
     old = pp.set_wait_limit(2000)
     pp.set_skip_copies(1)
     try:
-        pp.gemm_bf16(Ap, Bp, 256, 64, 128)
+        pp.gemm_bf16(Ap, Bp, 256, 64, K)
         st = pp.sync_status()
     finally:
         pp.set_skip_copies(0)
         pp.set_wait_limit(old)
     assert st == pp.PP_ERR_TIMEOUT
-    D = pp.gemm_bf16(Ap, Bp, 256, 64, 128)
+    D = pp.gemm_bf16(Ap, Bp, 256, 64, K)
     assert pp.sync_status() == pp.PP_OK
     ref = (bf16(A.cpu()) @ bf16(B.cpu()).T).numpy()
     assert np.abs(D.cpu().double().numpy() - ref).max() < 1e-3 * np.abs(ref).max()
