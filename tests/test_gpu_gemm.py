@@ -1,5 +1,7 @@
 """The BF16 tensor-core GEMM (tcgen05, FP32 accumulation) against an FP64
 product of the same BF16-rounded operands."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -61,6 +63,29 @@ def test_gemm_with_more_tiles_than_sms(pp, M, N, K):
     ref = (bf16(A.cpu()) @ bf16(B.cpu()).T).numpy()
     got = D.cpu().double().numpy()
     assert np.abs(got - ref).max() < 2e-5 * np.abs(ref).max() + 1e-5 * np.sqrt(K)
+
+
+@pytest.mark.parametrize("M,N,K,ldd", [(256, 144, 192, 144), (384, 144, 1024, 150), (256, 48, 64, 50)])
+def test_gemm_column_halves_and_unaligned_rows(pp, M, N, K, ldd):
+    """N between 128 and 256 (the second column half ends in a 16-column block) and
+    rows of D whose stride is not a multiple of 4 floats (the epilogue falls back
+    from 16-byte to 4-byte stores); columns past N are left alone."""
+    g = torch.Generator(device="cpu").manual_seed(M + N + K + ldd)
+    A = torch.randn(M, K, generator=g).cuda()
+    B = torch.randn(N, K, generator=g).cuda()
+    Ap, _, _ = pp.pack_bf16(A)
+    Bp, _, _ = pp.pack_bf16(B)
+    buf = torch.full((M, ldd), 7.0, device="cuda")
+    # through the C ABI: D is rows of ldd floats of which the first N are written
+    rc = pp.lib().pp_gemm_bf16(ctypes.c_void_p(Ap.data_ptr()), ctypes.c_void_p(Bp.data_ptr()),
+                               ctypes.c_void_p(buf.data_ptr()), M, N, K, ldd, None)
+    assert rc == pp.PP_OK
+    assert pp.sync_status() == pp.PP_OK
+    D = buf[:, :N]
+    ref = (bf16(A.cpu()) @ bf16(B.cpu()).T).numpy()
+    assert np.abs(D.cpu().double().numpy() - ref).max() < 2e-5 * np.abs(ref).max() + 1e-5 * np.sqrt(K)
+    if ldd > N:
+        assert torch.all(buf[:, N:] == 7.0)
 
 
 def test_gemm_transposed_packing(pp):
