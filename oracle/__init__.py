@@ -53,6 +53,15 @@ def lib():
         L.orc_de_propose.argtypes = [_pd, _i, _i, _pd, _pd, _pu8, _d, _d, _u64, _u64, _pd]
         L.orc_de_select.argtypes = [_pd, _pd, _pd, _pd, _i, _i]
         L.orc_num_threads.argtypes = [_i]
+        _vp = ctypes.c_void_p
+        L.pp_oracle_synth_field.argtypes = [_vp, ctypes.c_int32, _vp, _vp, ctypes.c_int32, _vp, _vp, _vp]
+        L.pp_oracle_pair_number.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _vp, _d, _vp, ctypes.c_int32,
+                                            ctypes.c_int32, _vp, _vp, _vp]
+        L.pp_oracle_de_propose.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp, _d, _d, _u64,
+                                           _u64, _vp, _vp]
+        L.pp_oracle_de_select.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int32, ctypes.c_int32, _vp]
+        L.pp_oracle_de_step.argtypes = [_vp, _vp, ctypes.c_int32, _vp, _vp, ctypes.c_int32, ctypes.c_int32, _vp,
+                                        _vp, _vp, _d, _d, _u64, _u64, _vp, _vp, _vp]
         L.orc_synth_hann.argtypes = [_pd, _i, _i, _i, _d, _d, _d, _d, _i, _i, _i, _pd, _pd, _pd,
                                      _pd]
         L.orc_synth_vjp_hann.argtypes = [_pd, _i, _i, _d, _d, _d, _i, _i, _pd, _pd, _pd, _pd, _pd,

@@ -1600,3 +1600,159 @@ int orc_de_select(double *pop, double *fit, const double *trial, const double *t
     }
     return ORC_OK;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Host mirror of the library's entry points                                 */
+/* ------------------------------------------------------------------------- */
+
+/* pp_oracle_* take the arguments of the CUDA library's pp_synth_field,
+ * pp_pair_number, pp_de_propose, pp_de_select and pp_de_step, in the same order
+ * and with the same meaning, but every array is a HOST pointer, the work is done
+ * here on the CPU in FP64 and `stream` is ignored (the call returns when done).
+ * The two structs below have the layout of the library's pulse model and
+ * momentum grid; they are declared here again because the oracle shares no
+ * header with the library.  Return values use the library's codes for the
+ * cases the oracle detects: 0 = OK, 1 = invalid argument, 4 = zero-fluence
+ * pulse. */
+typedef struct {
+    int32_t K;
+    int32_t order;
+    double w_min;
+    double w_max;
+    double T;
+    double fluence;
+    int32_t n_steps;
+    int32_t envelope; /* 0: g(t) = 1; 1: Hann envelope, Eq. (hann) */
+} orc_field_spec;
+
+typedef struct {
+    int32_t nx, ny, nz;
+    double x0, x1, y0, y1, z0, z1;
+    int32_t mirror_z;
+} orc_grid;
+
+enum { ORC_RK4 = 0, ORC_MAGNUS4 = 1, ORC_SPLIT2 = 2 };
+
+/* Eqs. (field), (energy), (hann), (vector_potential): as orc_synth_field
+ * (envelope 0) or orc_synth_hann with renormalisation (envelope 1). */
+int pp_oracle_synth_field(const double *params, int32_t ncand, const orc_field_spec *spec, double *A,
+                          int32_t ld, double *E, double *scale, void *stream)
+{
+    (void)stream;
+    if (!spec || (ncand > 0 && (!params || !A)) || (spec->envelope != 0 && spec->envelope != 1))
+        return ORC_ERR_ARG;
+    if (spec->envelope == 1)
+        return orc_synth_hann(params, ncand, spec->K, spec->order, spec->w_min, spec->w_max, spec->T,
+                              spec->fluence, 1, spec->n_steps, ld, A, E, NULL, scale);
+    return orc_synth_field(params, ncand, spec->K, spec->order, spec->w_min, spec->w_max, spec->T,
+                           spec->fluence, spec->n_steps, ld, A, E, scale);
+}
+
+/* Eq. (opt_prob) with the full spin trace of Eq. (pair_prod_homo): every mode
+ * integrated in FP64 with the requested scheme (classical RK4, the fourth-order
+ * Magnus step or the split operator); `precision` is checked and otherwise
+ * ignored (the oracle is FP64 throughout).  N = sum_p w(p) f(p) in grid order. */
+int pp_oracle_pair_number(const double *A, int32_t ncand, int32_t ld, const int32_t *n_steps, double dt,
+                          const orc_grid *grid, int32_t precision, int32_t scheme, double *N, double *n_p,
+                          void *stream)
+{
+    (void)stream;
+    if (!grid || ncand < 0 || (ncand > 0 && (!A || !N)) || !(dt > 0.0) || precision < 0 || precision > 2 ||
+        scheme < ORC_RK4 || scheme > ORC_SPLIT2 || grid->nx < 1 || grid->ny < 1 || grid->nz < 1)
+        return ORC_ERR_ARG;
+    const int nx = grid->nx, ny = grid->ny, nz = grid->nz, nm = nx * ny * nz;
+    double *p = malloc(sizeof(double) * 3 * (size_t)nm), *wgt = malloc(sizeof(double) * (size_t)nm);
+    double *wx = malloc(sizeof(double) * nx), *wy = malloc(sizeof(double) * ny), *wz = malloc(sizeof(double) * nz);
+    double *nbuf = malloc(sizeof(double) * (size_t)nm);
+    orc_trapz_weights(nx, grid->x0, grid->x1, 0, wx);
+    orc_trapz_weights(ny, grid->y0, grid->y1, 0, wy);
+    orc_trapz_weights(nz, grid->z0, grid->z1, grid->mirror_z, wz);
+    for (int k = 0; k < nz; k++)
+        for (int j = 0; j < ny; j++)
+            for (int i = 0; i < nx; i++) {
+                const int m = (k * ny + j) * nx + i;
+                p[3 * m + 0] = axis_point(i, nx, grid->x0, grid->x1);
+                p[3 * m + 1] = axis_point(j, ny, grid->y0, grid->y1);
+                p[3 * m + 2] = axis_point(k, nz, grid->z0, grid->z1);
+                wgt[m] = wx[i] * wy[j] * wz[k];
+            }
+    int status = ORC_OK;
+    for (int c = 0; c < ncand && status == ORC_OK; c++) {
+        const int ns = n_steps ? n_steps[c] : (ld - 1) / 2;
+        if (ns < 1 || ld < 2 * ns + 1) {
+            status = ORC_ERR_ARG;
+            break;
+        }
+        const double *Ac = A + (size_t)c * 2 * ld;
+        if (scheme == ORC_RK4)
+            status = orc_dirac_modes(Ac, ld, ns, dt, p, nm, 0, nbuf, 0);
+        else if (scheme == ORC_MAGNUS4)
+            status = orc_dirac_magnus_modes(Ac, ld, ns, dt, p, nm, nbuf, NULL, 0);
+        else
+            status = orc_dirac_split_modes(Ac, ld, ns, dt, p, nm, nbuf, NULL, 0);
+        double s = 0.0;
+        for (int m = 0; m < nm; m++)
+            s += wgt[m] * nbuf[m];
+        N[c] = s;
+        if (n_p)
+            memcpy(n_p + (size_t)c * nm, nbuf, sizeof(double) * (size_t)nm);
+    }
+    free(p);
+    free(wgt);
+    free(wx);
+    free(wy);
+    free(wz);
+    free(nbuf);
+    return status;
+}
+
+/* Sec. IV.B, steps 1-3 (orc_de_propose). */
+int pp_oracle_de_propose(const double *pop, int32_t NP, int32_t D, const double *lo, const double *hi,
+                         const uint8_t *periodic, double F, double CR, uint64_t seed, uint64_t generation,
+                         double *trial, void *stream)
+{
+    (void)stream;
+    return orc_de_propose(pop, NP, D, lo, hi, periodic, F, CR, seed, generation, trial);
+}
+
+/* Sec. IV.B, step 4 (orc_de_select). */
+int pp_oracle_de_select(double *pop, double *fit, const double *trial, const double *trial_fit, int32_t NP,
+                        int32_t D, void *stream)
+{
+    (void)stream;
+    return orc_de_select(pop, fit, trial, trial_fit, NP, D);
+}
+
+/* One generation of Sec. IV.B: propose, synthesise the trials (Sec. III),
+ * score them (Sec. II.A, Eq. (opt_prob)), select.  D = 4 K; the trials take
+ * spec->n_steps steps of dt = T / n_steps.  trial_out [NP][D] and
+ * trial_fit_out [NP] receive the proposals and their pair numbers (may be NULL). */
+int pp_oracle_de_step(double *pop, double *fit, int32_t NP, const orc_field_spec *spec, const orc_grid *grid,
+                      int32_t precision, int32_t scheme, const double *lo, const double *hi, const uint8_t *periodic,
+                      double F, double CR, uint64_t seed, uint64_t generation, double *trial_out,
+                      double *trial_fit_out, void *stream)
+{
+    (void)stream;
+    if (!spec || !grid || !pop || !fit || NP < 4 || spec->n_steps < 1 || !(spec->T > 0.0))
+        return ORC_ERR_ARG;
+    const int D = 4 * spec->K, ld = 2 * spec->n_steps + 1;
+    double *trial = malloc(sizeof(double) * (size_t)NP * D), *tfit = malloc(sizeof(double) * (size_t)NP);
+    double *A = malloc(sizeof(double) * (size_t)NP * 2 * ld);
+    int status = orc_de_propose(pop, NP, D, lo, hi, periodic, F, CR, seed, generation, trial);
+    if (status == ORC_OK)
+        status = pp_oracle_synth_field(trial, NP, spec, A, ld, NULL, NULL, NULL);
+    if (status == ORC_OK)
+        status = pp_oracle_pair_number(A, NP, ld, NULL, spec->T / spec->n_steps, grid, precision, scheme, tfit,
+                                       NULL, NULL);
+    if (status == ORC_OK) {
+        if (trial_out)
+            memcpy(trial_out, trial, sizeof(double) * (size_t)NP * D);
+        if (trial_fit_out)
+            memcpy(trial_fit_out, tfit, sizeof(double) * (size_t)NP);
+        status = orc_de_select(pop, fit, trial, tfit, NP, D);
+    }
+    free(trial);
+    free(tfit);
+    free(A);
+    return status;
+}
