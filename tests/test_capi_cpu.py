@@ -133,3 +133,25 @@ def test_product_package_does_not_import_the_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle\b", txt, re.M), f
                 assert "pp_oracle" not in txt and "liboracle" not in txt, f
+
+
+def test_envelope_limits_are_checked_on_the_host(pp):
+    """The Hann envelope widens the band by one harmonic on each side, so its mode
+    limit is 1534 instead of 1536; uneven batches need one envelope for all slots.
+    Every call here is refused before any device work."""
+    import math
+    L = pp.lib()
+    T = 1535.5 * math.pi  # w_max = 2: modes j = 1 .. 1535
+    hann = pp.FieldSpec(8, 4, 0.0, 2.0, T, 2.0, 100, 1)
+    rc = L.pp_synth_field(ctypes.c_void_p(8), 1, ctypes.byref(hann), ctypes.c_void_p(8), 201, None, None, None)
+    assert rc == pp.PP_ERR_INVALID_ARG and b"1534" in L.pp_last_error()
+    specs = [pp.FieldSpec(8, 4, 0.0, 2.0, 50.0 + c, 2.0, 1000 + 20 * c, 1 if c == 2 else 0) for c in range(4)]
+    grids = [pp._grid(dict(nx=2, ny=2, nz=1, x0=-1.0, x1=1.0, y0=-1.0, y1=1.0, z0=0.0, z1=0.0))] * 4
+    S, G = (pp.FieldSpec * 4)(*specs), (pp.Grid * 4)(*grids)
+    h = ctypes.c_void_p()
+    rc = L.pp_batch_create(4, S, G, 0, 0, 0.05, ctypes.byref(h))
+    assert rc == pp.PP_ERR_INVALID_ARG and b"envelope" in L.pp_last_error() and not h.value
+    for c in range(4):
+        S[c].envelope = 2
+    rc = L.pp_batch_create(4, S, G, 0, 0, 0.05, ctypes.byref(h))
+    assert rc == pp.PP_ERR_NOT_IMPLEMENTED and not h.value
