@@ -290,7 +290,7 @@ const PolicySlot &policy_slot(int precision, int scheme)
          {d_spl.run_fn, d_spl.static_fn, false, 0}},
         {{f_rk4.run_fn, f_rk4.static_fn, true, 0}, {f_mag.run_fn, f_mag.static_fn, true, 2},
          {f_spl.run_fn, f_spl.static_fn, true, 0}},
-        {{x_rk4.run_fn, x_rk4.static_fn, true, 0}, {x_mag.run_fn, x_mag.static_fn, true, 3},
+        {{x_rk4.run_fn, x_rk4.static_fn, true, 0}, {x_mag.run_fn, x_mag.static_fn, true, 0},
          {x_spl.run_fn, x_spl.static_fn, true, 3}},
     };
     return slots[precision][scheme];
