@@ -241,7 +241,8 @@ int pp_gemm_bf16(const void *A, const void *B, float *D, int32_t M, int32_t N, i
  * backward kernels (hidden layers on the tensor cores via pp_gemm_bf16; FP32
  * master weights, biases, activations and Adam).  Parameters are one FP32 vector
  * [W1 (H x d_in), b1, W2 (H x H), b2, W3 (H x H), b3, w4 (H), b4].
- *  pp_mlp_create       allocates everything for batches up to max_batch.
+ *  pp_mlp_create       allocates everything for batches up to max_batch
+ *                      (1 <= d_in <= 256, H = 128 or 256: whole 128-row GEMM tiles).
  *  pp_mlp_set_params / pp_mlp_get_params  copy the parameter vector (host or device
  *                      pointer); set_params also resets Adam.
  *  pp_mlp_forward      y (device [B]) for inputs X (device FP32 [B][d_in]).

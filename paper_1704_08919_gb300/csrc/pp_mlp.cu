@@ -471,10 +471,10 @@ int pp_mlp_create(int32_t d_in, int32_t hidden, int32_t max_batch, pp_mlp **out)
     if (!out)
         return fail(PP_ERR_INVALID_ARG, "out must not be NULL");
     *out = nullptr;
-    if (d_in < 1 || d_in > 256 || hidden < 16 || hidden > 256 || hidden % 16 || max_batch < 1 ||
-        max_batch > (1 << 20))
-        return fail(PP_ERR_INVALID_ARG, "need 1 <= d_in <= 256, hidden in [16, 256] with hidden %% 16 == 0, "
-                                        "1 <= max_batch <= 2^20");
+    // hidden is a whole number of 128-row GEMM tiles: it is the M of the weight-gradient
+    // products and the K (and packed width) of the hidden layers
+    if (d_in < 1 || d_in > 256 || (hidden != 128 && hidden != 256) || max_batch < 1 || max_batch > (1 << 20))
+        return fail(PP_ERR_INVALID_ARG, "need 1 <= d_in <= 256, hidden = 128 or 256, 1 <= max_batch <= 2^20");
     pp_mlp *h = new pp_mlp();
     cudaGetDevice(&h->dev);
     h->din = d_in;

@@ -155,3 +155,15 @@ def test_envelope_limits_are_checked_on_the_host(pp):
         S[c].envelope = 2
     rc = L.pp_batch_create(4, S, G, 0, 0, 0.05, ctypes.byref(h))
     assert rc == pp.PP_ERR_NOT_IMPLEMENTED and not h.value
+
+
+def test_surrogate_sizes_are_checked_on_the_host(pp):
+    """The hidden width is a whole number of 128-row GEMM tiles; other widths are
+    refused before anything is allocated."""
+    L = pp.lib()
+    h = ctypes.c_void_p()
+    for hidden in (16, 64, 144, 192, 512):
+        rc = L.pp_mlp_create(32, hidden, 256, ctypes.byref(h))
+        assert rc == pp.PP_ERR_INVALID_ARG and not h.value, hidden
+    assert L.pp_mlp_create(0, 256, 256, ctypes.byref(h)) == pp.PP_ERR_INVALID_ARG
+    assert L.pp_mlp_create(300, 256, 256, ctypes.byref(h)) == pp.PP_ERR_INVALID_ARG
