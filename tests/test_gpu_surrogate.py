@@ -40,9 +40,11 @@ def setup(d_in, H, B, seed):
     return p, X, t
 
 
-@pytest.mark.parametrize("d_in,B", [(32, 128), (32, 300), (64, 256)])
-def test_forward_and_gradient_match_oracle(pp, d_in, B):
-    H = 256
+@pytest.mark.parametrize("d_in,B,H", [(32, 128, 256), (32, 300, 256), (64, 256, 256), (100, 200, 128),
+                                     (200, 260, 256)])
+def test_forward_and_gradient_match_oracle(pp, d_in, B, H):
+    # d_in 100 and 200 pad to 128 and 256 input columns (the weight gradient of the
+    # first layer then has one or two column halves); H = 128 is one row tile
     p, X, t = setup(d_in, H, B, seed=d_in + B)
     net = pp.Surrogate(d_in, H, max_batch=512)
     net.set_params(torch.tensor(p, dtype=torch.float32, device="cuda"))
