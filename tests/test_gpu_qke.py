@@ -274,3 +274,28 @@ def test_rejects_bad_arguments(pp):
     with pytest.raises(pp.PPError):
         pp.qke_pair_number(A, A, A, 0.0, inputs.small_grid(2, 2, 1))
     assert pp.sync_status() == pp.PP_OK
+
+
+def test_chunked_gradient_equals_single_start_calls(pp):
+    """At the local-search size one start's checkpoints take ~0.8 GB, so 12 starts
+    exceed the adjoint's 8 GiB working budget and run in two chunks.  Every start's
+    work is independent and its sums run in a fixed order, so the batched J and
+    gradient equal those of single-start calls bit for bit."""
+    cfg = inputs.LOCAL_SEARCH
+    sp = dict(inputs.field_spec(dict(cfg, fluence=1.0)))
+    Kf = cfg["K"]
+    X = inputs.random_population(12, Kf, seed=31)
+    _, _, U0, _ = pp.qke_gradient(dev(X), sp, cfg["grid"], "fp32", want_grad=False)
+    sc = np.sqrt(cfg["U_const"] / U0.cpu().numpy())  # the starts of the local search: fluence U_const
+    X[:, :Kf] *= sc[:, None]
+    X[:, 2 * Kf:3 * Kf] *= sc[:, None]
+    Xd = dev(X)
+    J, gJ, U, dU = pp.qke_gradient(Xd, sp, cfg["grid"], "fp32")
+    assert pp.sync_status() == pp.PP_OK
+    for c in (0, 5, 9, 10, 11):
+        J1, g1, U1, dU1 = pp.qke_gradient(Xd[c:c + 1].contiguous(), sp, cfg["grid"], "fp32")
+        assert pp.sync_status() == pp.PP_OK
+        assert torch.equal(J[c:c + 1], J1) or (torch.isnan(J[c]) and torch.isnan(J1[0]))
+        assert torch.equal(gJ[c:c + 1], g1) or (torch.isnan(J[c]) and torch.isnan(J1[0]))
+        assert torch.equal(U[c:c + 1], U1) and torch.equal(dU[c:c + 1], dU1)
+    assert torch.isfinite(J).sum() >= 6
