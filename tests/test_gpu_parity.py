@@ -479,3 +479,35 @@ def test_release_scratch_then_reuse(pp):
     N2, _ = pp.pair_number(At, dt, grid, precision="fp64")
     assert pp.sync_status() == pp.PP_OK
     assert torch.equal(N1, N2)
+
+
+def test_empty_inputs_are_no_ops(pp):
+    """Zero candidates: every scoring entry point returns at once with empty results
+    and leaves no error behind (the launch-configuration tuner, which needs a
+    workload to time, refuses them instead)."""
+    cfg = inputs.DE_BATCH
+    n = 200
+    spec = dict(inputs.field_spec(cfg), n_steps=n)
+    grid = inputs.small_grid(3, 3, 2)
+    dt = spec["T"] / n
+    P = torch.empty((0, 4 * cfg["K"]), dtype=torch.float64, device=DEV)
+    A, E, s = pp.synth_field(P, spec, want_E=True, want_scale=True)
+    assert A.shape == (0, 2, 2 * n + 1) and s.shape == (0,)
+    for precision in ("fp64", "fp32", "fp32fast"):
+        N, nn = pp.pair_number(A, dt, grid, precision=precision, want_n=True)
+        assert N.shape == (0,) and nn.shape[0] == 0
+    N, _ = pp.pair_number_static(A, dt, grid, precision="fp32")
+    assert N.shape == (0,)
+    Ar, Er, Edr, Ur = pp.synth_field_raw(P, spec)
+    assert Ar.shape == (0, 2, 2 * n + 1)
+    J, _ = pp.qke_pair_number(Ar, Er, Edr, dt, grid, "fp32")
+    assert J.shape == (0,)
+    g = torch.empty((0, 6, 2 * n + 1), dtype=torch.float64, device=DEV)
+    grad, U, dU = pp.synth_vjp(P, spec, g)
+    assert grad.shape == (0, 4 * cfg["K"])
+    J, gJ, U, dU = pp.qke_gradient(P, spec, grid, "fp32")
+    assert J.shape == (0,) and gJ.shape == (0, 4 * cfg["K"])
+    assert pp.sync_status() == pp.PP_OK
+    with pytest.raises(pp.PPError):
+        pp.tune_pair_number(A, dt, grid)
+    assert pp.sync_status() == pp.PP_OK
