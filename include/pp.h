@@ -228,7 +228,11 @@ int pp_batch_de_run(pp_batch *batch, double *pop, double *fit, const double *lo,
  * transposed) into P (device), rounding to nearest.
  * pp_gemm_bf16 computes D[M][N] = A[M][K] . B[N][K]^T into FP32 D (device,
  * row-major, leading dimension ldd) from packed A (M x K) and B (N x K):
- * M % 128 == 0, 16 <= N <= 256 with N % 16 == 0, K % 64 == 0. */
+ * M % 128 == 0, 16 <= N <= 256 with N % 16 == 0, K % 64 == 0, ldd >= N.  Columns
+ * N .. ldd - 1 of D are not written.  The accumulation order over K is fixed
+ * (64-wide chunks in order), so results are reproducible run to run.  Errors:
+ * PP_ERR_INVALID_ARG for the shape conditions or NULL pointers; a stalled copy
+ * on the device surfaces as PP_ERR_TIMEOUT through pp_sync_status. */
 size_t pp_packed_bf16_bytes(int32_t rows, int32_t cols);
 int pp_pack_bf16(const float *X, int32_t rows, int32_t cols, int32_t ldx, int32_t transpose, void *P,
                  void *stream);
