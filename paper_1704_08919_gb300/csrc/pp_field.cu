@@ -227,7 +227,7 @@ __global__ void samples_kernel(const double2 *__restrict__ coef, int M, int j0, 
     sincospi((double)(((long long)k * j0) % two_n) / (double)n_steps, &js, &jc);
     // Horner: sum_{m=0}^{M-1} X_m z^m
     double cr = 0.0, ci = 0.0, dr = 0.0, di = 0.0, gr = 0.0, gi = 0.0;
-    double d0r = 0.0, d0i = 0.0;  // sum of D_j (the z = 1 value)
+    double d0i = 0.0;  // Im of the sum of D_j (the z = 1 value)
     for (int m = M - 1; m >= 0; --m) {
         const double2 C = sc[m], D = sc[M + m];
         double tr = cr * zc - ci * zs + C.x;
@@ -236,7 +236,6 @@ __global__ void samples_kernel(const double2 *__restrict__ coef, int M, int j0, 
         tr = dr * zc - di * zs + D.x;
         di = dr * zs + di * zc + D.y;
         dr = tr;
-        d0r += D.x;
         d0i += D.y;
         if (Ed) {  // dE/dt: coefficients i Omega_j C_j
             const double W = (double)(j0 + m) * dw;
@@ -257,7 +256,6 @@ __global__ void samples_kernel(const double2 *__restrict__ coef, int M, int j0, 
         E[((size_t)c * 2 + l) * ld + k] = Cr;
     if (Ed)
         Ed[((size_t)c * 2 + l) * ld + k] = gr * jc - gi * js;
-    (void)d0r;
 }
 
 // ---- chain rule of the un-normalised synthesis (the local search's gradient):
@@ -424,7 +422,6 @@ __global__ void hann_vjp_modes_kernel(const double *__restrict__ params, int K, 
                                       double2 *__restrict__ eph, double2 *__restrict__ dEP,
                                       double2 *__restrict__ dUP, double *__restrict__ U_out)
 {
-    __shared__ double red[256];
     const int c = blockIdx.x, Mp = M + 2, j0p = j0 - 1;
     const double *prm = params + (size_t)c * 4 * K;
     const double dw = 2.0 * M_PI / T;
@@ -462,15 +459,10 @@ __global__ void hann_vjp_modes_kernel(const double *__restrict__ params, int K, 
         hc[q] = v;
         ssq += (j0p + m == 0) ? 2.0 * v.x * v.x : v.x * v.x + v.y * v.y;
     }
-    red[threadIdx.x] = ssq;
-    __syncthreads();
-    for (int hh = blockDim.x / 2; hh > 0; hh >>= 1) {
-        if (threadIdx.x < hh)
-            red[threadIdx.x] += red[threadIdx.x + hh];
-        __syncthreads();
-    }
+    // block_sum's barriers also order the C' writes above before the reads below
+    const double usum = block_sum(ssq);
     if (threadIdx.x == 0 && U_out)
-        U_out[c] = 0.5 * T * red[0];
+        U_out[c] = 0.5 * T * usum;
     // dU/dC'_j: T C'_j (j >= 1), 2 T Re C'_0 (j = 0); transposed to the modes
     for (int q = threadIdx.x; q < 2 * M; q += blockDim.x) {
         const int l = q / M, m = q % M;
