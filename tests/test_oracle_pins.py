@@ -136,6 +136,88 @@ def test_linear_vs_circular_peak_field_ratio_sqrt2():
     assert abs(peaks[0] / peaks[1] - math.sqrt(2.0)) < 1e-13
 
 
+def _field_by_hand(aE, aP, K, order, wmin, wmax, T, n_steps):
+    """Eq. (field) with g = 1 and s = 1 for one polarisation, written out
+    independently of the oracle: spectrum E~_j = sum_i aE_i B_i(Omega_j) and
+    Phi_j = sum_i aP_i B_i(Omega_j) with scipy's B-splines (Eqs. (coeff_basis_E),
+    (coeff_basis_phi)), E(t) = sum_j E~_j cos(Omega_j t - Phi_j) and A(t) =
+    -int_{-T/2}^t E on the half-step grid.  Returns (E, A, (T/2) sum_j E~_j^2)."""
+    from scipy.interpolate import BSpline
+    n = K - order + 2
+    knots = np.concatenate([[wmin] * order, np.linspace(wmin, wmax, n)[1:-1], [wmax] * order])
+    dw = 2 * math.pi / T
+    W = dw * np.arange(1, int(math.floor(wmax / dw + 1e-12)) + 1)
+    W = W[W >= wmin]
+    Bm = np.array([BSpline(knots, np.eye(K)[i], order - 1, extrapolate=False)(W) for i in range(K)])
+    Bm = np.nan_to_num(Bm)
+    Et, Ph = aE @ Bm, aP @ Bm
+    t = -0.5 * T + np.arange(2 * n_steps + 1) * (T / (2 * n_steps))
+    arg = np.outer(t, W) - Ph
+    E = np.cos(arg) @ Et
+    A = -((np.sin(arg) - np.sin(-0.5 * T * W - Ph)) / W) @ Et
+    return E, A, 0.5 * T * np.sum(Et ** 2)
+
+
+@pytest.mark.parametrize("pol", [0, 1])
+def test_synth_single_amplitude_weight_with_phase_offset(pol):
+    # Sec. III, Eqs. (coeff_basis_E), (field): one nonzero amplitude weight a^E_{l,i}
+    # and a constant phase weight Phi_0 (partition of unity makes Phi_j = Phi_0 for
+    # every mode) give E_l(t) = s sum_j B_i(Omega_j) cos(Omega_j t - Phi_0).  A sign
+    # error on Phi or a coefficient/basis mispairing fails this for some i.
+    cfg = inputs.DE_BATCH
+    K, order, T, U, ns = cfg["K"], cfg["order"], cfg["T"], cfg["fluence"], 512
+    phi0 = 0.7
+    for i in range(K):
+        prm = np.zeros(4 * K)
+        prm[2 * pol * K + i] = 1.0
+        prm[(2 * pol + 1) * K:(2 * pol + 2) * K] = phi0
+        A, E, s, rc = o.synth_field(prm, K, order, cfg["w_min"], cfg["w_max"], T, U, ns)
+        assert rc == 0
+        e_ref, a_ref, u_raw = _field_by_hand(prm[2 * pol * K:(2 * pol + 1) * K], np.full(K, phi0), K,
+                                             order, cfg["w_min"], cfg["w_max"], T, ns)
+        sc = math.sqrt(U / u_raw)
+        assert abs(s[0] / sc - 1) < 1e-14
+        assert np.abs(E[0, pol] - sc * e_ref).max() <= 1e-13 * sc * np.abs(e_ref).max()
+        assert np.abs(A[0, pol] - sc * a_ref).max() <= 1e-13 * sc * np.abs(a_ref).max()
+        assert np.abs(E[0, 1 - pol]).max() == 0.0 and np.abs(A[0, 1 - pol]).max() == 0.0
+
+
+@pytest.mark.parametrize("pol", [0, 1])
+def test_synth_single_phase_weight(pol):
+    # Sec. III, Eqs. (coeff_basis_phi), (field): unit amplitude weights (E~_j = 1) and
+    # one nonzero phase weight a^phi_{l,i} = a give E_l(t) = s sum_j cos(Omega_j t - a B_i(Omega_j)).
+    cfg = inputs.DE_BATCH
+    K, order, T, U, ns = cfg["K"], cfg["order"], cfg["T"], cfg["fluence"], 512
+    for i in range(K):
+        prm = np.zeros(4 * K)
+        prm[2 * pol * K:(2 * pol + 1) * K] = 1.0
+        prm[(2 * pol + 1) * K + i] = 2.1
+        A, E, s, rc = o.synth_field(prm, K, order, cfg["w_min"], cfg["w_max"], T, U, ns)
+        assert rc == 0
+        e_ref, a_ref, u_raw = _field_by_hand(np.ones(K), prm[(2 * pol + 1) * K:(2 * pol + 2) * K], K,
+                                             order, cfg["w_min"], cfg["w_max"], T, ns)
+        sc = math.sqrt(U / u_raw)
+        assert np.abs(E[0, pol] - sc * e_ref).max() <= 1e-13 * sc * np.abs(e_ref).max()
+        assert np.abs(A[0, pol] - sc * a_ref).max() <= 1e-13 * sc * np.abs(a_ref).max()
+
+
+def test_synth_random_weights_both_polarisations():
+    # Eq. (field) for a general candidate: both polarisations, random amplitude and
+    # phase weights, one global scale s from the fluence of both (Eq. (energy)).
+    cfg = inputs.DE_BATCH
+    K, order, T, U, ns = cfg["K"], cfg["order"], cfg["T"], cfg["fluence"], 256
+    prm = inputs.random_population(1, K, seed=17)[0]
+    A, E, s, rc = o.synth_field(prm, K, order, cfg["w_min"], cfg["w_max"], T, U, ns)
+    assert rc == 0
+    refs = [_field_by_hand(prm[2 * l * K:(2 * l + 1) * K], prm[(2 * l + 1) * K:(2 * l + 2) * K], K, order,
+                           cfg["w_min"], cfg["w_max"], T, ns) for l in (0, 1)]
+    sc = math.sqrt(U / (refs[0][2] + refs[1][2]))
+    for l in (0, 1):
+        e_ref, a_ref = sc * refs[l][0], sc * refs[l][1]
+        assert np.abs(E[0, l] - e_ref).max() <= 1e-12 * np.abs(e_ref).max()
+        assert np.abs(A[0, l] - a_ref).max() <= 1e-12 * np.abs(a_ref).max()
+
+
 def test_zero_fluence_is_degenerate():
     K = 8
     prm = np.zeros((1, 4 * K))
