@@ -58,8 +58,15 @@ typedef enum {
     PP_FP32_FAST = 2 /* as PP_FP32 but with plain FP32 accumulation of the state: about 27%
                         faster; N stays within ~2e-6 of FP64 on the DE-batch workload while
                         single n(p) values lose accuracy (a rounding walk of ~1e-6 in the
-                        transition amplitude) */
+                        transition amplitude): n_p is written in this mode but is not accurate
+                        mode by mode, and no flag marks it; use PP_FP32 or PP_FP64 where n(p)
+                        itself matters */
 } pp_precision;
+/* Note on the FP32 paths.  A recipe that keeps the time coordinate and the
+ * dynamical phase in FP64 has no counterpart here: the propagation runs on two
+ * 2-level systems in the lab frame, time is an index into a table of potential
+ * samples synthesised in FP64 at exact grid times, and the initial state, the
+ * projection and the momentum sum are FP64. */
 
 /* Time integrator of the momentum-space Dirac equation (all on the same grid:
  * step dt, potential samples at t_n, t_n + dt/2, t_n + dt).
@@ -68,7 +75,17 @@ typedef enum {
  *             parity path against the CPU oracle.
  *  PP_MAGNUS4 fourth-order Magnus step exp(Omega), Omega = -i dt/6 (H_0 + 4 H_h +
  *             H_1) + dt^2/12 [H_0, H_1]: unitary; the fourth-order scheme the
- *             paper's outlook (Sec. V.C.2) calls for.
+ *             paper's outlook (Sec. V.C.2) calls for.  On each 2-level system the
+ *             step is exp(-i th n.sigma) with th = |dt h_eff|; cos th - 1 and
+ *             sin th / th come from even polynomials, which hold (to FP32/FP64
+ *             rounding) for th <= 0.2.  The step table bounds th per step over the
+ *             whole momentum grid (corner momenta and the step's potential terms);
+ *             every tile of steps in which that bound exceeds 0.2 takes an
+ *             argument-halved form instead (th halved k times into the range, the
+ *             polynomials there, k double-angle steps back), which is exact for th
+ *             up to 0.2 * 2^60 and costs about 2k more instructions per step.  The
+ *             workloads here stay near th = 0.11-0.14 (dt ~ 0.02, |p| <= 2.5), where
+ *             only the polynomials run.
  *  PP_SPLIT2  second-order Strang split operator, the paper's own integrator
  *             (Sec. II.A): free part alpha.p + beta (two half steps), coupling
  *             -alpha.A(t_n + dt/2) (one full step), each factor an exact
@@ -139,7 +156,9 @@ int pp_synth_field(const double *params, int32_t ncand, const pp_field_spec *spe
  *  n_steps (host)   [ncand] steps per candidate (each 2 n_steps[c] + 1 <= ld), or
  *                   NULL: every candidate takes (ld - 1) / 2 steps.
  *  dt      step size (> 0).
- *  grid    (host)   momentum grid shared by all candidates.
+ *  grid    (host)   momentum grid shared by all candidates.  (This entry point takes
+ *                   one grid; candidates with grids of their own, and their own pulse
+ *                   lengths, are scored together by pp_batch_pair_number.)
  *  precision PP_FP64, PP_FP32 or PP_FP32_FAST.
  *  scheme  PP_RK4, PP_MAGNUS4 or PP_SPLIT2.
  *  N       (device) [ncand] FP64 output.

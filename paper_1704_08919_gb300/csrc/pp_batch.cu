@@ -28,33 +28,46 @@ struct BatchCand {
     long long part_off;   // partial sums before this candidate's
 };
 
+// As build_table_kernel, per slot with its own grid and step count; wide_flags[c]
+// (zeroed before the launch) marks slots that leave the policy's series range.
 template <class P>
 __global__ void build_table_batch_kernel(const double *__restrict__ A, int ld,
                                          const BatchCand *__restrict__ cands, int row_quantum, double dt,
-                                         typename P::Entry *__restrict__ table)
+                                         typename P::Entry *__restrict__ table, int *__restrict__ wide_flags)
 {
     const int c = blockIdx.y;
     const BatchCand d = cands[c];
     const int padded = ((d.ns + row_quantum - 1) / row_quantum) * row_quantum;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= padded)
-        return;
     const double *Ax = A + (size_t)c * 2 * ld, *Ay = Ax + ld;
-    typename P::Entry e;
-    if (n < d.ns)
-        e = table_entry((const P *)nullptr, Ax, Ay, n, dt);
-    else
-        memset(&e, 0, sizeof e);
-    table[d.table_off + n] = e;
+    bool big = false;
+    if (n < padded) {
+        typename P::Entry e;
+        if (n < d.ns) {
+            e = table_entry((const P *)nullptr, Ax, Ay, n, dt, d.g);
+            if constexpr (HasSeriesGuard<P>::value)
+                big = P::beyond_series(e);
+        } else {
+            memset(&e, 0, sizeof e);
+        }
+        table[d.table_off + n] = e;
+    }
+    if constexpr (HasSeriesGuard<P>::value) {
+        if (__syncthreads_or(big) && threadIdx.x == 0)
+            atomicOr(wide_flags + c, 1);
+    }
 }
 
-template <class P, int THREADS, int TILE_BYTES>
+// WIDE selects the slots this launch takes (see takes_candidate); items of the
+// other kind are drawn from the queue and skipped.
+template <class P, int THREADS, int TILE_BYTES, bool WIDE>
 __global__ void __launch_bounds__(THREADS)
     propagate_batch_kernel(const double *__restrict__ A, int ld, const BatchCand *__restrict__ cands,
                            const int2 *__restrict__ work, int nwork, int *__restrict__ counter,
                            const typename P::Entry *__restrict__ table, double dt,
                            double *__restrict__ n_p, double *__restrict__ partial,
-                           long long wait_limit, int skip_copies, unsigned int *__restrict__ status)
+                           long long wait_limit, int skip_copies, unsigned int *__restrict__ status,
+                           const int *__restrict__ wide_flags)
 {
     using V = typename P::Entry;
     constexpr int TILE = TILE_BYTES / (int)sizeof(V);
@@ -75,9 +88,13 @@ __global__ void __launch_bounds__(THREADS)
         if (it >= nwork)
             break;
         const int2 w = work[it];
+        if (!takes_candidate<P, WIDE>(wide_flags, w.x)) {
+            __syncthreads();  // every thread has read s_item before thread 0 draws again
+            continue;
+        }
         const BatchCand d = cands[w.x];
         const double *Ax = A + (size_t)w.x * 2 * ld;
-        const bool ok = process_item<P, THREADS, TILE_BYTES>(
+        const bool ok = process_item<P, THREADS, TILE_BYTES, WIDE>(
             sm, w.y, d.g, d.ns, table + d.table_off, Ax, Ax + ld, dt, n_p ? n_p + d.n_off : nullptr,
             partial + d.part_off, wait_limit, skip_copies, status, tile_base);
         if (!ok)
@@ -144,15 +161,21 @@ int run_batch(const BatchLaunch &L, cudaStream_t stream)
     unsigned int *status = pp::status_word();
     if (!status)
         return pp::fail(PP_ERR_CUDA, "status word unavailable");
-    cudaError_t e = cudaMemsetAsync(L.counter, 0, sizeof(int), stream);
+    // counter[0], counter[1]: the work counters of the two launches; counter[2 + c]: wide flags
+    cudaError_t e = cudaMemsetAsync(L.counter, 0, sizeof(int) * (2 + (size_t)L.ncand), stream);
     if (e != cudaSuccess)
         return pp::cuda_fail(e, "batch work counter reset");
+    int *flags = L.counter + 2;
     dim3 tg((L.max_padded + 255) / 256, L.ncand);
     build_table_batch_kernel<P><<<tg, 256, 0, stream>>>(L.A, L.ld, L.cands, L.row_quantum, L.dt,
-                                                       (typename P::Entry *)L.table);
-    propagate_batch_kernel<P, THREADS, TILE_BYTES><<<L.grid_ctas, THREADS, 0, stream>>>(
+                                                       (typename P::Entry *)L.table, flags);
+    propagate_batch_kernel<P, THREADS, TILE_BYTES, false><<<L.grid_ctas, THREADS, 0, stream>>>(
         L.A, L.ld, L.cands, L.work, L.nwork, L.counter, (const typename P::Entry *)L.table, L.dt,
-        L.n_p, L.partial, (long long)pp::wait_limit(), pp::skip_copies(), status);
+        L.n_p, L.partial, (long long)pp::wait_limit(), pp::skip_copies(), status, flags);
+    if constexpr (HasSeriesGuard<P>::value)
+        propagate_batch_kernel<P, THREADS, TILE_BYTES, true><<<L.grid_ctas, THREADS, 0, stream>>>(
+            L.A, L.ld, L.cands, L.work, L.nwork, L.counter + 1, (const typename P::Entry *)L.table, L.dt,
+            L.n_p, L.partial, (long long)pp::wait_limit(), pp::skip_copies(), status, flags);
     finalize_batch_kernel<<<L.ncand, 256, 0, stream>>>(L.partial, L.cands, L.N, status);
     e = cudaGetLastError();
     if (e != cudaSuccess)
@@ -164,7 +187,7 @@ template <class P, int THREADS, int TILE_BYTES>
 int occupancy(int *blocks)
 {
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        blocks, propagate_batch_kernel<P, THREADS, TILE_BYTES>, THREADS, 0);
+        blocks, propagate_batch_kernel<P, THREADS, TILE_BYTES, false>, THREADS, 0);
     return e == cudaSuccess ? PP_OK : pp::cuda_fail(e, "occupancy query");
 }
 
@@ -418,7 +441,7 @@ int pp_batch_create(int32_t ncand, const pp_field_spec *specs, const pp_grid *gr
     if (e == cudaSuccess)
         e = cudaMalloc(&b->d_partial, sizeof(double) * (size_t)poff);
     if (e == cudaSuccess)
-        e = cudaMalloc(&b->d_counter, sizeof(int));
+        e = cudaMalloc(&b->d_counter, sizeof(int) * (2 + (size_t)ncand));
     // work lists (longest candidates first) for each CTA size
     const int sizes[3] = {128, 256, 512};
     std::vector<int> order(ncand);

@@ -366,7 +366,14 @@ struct PackedPolicy {
 
 // cos(th) - 1 and sin(th)/th as polynomials in t = th^2 for th <= 0.2: FP32
 // keeps terms through th^6 / th^4 (the rest is below 1e-9 relative), FP64
-// through th^12 (the rest is below 1e-17 relative).
+// through th^12 (the rest is below 1e-17 relative).  Beyond th = 0.2 the FP32
+// truncation grows as th^6 / 5040 per step (8e-7 at 0.4, 5e-5 at 0.8) and the
+// step stops being unitary, so the Magnus policy only uses these polynomials on
+// tiles of steps whose bound on th stays within kSeriesLimit.
+constexpr double kSeriesLimit = 0.2;
+// Most halvings of th in the wide-range Magnus step (the scale 2^-2k stays a
+// normal number in both precisions); th up to kSeriesLimit 2^60 ~ 2e17.
+constexpr int kMaxHalvings = 60;
 template <typename T>
 struct TrigSeries;
 template <>
@@ -410,13 +417,21 @@ struct TrigSeries<double> {
 // ([a.sigma, b.sigma] = 2i (a x b).sigma).  With H = dt h_eff and th = |H|:
 // exp(-i H.sigma) = cos th - i (sin th / th) H.sigma; the increment
 // (cos th - 1) psi - i (sin th / th) H.sigma psi uses the even polynomials of
-// TrigSeries (th <= 0.2 on the grids used here).
-// Table entry: (dt Abar_x, dt Abar_y, D_x, D_y, C) with Abar = (A_0 + 4 A_h + A_1)/6,
+// TrigSeries where th <= kSeriesLimit, and their argument-halved form elsewhere.
+// Table entry: (dt Abar_x, dt Abar_y, D_x, D_y, C, th_max, 4^-k, k) with Abar = (A_0 + 4 A_h + A_1)/6,
 // D_x = dt^2/6 (A0x - A1x), D_y = dt^2/6 (A1y - A0y), C = dt^2/6 (A0x A1y - A0y A1x),
 // which makes dt h_eff for spin channel s:
 //     x = (dt p_x - dt Abar_x) - s eps D_y
 //     y = s (dt p_y - dt Abar_y) - eps D_x
 //     z = dt eps + s (D_y p_x + D_x p_y - C)
+// and th_max bounds |dt h_eff| over every mode of the grid and both channels:
+// with P_x = max |p_x|, P_y = max |p_y|, E = max eps over the grid,
+//     th_max^2 = (dt P_x + |dt Abar_x| + E |D_y|)^2 + (dt P_y + |dt Abar_y| + E |D_x|)^2
+//              + (dt E + |D_y| P_x + |D_x| P_y + |C|)^2.
+// A candidate with any th_max > kSeriesLimit takes the wide-range step (in a kernel
+// of its own) for all its steps; step n halves th k_n times, k_n the least k with th_max 2^-k <= kSeriesLimit
+// (0 where the bound is inside the range), the same for every mode, so the
+// threads of a warp never diverge.
 template <typename T, bool COMP>
 struct MagnusPolicy {
     struct alignas(sizeof(T) * 8) Entry {
@@ -424,18 +439,39 @@ struct MagnusPolicy {
     };
 
     __device__ static Entry make_entry6(double dt, double a0x, double a0y, double ahx, double ahy,
-                                        double a1x, double a1y)
+                                        double a1x, double a1y, const pp_grid &g)
     {
         Entry e;
         const double d6 = dt * dt / 6.0;
-        e.ax = (T)(dt * (a0x + 4.0 * ahx + a1x) / 6.0);
-        e.ay = (T)(dt * (a0y + 4.0 * ahy + a1y) / 6.0);
-        e.dx = (T)(d6 * (a0x - a1x));
-        e.dy = (T)(d6 * (a1y - a0y));
-        e.c = (T)(d6 * (a0x * a1y - a0y * a1x));
-        e.pad0 = e.pad1 = e.pad2 = (T)0;
+        const double ax = dt * (a0x + 4.0 * ahx + a1x) / 6.0;
+        const double ay = dt * (a0y + 4.0 * ahy + a1y) / 6.0;
+        const double dx = d6 * (a0x - a1x), dy = d6 * (a1y - a0y);
+        const double c = d6 * (a0x * a1y - a0y * a1x);
+        e.ax = (T)ax;
+        e.ay = (T)ay;
+        e.dx = (T)dx;
+        e.dy = (T)dy;
+        e.c = (T)c;
+        // bound on th = |dt h_eff| over the grid (see above)
+        const double Px = fmax(fabs(g.x0), fabs(g.x1)), Py = fmax(fabs(g.y0), fabs(g.y1));
+        const double Pz = fmax(fabs(g.z0), fabs(g.z1)), E = sqrt(1.0 + Pz * Pz);
+        const double bx = dt * Px + fabs(ax) + E * fabs(dy);
+        const double by = dt * Py + fabs(ay) + E * fabs(dx);
+        const double bz = dt * E + fabs(dy) * Px + fabs(dx) * Py + fabs(c);
+        double th = sqrt(bx * bx + by * by + bz * bz);
+        e.pad0 = (T)th;
+        int k = 0;
+        while (th > kSeriesLimit && k < kMaxHalvings) {
+            th *= 0.5;
+            ++k;
+        }
+        e.pad1 = (T)ldexp(1.0, -2 * k);
+        e.pad2 = (T)k;
         return e;
     }
+
+    // True if the step of this entry may leave the range of TrigSeries.
+    __device__ static __forceinline__ bool beyond_series(const Entry &e) { return e.pad0 > (T)kSeriesLimit; }
 
     struct State {
         T hi[2][4], lo[2][4];
@@ -460,7 +496,13 @@ struct MagnusPolicy {
         st.py = (T)py;
     }
 
-    __device__ static __forceinline__ void step(State &st, const Entry &e)
+    // WIDE = false: cos th - 1 and sin th / th from TrigSeries (th <= kSeriesLimit).
+    // WIDE = true: th is halved k = e.pad2 times (th^2 scaled by e.pad1 = 4^-k) into
+    // the series range, the series gives c = cos a - 1 and S = sin a / a there, and k
+    // double-angle steps restore th: sin 2a / 2a = S (1 + c) and
+    // cos 2a - 1 = 2 c (c + 2).  With k = 0 this is the series path exactly.
+    template <bool WIDE>
+    __device__ static __forceinline__ void step_impl(State &st, const Entry &e)
     {
         const T u = st.dtpx - e.ax, v = st.dtpy - e.ay;
         const T w = fma(e.dy, st.px, fma(e.dx, st.py, -e.c));
@@ -470,8 +512,20 @@ struct MagnusPolicy {
             const T Hy = s ? fma(-st.eps, e.dx, -v) : fma(-st.eps, e.dx, v);
             const T Hz = s ? st.dteps - w : st.dteps + w;
             const T t2 = fma(Hz, Hz, fma(Hy, Hy, Hx * Hx));
-            const T cm1 = TrigSeries<T>::cm1(t2);
-            const T sc = TrigSeries<T>::sinc(t2);
+            T cm1, sc;
+            if constexpr (WIDE) {
+                const T tr = t2 * e.pad1;
+                const int k = (int)e.pad2;
+                cm1 = TrigSeries<T>::cm1(tr);
+                sc = TrigSeries<T>::sinc(tr);
+                for (int i = 0; i < k; ++i) {
+                    sc = fma(sc, cm1, sc);
+                    cm1 = (T)2 * fma(cm1, cm1, (T)2 * cm1);
+                }
+            } else {
+                cm1 = TrigSeries<T>::cm1(t2);
+                sc = TrigSeries<T>::sinc(t2);
+            }
             const T gx = sc * Hx, gy = sc * Hy, gz = sc * Hz;
             const T *z = st.hi[s];
             if (COMP) {
@@ -500,6 +554,9 @@ struct MagnusPolicy {
             }
         }
     }
+
+    __device__ static __forceinline__ void step(State &st, const Entry &e) { step_impl<false>(st, e); }
+    __device__ static __forceinline__ void step_wide(State &st, const Entry &e) { step_impl<true>(st, e); }
 
     __device__ static void psi(const State &st, int s, double out[4], double, double, double,
                                double)
@@ -635,7 +692,8 @@ struct SplitPolicy {
 // split policy dt A_{n+1/2}.
 template <class P>
 __device__ __forceinline__ typename P::Entry table_entry(const P *, const double *Ax,
-                                                         const double *Ay, int n, double dt)
+                                                         const double *Ay, int n, double dt,
+                                                         const pp_grid &)
 {
     const double d3 = dt / 3.0, d6 = dt / 6.0;
     return P::make_entry(d3 * Ax[2 * n + 1], d3 * Ay[2 * n + 1], d6 * Ax[2 * n + 2],
@@ -643,14 +701,16 @@ __device__ __forceinline__ typename P::Entry table_entry(const P *, const double
 }
 template <typename T, bool C>
 __device__ __forceinline__ typename MagnusPolicy<T, C>::Entry
-table_entry(const MagnusPolicy<T, C> *, const double *Ax, const double *Ay, int n, double dt)
+table_entry(const MagnusPolicy<T, C> *, const double *Ax, const double *Ay, int n, double dt,
+            const pp_grid &g)
 {
     return MagnusPolicy<T, C>::make_entry6(dt, Ax[2 * n], Ay[2 * n], Ax[2 * n + 1], Ay[2 * n + 1],
-                                           Ax[2 * n + 2], Ay[2 * n + 2]);
+                                           Ax[2 * n + 2], Ay[2 * n + 2], g);
 }
 template <typename T, bool C>
 __device__ __forceinline__ typename SplitPolicy<T, C>::Entry
-table_entry(const SplitPolicy<T, C> *, const double *Ax, const double *Ay, int n, double dt)
+table_entry(const SplitPolicy<T, C> *, const double *Ax, const double *Ay, int n, double dt,
+            const pp_grid &)
 {
     return SplitPolicy<T, C>::make_entry2(dt, Ax[2 * n + 1], Ay[2 * n + 1]);
 }
@@ -677,24 +737,57 @@ struct UsesDtInit<SplitPolicy<T, C>> {
     static constexpr bool value = true;
 };
 
+// Policies whose step has a series range (beyond_series, step_wide).
+template <class P>
+struct HasSeriesGuard {
+    static constexpr bool value = false;
+};
+template <typename T, bool C>
+struct HasSeriesGuard<MagnusPolicy<T, C>> {
+    static constexpr bool value = true;
+};
+
+// Table of candidate c (grid (blocks, candidates), 256 threads).  For policies with
+// a series range, wide_flags[c] (zeroed before the launch) is set when any step of
+// the candidate leaves it; the propagation then runs that candidate in the
+// wide-range kernel instead.
 template <class P>
 __global__ void build_table_kernel(const double *__restrict__ A, int ld, int ns_uniform,
                                    const int *__restrict__ ns_array, int padded, double dt,
-                                   typename P::Entry *__restrict__ table)
+                                   pp_grid g, typename P::Entry *__restrict__ table,
+                                   int *__restrict__ wide_flags)
 {
     int c = blockIdx.y;
     int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= padded)
-        return;
     int ns = ns_array ? ns_array[c] : ns_uniform;
     const double *Ax = A + (size_t)c * 2 * ld, *Ay = Ax + ld;
-    typename P::Entry e;
-    if (n < ns) {
-        e = table_entry((const P *)nullptr, Ax, Ay, n, dt);
-    } else {
-        memset(&e, 0, sizeof e);
+    bool big = false;
+    if (n < padded) {
+        typename P::Entry e;
+        if (n < ns) {
+            e = table_entry((const P *)nullptr, Ax, Ay, n, dt, g);
+            if constexpr (HasSeriesGuard<P>::value)
+                big = P::beyond_series(e);
+        } else {
+            memset(&e, 0, sizeof e);
+        }
+        table[(size_t)c * padded + n] = e;
     }
-    table[(size_t)c * padded + n] = e;
+    if constexpr (HasSeriesGuard<P>::value) {
+        if (__syncthreads_or(big) && threadIdx.x == 0)
+            atomicOr(wide_flags + c, 1);
+    }
+}
+
+// The candidate's kernel: a policy with a series range runs each candidate in
+// exactly one of its two kernels (WIDE = wide_flags[c] != 0).
+template <class P, bool WIDE>
+__device__ __forceinline__ bool takes_candidate(const int *__restrict__ wide_flags, int c)
+{
+    if constexpr (HasSeriesGuard<P>::value)
+        return (wide_flags[c] != 0) == WIDE;
+    else
+        return !WIDE;
 }
 
 // One work item: the modes [blk * THREADS, (blk + 1) * THREADS) of candidate c.
@@ -710,7 +803,7 @@ struct ItemSmem {
     double red[THREADS / 32];
 };
 
-template <class P, int THREADS, int TILE_BYTES>
+template <class P, int THREADS, int TILE_BYTES, bool WIDE>
 __device__ __forceinline__ bool process_item(ItemSmem<P, THREADS, TILE_BYTES> &sm, int blk,
                                              const pp_grid &g, int ns,
                                              const typename P::Entry *__restrict__ trow,
@@ -781,9 +874,14 @@ __device__ __forceinline__ bool process_item(ItemSmem<P, THREADS, TILE_BYTES> &s
         const int nst = min(TILE, ns - t * TILE);
         if (active) {
             const V *tb = sm.buf[b];
+            if constexpr (WIDE) {
+                for (int kk = 0; kk < nst; ++kk)
+                    P::step_wide(st, tb[kk]);
+            } else {
 #pragma unroll 2
-            for (int kk = 0; kk < nst; ++kk)
-                P::step(st, tb[kk]);
+                for (int kk = 0; kk < nst; ++kk)
+                    P::step(st, tb[kk]);
+            }
         }
         __syncthreads();  // every thread is done with buf[b]
         if (tid == 0 && !skip_copies && t + 2 < ntiles) {

@@ -34,16 +34,21 @@
 
 namespace {
 
-template <class P, int THREADS, int TILE_BYTES>
+// WIDE = false: the candidates whose steps stay in the policy's series range (all
+// candidates for policies without one); WIDE = true: the others (see
+// build_table_kernel).  A CTA of the other kind returns at once.
+template <class P, int THREADS, int TILE_BYTES, bool WIDE>
 __global__ void __launch_bounds__(THREADS)
     propagate_kernel(const double *__restrict__ A, int ld, int ns_uniform,
                      const int *__restrict__ ns_array, const typename P::Entry *__restrict__ table,
                      int padded, double dt, pp_grid g, double *__restrict__ n_p,
                      double *__restrict__ partial, long long wait_limit, int skip_copies,
-                     unsigned int *__restrict__ status)
+                     unsigned int *__restrict__ status, const int *__restrict__ wide_flags)
 {
     __shared__ ItemSmem<P, THREADS, TILE_BYTES> sm;
     const int c = blockIdx.y;
+    if (!takes_candidate<P, WIDE>(wide_flags, c))
+        return;
     const int nmodes = g.nx * g.ny * g.nz;
     const int ngroups = (nmodes + kGroup - 1) / kGroup;
     const int ns = ns_array ? ns_array[c] : ns_uniform;
@@ -54,7 +59,7 @@ __global__ void __launch_bounds__(THREADS)
         mbar_fence_init();
     }
     __syncthreads();
-    process_item<P, THREADS, TILE_BYTES>(sm, blockIdx.x, g, ns, table + (size_t)c * padded, Ax,
+    process_item<P, THREADS, TILE_BYTES, WIDE>(sm, blockIdx.x, g, ns, table + (size_t)c * padded, Ax,
                                          Ax + ld, dt, n_p ? n_p + (size_t)c * nmodes : nullptr,
                                          partial + (size_t)c * ngroups, wait_limit, skip_copies,
                                          status, 0);
@@ -110,27 +115,36 @@ int run(const double *A, int ncand, int ld, const int32_t *ns_host, double dt, c
     int rc = pp::scratch(pp::SCR_TABLE, (size_t)ncand * padded * sizeof(V), &table);
     if (rc)
         return rc;
-    rc = pp::scratch(pp::SCR_PARTIAL, (size_t)ncand * ngroups * sizeof(double) + 256 * sizeof(int) +
-                                          (size_t)ncand * sizeof(int),
+    rc = pp::scratch(pp::SCR_PARTIAL, (size_t)ncand * ngroups * sizeof(double) + 512 * sizeof(int) +
+                                          2 * (size_t)ncand * sizeof(int),
                      &partial);
     if (rc)
         return rc;
+    // after the partial sums: the per-candidate wide flags, then (uneven) n_steps
+    int *flags = (int *)(((uintptr_t)((char *)partial + (size_t)ncand * ngroups * sizeof(double)) + 255) &
+                         ~(uintptr_t)255);
     const int *ns_array = nullptr;
     if (!uniform) {
-        nsdev = (char *)partial + (size_t)ncand * ngroups * sizeof(double);
-        nsdev = (void *)(((uintptr_t)nsdev + 255) & ~(uintptr_t)255);
+        nsdev = (void *)(((uintptr_t)(flags + ncand) + 255) & ~(uintptr_t)255);
         cudaError_t e = cudaMemcpyAsync(nsdev, ns_host, sizeof(int) * ncand, cudaMemcpyHostToDevice, stream);
         if (e != cudaSuccess)
             return pp::cuda_fail(e, "copy of n_steps");
         ns_array = (const int *)nsdev;
     }
+    cudaError_t ez = cudaMemsetAsync(flags, 0, sizeof(int) * ncand, stream);
+    if (ez != cudaSuccess)
+        return pp::cuda_fail(ez, "wide-flag reset");
     dim3 tg((padded + 255) / 256, ncand);
-    build_table_kernel<P><<<tg, 256, 0, stream>>>(A, ld, ns0, ns_array, padded, dt, (V *)table);
+    build_table_kernel<P><<<tg, 256, 0, stream>>>(A, ld, ns0, ns_array, padded, dt, *grid, (V *)table, flags);
     dim3 pg(nblk, ncand);
     pp::profile_mark_start(stream);
-    propagate_kernel<P, THREADS, TILE_BYTES><<<pg, THREADS, 0, stream>>>(A, ld, ns0, ns_array, (const V *)table,
-                                                             padded, dt, *grid, n_p, (double *)partial,
-                                                             (long long)pp::wait_limit(), pp::skip_copies(), status);
+    propagate_kernel<P, THREADS, TILE_BYTES, false><<<pg, THREADS, 0, stream>>>(
+        A, ld, ns0, ns_array, (const V *)table, padded, dt, *grid, n_p, (double *)partial,
+        (long long)pp::wait_limit(), pp::skip_copies(), status, flags);
+    if constexpr (HasSeriesGuard<P>::value)
+        propagate_kernel<P, THREADS, TILE_BYTES, true><<<pg, THREADS, 0, stream>>>(
+            A, ld, ns0, ns_array, (const V *)table, padded, dt, *grid, n_p, (double *)partial,
+            (long long)pp::wait_limit(), pp::skip_copies(), status, flags);
     pp::profile_mark_stop(stream);
     finalize_kernel<<<ncand, 256, 0, stream>>>((const double *)partial, ngroups, N, status);
     cudaError_t e = cudaGetLastError();
@@ -142,9 +156,10 @@ int run(const double *A, int ncand, int ld, const int32_t *ns_host, double dt, c
 // ---------------------------------------------------------------- no-allocation variant
 // Scratch of pp_pair_number_static: a fixed device array in this file, held by
 // every GPU that loads the library until the process exits.  It holds, in
-// order, the per-step table, the per-block partial sums and (for uneven step
-// counts) a copy of n_steps; each call writes every byte it later reads, so
-// nothing needs clearing, and calls that overlap on the GPU race on it.
+// order, the per-step table, the per-block partial sums, the per-candidate
+// wide-range flags (cleared by each call before use) and (for uneven step
+// counts) a copy of n_steps; each call writes every byte it later reads, and
+// calls that overlap on the GPU race on it.
 constexpr size_t kStaticScratchBytes = (size_t)16 << 20;
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
@@ -190,8 +205,9 @@ int run_static(const double *A, int ncand, int ld, const int32_t *ns_host, doubl
     const int ngroups = (nmodes + kGroup - 1) / kGroup;
     const size_t table_bytes = align256((size_t)ncand * padded * sizeof(V));
     const size_t part_bytes = align256((size_t)ncand * ngroups * sizeof(double));
+    const size_t flag_bytes = align256((size_t)ncand * sizeof(int));
     const size_t ns_bytes = uniform ? 0 : align256((size_t)ncand * sizeof(int));
-    const size_t need = table_bytes + part_bytes + ns_bytes;
+    const size_t need = table_bytes + part_bytes + flag_bytes + ns_bytes;
     if (need > kStaticScratchBytes)
         return pp::fail(PP_ERR_INVALID_ARG,
                         "this call needs %zu bytes of scratch; the static scratch holds %zu "
@@ -205,20 +221,28 @@ int run_static(const double *A, int ncand, int ld, const int32_t *ns_host, doubl
         return pp::fail(PP_ERR_CUDA, "status word unavailable");
     V *table = (V *)base;
     double *partial = (double *)(base + table_bytes);
+    int *flags = (int *)(base + table_bytes + part_bytes);
     const int *ns_array = nullptr;
     if (!uniform) {
-        int *nsdev = (int *)(base + table_bytes + part_bytes);
+        int *nsdev = (int *)(base + table_bytes + part_bytes + flag_bytes);
         cudaError_t e = cudaMemcpyAsync(nsdev, ns_host, sizeof(int) * ncand, cudaMemcpyHostToDevice, stream);
         if (e != cudaSuccess)
             return pp::cuda_fail(e, "copy of n_steps");
         ns_array = nsdev;
     }
+    cudaError_t ez = cudaMemsetAsync(flags, 0, sizeof(int) * ncand, stream);
+    if (ez != cudaSuccess)
+        return pp::cuda_fail(ez, "wide-flag reset");
     dim3 tg((padded + 255) / 256, ncand);
-    build_table_kernel<P><<<tg, 256, 0, stream>>>(A, ld, ns0, ns_array, padded, dt, table);
+    build_table_kernel<P><<<tg, 256, 0, stream>>>(A, ld, ns0, ns_array, padded, dt, *grid, table, flags);
     dim3 pg(nblk, ncand);
-    propagate_kernel<P, THREADS, TILE_BYTES><<<pg, THREADS, 0, stream>>>(A, ld, ns0, ns_array, table, padded, dt, *grid,
-                                                     n_p, partial, (long long)pp::wait_limit(),
-                                                     pp::skip_copies(), status);
+    propagate_kernel<P, THREADS, TILE_BYTES, false><<<pg, THREADS, 0, stream>>>(
+        A, ld, ns0, ns_array, table, padded, dt, *grid, n_p, partial, (long long)pp::wait_limit(),
+        pp::skip_copies(), status, flags);
+    if constexpr (HasSeriesGuard<P>::value)
+        propagate_kernel<P, THREADS, TILE_BYTES, true><<<pg, THREADS, 0, stream>>>(
+            A, ld, ns0, ns_array, table, padded, dt, *grid, n_p, partial, (long long)pp::wait_limit(),
+            pp::skip_copies(), status, flags);
     finalize_kernel<<<ncand, 256, 0, stream>>>(partial, ngroups, N, status);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)

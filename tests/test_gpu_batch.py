@@ -99,6 +99,39 @@ def test_batch_pair_number_matches_oracle_and_uniform_path(pp, precision, scheme
     b.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32fast"])
+def test_batch_magnus_beyond_the_series_range(pp, precision):
+    # a step large enough that th = |dt h_eff| exceeds the Magnus polynomials' range
+    # (0.2) on every slot: the batch builds each slot's step bound from its own grid,
+    # takes the argument-halved step and still equals the uniform path bit for bit
+    # (and the oracle twin in FP64)
+    dt, steps = 0.3, [100, 140, 90, 120]
+    sp = [dict(K=K, order=ORDER, w_min=0.0, w_max=2.0, T=n * dt, fluence=2.0, n_steps=n) for n in steps]
+    gr = [inputs.small_grid(6, 5, 3, ext=1.5), inputs.small_grid(4, 4, 2, ext=2.0),
+          inputs.small_grid(5, 3, 2, ext=1.0), inputs.small_grid(3, 4, 2, ext=1.7)]
+    params = inputs.random_population(len(steps), K, seed=53)
+    b = pp.Batch(sp, gr, dt, precision=precision, scheme="magnus4")
+    A = b.synth(torch.tensor(params, device=DEV))
+    N, _ = b.pair_number(A)
+    assert pp.sync_status() == pp.PP_OK
+    for c, (ns, g) in enumerate(zip(steps, gr)):
+        Nu, _ = pp.pair_number(A[c:c + 1, :, :2 * ns + 1].contiguous(), dt, g, precision=precision,
+                               scheme="magnus4")
+        assert torch.equal(N[c:c + 1], Nu)
+        if precision == "fp64":
+            Ao = A[c, :, :2 * ns + 1].cpu().numpy()
+            fo = oracle.dirac_magnus_modes(Ao, ns, dt, inputs.grid_points(g))[0]
+            x, y, z = inputs.grid_axes(g)
+
+            def tw(a, mirror):
+                w = np.full(a.size, a[1] - a[0])
+                w[[0, -1]] /= 2
+                return w * (2 if mirror else 1)
+            W = (tw(z, g["mirror_z"])[:, None, None] * tw(y, 0)[None, :, None] * tw(x, 0)[None, None, :])
+            assert abs(N[c].item() / float(np.sum(W.ravel() * fo)) - 1) < 1e-9
+    b.close()
+
+
 def test_batch_tuner_keeps_results_bitwise(pp):
     params = inputs.random_population(len(STEPS), K, seed=47)
     b = pp.Batch(specs(), grids(), DT, precision="fp32fast", scheme="magnus4")

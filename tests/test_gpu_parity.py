@@ -408,6 +408,51 @@ def test_magnus_fp32_at_full_de_batch_size(pp):
     assert n_excess(n_m64[0].cpu().numpy().ravel()[idx], no, cfg["n_steps"]) <= 1.0
 
 
+def magnus_theta_bound(A, dt, grid):
+    """Largest per-step bound on th = |dt h_eff| over the grid, as pp.h defines it for
+    PP_MAGNUS4 (restated here from that definition, in FP64)."""
+    Px, Py = max(abs(grid["x0"]), abs(grid["x1"])), max(abs(grid["y0"]), abs(grid["y1"]))
+    Em = math.sqrt(1 + max(grid["z0"] ** 2, grid["z1"] ** 2))
+    a0x, ahx, a1x = A[0, 0:-1:2], A[0, 1::2], A[0, 2::2]
+    a0y, ahy, a1y = A[1, 0:-1:2], A[1, 1::2], A[1, 2::2]
+    ax, ay = dt * (a0x + 4 * ahx + a1x) / 6, dt * (a0y + 4 * ahy + a1y) / 6
+    d6 = dt * dt / 6
+    dx, dy, c = d6 * (a0x - a1x), d6 * (a1y - a0y), d6 * (a0x * a1y - a0y * a1x)
+    bx = dt * Px + np.abs(ax) + Em * np.abs(dy)
+    by = dt * Py + np.abs(ay) + Em * np.abs(dx)
+    bz = dt * Em + np.abs(dy) * Px + np.abs(dx) * Py + np.abs(c)
+    return float(np.sqrt(bx ** 2 + by ** 2 + bz ** 2).max())
+
+
+@pytest.mark.parametrize("target", [0.19, 0.4, 0.8])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32fast"])
+def test_magnus_beyond_the_series_range(pp, target, precision):
+    # Sec. V.C.2 (a unitary fourth-order step): the Magnus step must stay exact when
+    # th = |dt h_eff| leaves the range of its polynomials (th <= 0.2).  At 0.19 every
+    # tile uses the polynomials; at 0.4 and 0.8 the argument-halved form.  Against the
+    # oracle twin, which exponentiates the 4x4 Omega by its full Taylor series.
+    grid = inputs.small_grid(6, 5, 3, ext=1.3)
+    dt = 0.05
+    for _ in range(3):  # scale dt until the bound hits the target
+        ns = int(round(24.0 / dt))
+        A, _, _ = oracle.gaussian_rotating_field(0.3, 0.9, 3.0, -0.5 * ns * dt, dt / 2, 2 * ns + 1)
+        dt *= target / magnus_theta_bound(A, dt, grid)
+    ns = int(round(24.0 / dt))
+    A, _, _ = oracle.gaussian_rotating_field(0.3, 0.9, 3.0, -0.5 * ns * dt, dt / 2, 2 * ns + 1)
+    assert abs(magnus_theta_bound(A, dt, grid) - target) < 0.01
+    no = oracle.dirac_magnus_modes(A, ns, dt, inputs.grid_points(grid))[0]
+    No = weighted_N(grid, no)
+    N, n = pp.pair_number(torch.tensor(A[None], device=DEV), dt, grid, precision=precision,
+                          want_n=True, scheme="magnus4")
+    assert pp.sync_status() == pp.PP_OK
+    N, n = N.cpu().numpy(), n.cpu().numpy()
+    if precision == "fp64":
+        assert abs(N[0] / No - 1) < 1e-9
+        assert n_excess(n, no, ns) <= 1.0
+    else:
+        assert abs(N[0] / No - 1) < 1e-4
+
+
 @pytest.mark.parametrize("precision,scheme", [("fp32", "magnus4"), ("fp32fast", "magnus4"),
                                               ("fp32", "rk4"), ("fp32fast", "split2"),
                                               ("fp64", "rk4")])
