@@ -74,16 +74,30 @@ def held_out_error(pp, net, lt, P, N, lo, hi):
             "n": int(X.shape[0])}
 
 
+def mean_loss(pp, net, X, t):
+    """The network's mean squared error on rows X, t (pp_mlp_loss_grad over slices of
+    at most max_batch rows, weighted by slice length)."""
+    tot = 0.0
+    for b in range(0, X.shape[0], net.max_batch):
+        loss, _ = net.loss_grad(X[b:b + net.max_batch].contiguous(), t[b:b + net.max_batch].contiguous())
+        tot += loss.item() * min(net.max_batch, X.shape[0] - b)
+    return tot / X.shape[0]
+
+
 def run_de(pp, pop0, fit0, spec, grid, generations, seed, F, CR, net=None, R=8, lt=None,
-           online=None, precision="fp32fast", scheme="magnus4", target=None, mode="individual"):
+           online=None, precision="fp32fast", scheme="magnus4", target=None, mode="individual",
+           seen=None):
     """`generations` DE generations from (pop0, fit0); plain DE when net is None.
 
     online = (every, epochs, batch, lr) refits the network on all trials the
-    exact solver scored so far every `every` generations; mode is the screening
-    mode of pp_de_screened_step ("individual" or "global").  Stops early once the
-    best N reaches `target` (if given).  Returns the best N after the initial
-    population and after every generation, the exact-evaluation count at each
-    of those points, and the wall-clock seconds (device-synchronised).
+    exact solver scored so far (plus `seen` = (features, N) scored before the run,
+    if given) every `every` generations; mode is the screening mode of
+    pp_de_screened_step ("individual" or "global").  Stops early once the best N
+    reaches `target` (if given).  Returns the best N after the initial population
+    and after every generation, the exact-evaluation count at each of those
+    points, the wall-clock seconds (device-synchronised), the final population
+    and fitness, and per refit (generation, rows, mean loss on those rows before
+    and after, seconds).
     """
     import torch
     lo, hi, per = (torch.tensor(x, device=pop0.device) for x in inputs.param_bounds(spec["K"]))
@@ -91,7 +105,8 @@ def run_de(pp, pop0, fit0, spec, grid, generations, seed, F, CR, net=None, R=8, 
     NP, D = pop.shape
     trial = torch.empty_like(pop)
     tfit = torch.empty_like(fit)
-    seen_P, seen_N = [], []
+    seen_P, seen_N = ([seen[0]], [seen[1]]) if seen is not None else ([], [])
+    refits = []
     best = [fit.max().item()]
     calls = [NP]
     torch.cuda.synchronize()
@@ -113,13 +128,22 @@ def run_de(pp, pop0, fit0, spec, grid, generations, seed, F, CR, net=None, R=8, 
                     t = lt.targets(pp, torch.cat(seen_N))
                     perm = torch.randperm(X.shape[0], device=X.device,
                                           generator=torch.Generator(device=X.device).manual_seed(g))
-                    net.fit(X[perm].contiguous(), t[perm].contiguous(), batch, epochs, lr, lr)
+                    X, t = X[perm].contiguous(), t[perm].contiguous()
+                    before = mean_loss(pp, net, X, t)
+                    torch.cuda.synchronize()
+                    t_fit = time.perf_counter()
+                    net.fit(X, t, batch, epochs, lr, lr)
+                    torch.cuda.synchronize()
+                    t_fit = time.perf_counter() - t_fit
+                    refits.append({"generation": g, "rows": int(X.shape[0]), "loss_before": before,
+                                   "loss_after": mean_loss(pp, net, X, t), "seconds": t_fit})
         best.append(fit.max().item())
         calls.append(calls[-1] + NP)
         if target is not None and best[-1] >= target:
             break
     torch.cuda.synchronize()
-    return {"best": best, "calls": calls, "seconds": time.perf_counter() - t0}
+    return {"best": best, "calls": calls, "seconds": time.perf_counter() - t0, "pop": pop, "fit": fit,
+            "refits": refits}
 
 
 def calls_to_reach(run, target):

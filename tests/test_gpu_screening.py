@@ -225,3 +225,36 @@ def test_trained_network_saves_exact_calls(pp, mode):
     assert pp.sync_status() == pp.PP_OK
     assert min(gains) >= 2.0, (gains, held)
     net.close()
+
+
+def test_online_refit_fires_lowers_the_loss_and_selection_stays_exact(pp):
+    """The online refit of the large-scale configuration ("retrained every 20
+    generations on newly scored pulses") at a small size: a network fitted on the
+    initial population's 64 exact evaluations screens 10 generations (R = 8) and is
+    refitted every 5 on every pulse scored so far.  The refit runs twice, each time
+    on more rows, and lowers the network's loss on them; the network's parameters
+    change; and the final fitness is the exact pair number of the final population,
+    bit for bit, so selection never saw a prediction."""
+    from paper_1704_08919_gb300 import screening as scr
+    lo, hi, per = bounds()
+    P0, N0, _ = scr.score_random(pp, 64, SPEC, GRID, 21)
+    lt = scr.LogTarget(N0)
+    net = pp.Surrogate(32, 256, max_batch=512)
+    net.init(3)
+    X0 = pp.mlp_features(P0, lo, hi)
+    net.fit(X0, lt.targets(pp, N0), 32, 100, 2e-3, 5e-5)
+    w0 = net.get_params().clone()
+    pop0, fit0 = start(pp, 16, 7)
+    r = scr.run_de(pp, pop0, fit0, SPEC, GRID, 10, 31, 0.8, 0.9, net=net, R=8, lt=lt,
+                   online=(5, 8, 32, 2e-4), seen=(X0, N0))
+    assert [x["generation"] for x in r["refits"]] == [4, 9]
+    assert r["refits"][0]["rows"] == 64 + 5 * 16 and r["refits"][1]["rows"] == 64 + 10 * 16
+    for x in r["refits"]:
+        assert x["loss_after"] < x["loss_before"], r["refits"]
+    assert not torch.equal(net.get_params(), w0)
+    A, _, _ = pp.synth_field(r["pop"], SPEC)
+    N, _ = pp.pair_number(A, SPEC["T"] / SPEC["n_steps"], GRID, precision="fp32fast", scheme="magnus4")
+    assert pp.sync_status() == pp.PP_OK
+    assert torch.equal(N, r["fit"])
+    assert r["best"][-1] >= r["best"][0] and r["calls"][-1] == 16 * 11
+    net.close()
