@@ -28,7 +28,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-from paper_1704_08919_gb300 import inputs  # noqa: E402
+from paper_1704_08919_gb300 import inputs, shard  # noqa: E402
 
 CFG = inputs.DE_BATCH
 # Arithmetic of one mode-step (one momentum mode, both spin channels, one
@@ -44,8 +44,10 @@ WORK = {("fp32", "rk4"): (268, 184), ("fp32", "magnus4"): (138, 96), ("fp32", "s
 # DRAM bytes per candidate per launch of the propagation kernel, from ncu captures
 # (profiles/): the FP32-fast Magnus kernel (256 threads, 8 KiB tiles) read 1.088512 MB for 4 candidates.
 TRAFFIC_PER_CAND = {("fp32fast", "magnus4"): 1.088512e6 / 4}
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
+# GB300 FP64 rate from the part's datasheet figure (no measured FP64 peak exists
+# for this pool); FP32 is derived from the device's SM count and maximum clock.
+FP64_NOMINAL_TFLOPS = 1.25
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -82,7 +84,45 @@ def parse():
                     help="surrogate: also run a screened DE refitted every N generations (0: off)")
     ap.add_argument("--ncand", type=int, default=CFG["NP"],
                     help="population size (smaller values only for profiling runs)")
+    ap.add_argument("--branch", type=int, default=0,
+                    help="large: generations run with and without the scheduled refit after --steps")
+    ap.add_argument("--refit-epochs", type=int, default=20, help="large: epochs of the scheduled refit")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="de-batch: skip the sub-records of the other configurations (single-field "
+                         "FP64 solve, FP64 DE generation, uneven batch)")
+    ap.add_argument("--no-oracle-n", action="store_true",
+                    help="de-batch: skip the oracle's full-grid N of one candidate")
     return ap.parse_args()
+
+
+def device_peaks(local):
+    """ALU peaks of this GPU for the roofline: FP32 = SMs (read from the device) x 128
+    lanes x 2 flop x the maximum SM clock (nvidia-smi clocks.max.sm, else the clock
+    recorded in MEASURED_PEAKS.json); FP64 = the nominal datasheet figure.  Neither
+    is a measured peak: MEASURED_PEAKS.json holds HBM and BF16 figures only."""
+    import torch
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    clk, src = None, None
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(local), "--query-gpu=clocks.max.sm",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                             timeout=20).stdout.strip()
+        clk, src = float(out.splitlines()[0]), "nvidia-smi clocks.max.sm"
+    except (OSError, ValueError, IndexError, subprocess.TimeoutExpired):
+        pass
+    if clk is None:
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                clk, src = float(json.load(f)["sm_max_mhz"]), "MEASURED_PEAKS.json sm_max_mhz"
+        except (OSError, KeyError, ValueError):
+            clk, src = 2070.0, "GB300 maximum SM clock (datasheet)"
+    fp32 = sms * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12
+    return {"sm_count": sms, "sm_max_mhz": clk, "fp32_tflops": fp32, "fp64_tflops": FP64_NOMINAL_TFLOPS,
+            "fp32_lanes_per_s": sms * FP32_LANES_PER_SM * clk * 1e6,
+            "fp32_source": "nominal, derived: %d SMs (device) x %d FP32 lanes x 2 flop x %g MHz (%s)"
+                           % (sms, FP32_LANES_PER_SM, clk, src),
+            "fp64_source": "nominal: GB300 FP64 %.2f TFLOP/s datasheet figure (no measured FP64 peak)"
+                           % FP64_NOMINAL_TFLOPS}
 
 
 def dist_env():
@@ -220,7 +260,12 @@ def reference_main(args):
     line = {
         "metric": "candidate pulses scored/s (DE batch, rel. N err <= 1e-4 vs FP64 oracle)",
         "value": cand_per_s, "unit": "candidates/s", "n_gpus": args.gpus, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1000.0 * CFG["NP"] / cand_per_s,
+        "warmup": args.warmup,
+        # each step is the bounded sample: its mean wall time, not a whole generation's
+        "ms_per_step": 1000.0 * sum(times) / args.steps,
+        "ms_per_generation_extrapolated": 1000.0 * CFG["NP"] / cand_per_s,
+        "units_per_step": "%d of the %d mode x step units of one candidate" % (
+            nm * CFG["n_steps"], units_per_candidate()),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded B-spline pulses)",
         # the same workload as the library arm; this arm computes it in FP64 RK4 (the oracle)
@@ -239,45 +284,36 @@ def reference_main(args):
 # ----------------------------------------------------------------------------- uneven batch
 
 
-def uneven_main(args):
-    """128 slots of uneven length and grid; each timed step is one DE generation, all
-    K timed generations in one CUDA graph launch (pp_batch_de_run)."""
-    import torch
-    import paper_1704_08919_gb300 as pp
+def measure_uneven(pp, torch, local, peaks, G, precision="fp32fast", scheme="magnus4", tune=True,
+                   pop_seed=1, seed=1000, dist=None):
+    """The uneven batch: 128 slots of uneven length and grid; G DE generations as one
+    CUDA graph launch (pp_batch_de_run), timed with CUDA events after a capture and
+    warm-up launch of the same graph.  Returns (record, total_ms)."""
     U = inputs.UNEVEN_BATCH
-    ws, rank, local = dist_env()
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    dist = None
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
-    pp.lib()
     stream = torch.cuda.current_stream()
-    pop_seed, seed = rank_seeds(rank)
     steps = inputs.uneven_steps(U, pop_seed)
     specs = inputs.uneven_specs(U, steps)
     pop = torch.tensor(inputs.random_population(U["NP"], U["K"], seed=pop_seed), device=dev)
-    peaks = []
+    peaks_E = []
     for c, sp in enumerate(specs):
         _, E, _ = pp.synth_field(pop[c:c + 1].contiguous(), sp, want_E=True)
-        peaks.append(torch.sqrt(E[0, 0] ** 2 + E[0, 1] ** 2).max().item())
-    grids = inputs.grids_by_rank(U, peaks)
-    b = pp.Batch(specs, grids, U["dt"], precision=args.precision, scheme=args.scheme)
+        peaks_E.append(torch.sqrt(E[0, 0] ** 2 + E[0, 1] ** 2).max().item())
+    grids = inputs.grids_by_rank(U, peaks_E)
+    b = pp.Batch(specs, grids, U["dt"], precision=precision, scheme=scheme)
     lo, hi, per = inputs.param_bounds(U["K"])
     lo_t, hi_t, per_t = (torch.tensor(x, device=dev) for x in (lo, hi, per))
     A = b.synth(pop)
     tuned = None
-    if not args.no_tune:
+    if tune:
         chosen, cfg_ms = b.tune(A)
         tuned = {"chosen": pp.launch_configs()[chosen], "ms": [round(x, 2) for x in cfg_ms]}
     fit, _ = b.pair_number(A)
     b.set_generation(0)
-    G = args.steps
     b.de_run(pop, fit, lo_t, hi_t, per_t, U["F"], U["CR"], seed, G)  # capture + warm-up
     torch.cuda.synchronize()
     if pp.sync_status() != pp.PP_OK:
-        raise RuntimeError("warm-up failed")
+        raise RuntimeError("uneven batch: warm-up failed")
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if dist is not None:
         dist.barrier()
@@ -290,7 +326,7 @@ def uneven_main(args):
     torch.cuda.synchronize()
     clk = clocks.stop()
     if pp.sync_status() != pp.PP_OK:
-        raise RuntimeError("device status after the timed region")
+        raise RuntimeError("uneven batch: device status after the timed region")
     total_ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
     modes = np.array([g["nx"] * g["ny"] * g["nz"] for g in grids], dtype=np.float64)
     mode_steps = float(np.sum(modes * steps)) * G
@@ -298,33 +334,71 @@ def uneven_main(args):
     idx = list(range(4))
     sub_specs = [specs[i] for i in idx]
     sub_grids = [grids[i] for i in idx]
-    bf = pp.Batch(sub_specs, sub_grids, U["dt"], precision=args.precision, scheme=args.scheme)
+    bf = pp.Batch(sub_specs, sub_grids, U["dt"], precision=precision, scheme=scheme)
     b64 = pp.Batch(sub_specs, sub_grids, U["dt"], precision="fp64", scheme="rk4")
     As = bf.synth(pop[idx].contiguous())
     Nf, _ = bf.pair_number(As)
     N64, _ = b64.pair_number(As)
     pp.sync_status()
     rel_err = (Nf / N64 - 1).abs().max().item()
+    for x in (bf, b64, b):
+        x.close()
     if rel_err > 1e-4:
-        raise RuntimeError("N error %.3e vs FP64 RK4 exceeds 1e-4" % rel_err)
+        raise RuntimeError("uneven batch: N error %.3e vs FP64 RK4 exceeds 1e-4" % rel_err)
+    flop, inst = WORK[(precision, scheme)]
+    fp32 = precision != "fp64"
+    pk = peaks["fp32_tflops"] if fp32 else peaks["fp64_tflops"]
+    achieved = flop * mode_steps / (total_ms * 1e-3) / 1e12
+    rec = {"workload": U["name"], "NP": U["NP"], "precision": precision, "scheme": scheme,
+           "generations": G, "ms_per_generation": total_ms / G,
+           "candidates_per_s": U["NP"] * G / (total_ms * 1e-3),
+           "mode_steps_per_s": mode_steps / (total_ms * 1e-3),
+           "steps_per_slot": [int(steps.min()), int(steps.max())],
+           "modes_per_slot": [int(modes.min()), int(modes.max())],
+           "graph": "%d generations per CUDA graph launch" % G,
+           "l2": "not flushed between generations inside the graph (ALU-bound kernel)",
+           "n_rel_err_vs_fp64_rk4_max": rel_err, "launch_tuning": tuned, "clocks": clk,
+           "roofline": {"bound": "alu", "kernel": "propagate_batch_kernel<%s>" % scheme,
+                        "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
+                        "peak_source": peaks["fp32_source"] if fp32 else peaks["fp64_source"],
+                        "flop_per_mode_step": flop,
+                        "note": "whole graph timed (proposal, synthesis, tables, propagation, selection)"},
+           "gpu_launches": 8 * G}
+    return rec, total_ms
+
+
+def uneven_main(args):
+    """--workload uneven: the uneven batch as its own JSON line; every rank runs its
+    own population (weak scaling)."""
+    import torch
+    import paper_1704_08919_gb300 as pp
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    pp.lib()
+    pop_seed, seed = rank_seeds(rank)
+    G = args.steps
+    rec, total_ms = measure_uneven(pp, torch, local, device_peaks(local), G, args.precision, args.scheme,
+                                   not args.no_tune, pop_seed, seed, dist)
     if rank == 0:
-        cand = throughput(ws, U["NP"], G, total_ms)
+        U = inputs.UNEVEN_BATCH
         print(json.dumps({
             "metric": "candidate pulses scored/s (uneven batch, rel. N err <= 1e-4 vs FP64 oracle)",
-            "value": cand, "unit": "candidates/s", "n_gpus": ws, "steps": G, "warmup": G,
-            "ms_per_step": total_ms / G, "higher_is_better": True, "scaling": "weak",
+            "value": throughput(ws, U["NP"], G, total_ms), "unit": "candidates/s", "n_gpus": ws, "steps": G,
+            "warmup": G, "ms_per_step": total_ms / G, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
             "scheme": args.scheme, "data": "synthetic (seeded B-spline pulses, uniform in bounds)",
             "config": {"workload": U["name"], "NP": U["NP"], "precision": args.precision,
-                       "steps_per_slot": [int(steps.min()), int(steps.max())],
-                       "modes_per_slot": [int(modes.min()), int(modes.max())],
-                       "graph": "%d generations per CUDA graph launch" % G,
-                       "l2": "not flushed between generations inside the graph (ALU-bound kernel)"},
-            "mode_steps_per_s": ws * mode_steps / (total_ms / 1000.0),
-            "n_rel_err_vs_fp64_rk4_max": rel_err, "launch_tuning": tuned, "clocks": clk,
-            "gpu_launches": 8 * G}), flush=True)
-    for x in (bf, b64, b):
-        x.close()
+                       "steps_per_slot": rec["steps_per_slot"], "modes_per_slot": rec["modes_per_slot"],
+                       "graph": rec["graph"], "l2": rec["l2"]},
+            "mode_steps_per_s": ws * rec["mode_steps_per_s"],
+            "n_rel_err_vs_fp64_rk4_max": rec["n_rel_err_vs_fp64_rk4_max"], "launch_tuning": rec["launch_tuning"],
+            "roofline": rec["roofline"], "clocks": rec["clocks"], "gpu_launches": rec["gpu_launches"]}),
+            flush=True)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
@@ -454,8 +528,9 @@ def localsearch_main(args):
     if pp.sync_status() != pp.PP_OK:
         raise RuntimeError("device status after the local search")
     J0 = J0.cpu().numpy()
+    pk = device_peaks(local)
     achieved = QKE_ADJ_FLOP * mode_steps / (eval_ms * 1e-3) / 1e12
-    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
+    peak = pk["fp32_tflops"]
     print(json.dumps({
         "metric": "local-search gradient evaluations/s (QKE forward + adjoint, all starts batched)",
         "value": S / (eval_ms * 1e-3), "unit": "gradients/s", "n_gpus": 1, "steps": reps,
@@ -469,10 +544,10 @@ def localsearch_main(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
                      "pipe_frac": QKE_ADJ_FP32_INSTR * mode_steps / (eval_ms * 1e-3)
-                     / (SM_COUNT * FP32_LANES_PER_SM * 2070e6),
+                     / pk["fp32_lanes_per_s"],
+                     "peak_source": pk["fp32_source"],
                      "note": "%d FP32 flop (%d instructions) per mode-step from ncu SASS counts; "
-                             "whole evaluation (synthesis, adjoint, chain rule) timed; "
-                             "peak = 152 SMs x 128 lanes x 2 flop x 2070 MHz"
+                             "whole evaluation (synthesis, adjoint, chain rule) timed"
                              % (QKE_ADJ_FLOP, QKE_ADJ_FP32_INSTR)},
         "search": None if r is None else {
             "seconds": wall, "evals_total": int(r["evals"].sum()),
@@ -486,10 +561,13 @@ def localsearch_main(args):
 
 def large_main(args):
     """The large-scale configuration: population 1024, K = 16, T = 400 (20000 steps),
-    grid 128 x 128 x 64, surrogate-screened DE.  Scores the initial population, fits
-    the network on those exact evaluations (the refit that would recur every 20
-    generations), runs --steps full generations (default 2) and extrapolates the
-    wall-clock of the configured 200 generations."""
+    grid 128 x 128 x 64, surrogate-screened DE (R = 8).  Scores the initial
+    population and fits the network on those exact evaluations, then runs --steps
+    generations (default 2).  With --branch B and --steps equal to the refit period
+    (20), the run reaches the first scheduled refit and continues B generations two
+    ways from the same state: with the network refitted on every pulse scored so far,
+    and without.  The wall-clock of the configured 200 generations is extrapolated
+    from the measured generation and refit times."""
     import torch
     import paper_1704_08919_gb300 as pp
     from paper_1704_08919_gb300 import screening as scr
@@ -528,18 +606,54 @@ def large_main(args):
     net.fit(X, t, 256, 200, 2e-3, 5e-5)
     torch.cuda.synchronize()
     fit_s = time.perf_counter() - t0
+    seen_X, seen_N = [X], [fit.clone()]
     trial = torch.empty_like(pop)
     tfit = torch.empty_like(fit)
-    best = [fit.max().item()]
-    gen_ms = []
-    for g in range(G):
-        e0.record(st)
-        pp.de_screened_step(pop, fit, spec, grid, lo, hi, per, Lg["F"], Lg["CR"], Lg["de_seed"], g, R, net,
-                            precision=prec, scheme=sch, trial_out=trial, trial_fit_out=tfit)
-        e1.record(st)
+
+    def generations(net_g, pop_g, fit_g, g0, count, log):
+        best, ms = [fit_g.max().item()], []
+        for g in range(g0, g0 + count):
+            e0.record(st)
+            pp.de_screened_step(pop_g, fit_g, spec, grid, lo, hi, per, Lg["F"], Lg["CR"], Lg["de_seed"], g, R,
+                                net_g, precision=prec, scheme=sch, trial_out=trial, trial_fit_out=tfit)
+            e1.record(st)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            best.append(fit_g.max().item())
+            if log:
+                seen_X.append(pp.mlp_features(trial, lo, hi))
+                seen_N.append(tfit.clone())
+        return best, ms
+
+    best, gen_ms = generations(net, pop, fit, 0, G, True)
+    branch = None
+    if args.branch > 0:
+        # the first scheduled refit, then both continuations from the same state
+        snap_pop, snap_fit, snap_w = pop.clone(), fit.clone(), net.get_params().clone()
+        Xs = torch.cat(seen_X)
+        ts = lt.targets(pp, torch.cat(seen_N))
+        perm = torch.randperm(Xs.shape[0], device="cuda", generator=torch.Generator(device="cuda").manual_seed(G))
+        Xs, ts = Xs[perm].contiguous(), ts[perm].contiguous()
+        loss_before = scr.mean_loss(pp, net, Xs, ts)
         torch.cuda.synchronize()
-        gen_ms.append(e0.elapsed_time(e1))
-        best.append(fit.max().item())
+        t0 = time.perf_counter()
+        net.fit(Xs, ts, 256, args.refit_epochs, 2e-4, 2e-4)
+        torch.cuda.synchronize()
+        refit_s = time.perf_counter() - t0
+        loss_after = scr.mean_loss(pp, net, Xs, ts)
+        best_r, ms_r = generations(net, pop, fit, G, args.branch, False)
+        net_plain = pp.Surrogate(D, 256, max_batch=R * NP)
+        net_plain.set_params(snap_w)
+        best_p, ms_p = generations(net_plain, snap_pop, snap_fit, G, args.branch, False)
+        net_plain.close()
+        gen_ms += ms_r + ms_p
+        calls = [NP * (G + 1 + k) for k in range(args.branch + 1)]
+        branch = {"at_generation": G, "rows": int(Xs.shape[0]), "epochs": args.refit_epochs,
+                  "refit_seconds": refit_s, "loss_before": loss_before, "loss_after": loss_after,
+                  "exact_calls": calls, "best_N_with_refit": best_r, "best_N_without_refit": best_p}
+        fit_s_refit = refit_s
+    else:
+        fit_s_refit = fit_s
     clk = clocks.stop()
     if pp.sync_status() != pp.PP_OK:
         raise RuntimeError("device status after the large-scale run")
@@ -551,83 +665,103 @@ def large_main(args):
     ms = statistics.mean(gen_ms)
     print(json.dumps({
         "metric": "candidate pulses scored/s (large-scale configuration, screened DE)",
-        "value": NP / (ms * 1e-3), "unit": "candidates/s", "n_gpus": 1, "steps": G, "warmup": 0,
+        "value": NP / (ms * 1e-3), "unit": "candidates/s", "n_gpus": 1, "steps": len(gen_ms), "warmup": 0,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "none", "vs_baseline": None,
         "dtype": "f32" if prec != "fp64" else "f64", "data": "synthetic (seeded B-spline pulses)",
         "config": {"workload": Lg["name"], "precision": prec, "scheme": sch, "NP": NP, "K": K,
                    "T": Lg["T"], "n_steps": Lg["n_steps"], "grid": "128x128x64 over [-2.5,2.5]^2 x [0,2.5]",
-                   "R": R, "generations_run": G, "generations_configured": Lg["generations"]},
+                   "R": R, "generations_run": G, "branch_generations": args.branch,
+                   "generations_configured": Lg["generations"]},
         "mode_steps_per_s": NP * modes * Lg["n_steps"] / (ms * 1e-3),
         "generation_ms": gen_ms, "initial_population_ms": init_ms, "surrogate_fit_s": fit_s,
-        "best_N": best, "n_rel_err_vs_fp64_rk4_max": rel,
+        "best_N": best, "n_rel_err_vs_fp64_rk4_max": rel, "refit_branch": branch,
         "extrapolated_hours_for_configured_generations":
             (init_ms + ms * Lg["generations"]) / 3.6e6
-            + fit_s * (Lg["generations"] // Lg["refit_every"]) / 3600.0,
-        "note": "%d of %d generations run; the rest extrapolated from their mean time (the network "
-                "refits every %d generations, at the measured fit time)"
-                % (G, Lg["generations"], Lg["refit_every"]),
+            + fit_s_refit * (Lg["generations"] // Lg["refit_every"]) / 3600.0,
+        "note": "%d generations to the branch point plus %d on each branch; the configured %d "
+                "extrapolated from their mean time and %d refits at the measured refit time"
+                % (G, args.branch, Lg["generations"], Lg["generations"] // Lg["refit_every"]),
         "clocks": clk}), flush=True)
     return 0
 
 
-def single_main(args):
+def measure_single(pp, torch, local, peaks, steps=10, warmup=3, tune=True, with_oracle=True):
     """The plain FP64 single-field solve (the rotating Gaussian of the parity case):
-    GPU FP64 RK4 on all 16384 modes, timed, and the FP64 oracle on all of them."""
-    import torch
-    import oracle
-    import paper_1704_08919_gb300 as pp
+    GPU FP64 RK4 on all 16384 modes x 4000 steps, timed with CUDA events over
+    `steps` solves after `warmup`; with_oracle: the FP64 oracle on the same
+    potential (all modes), for the N and n(p) errors and the CPU time."""
     g = inputs.ROTATING_GAUSSIAN
+    ns = g["n_steps"]
+    dt = (g["t1"] - g["t0"]) / ns
+    A = inputs.rotating_gaussian_potential(g, 2 * ns + 1)
+    Ad = torch.tensor(A[None], device="cuda")
+    tuned = None
+    if tune:  # 16384 modes: the CTA size decides how many SMs get work
+        chosen, cfg_ms, _ = pp.tune_pair_number(Ad, dt, g["grid"], precision="fp64", scheme="rk4")
+        tuned = {"chosen": pp.launch_configs()[chosen], "ms": [round(x, 2) for x in cfg_ms]}
+    for _ in range(warmup):
+        pp.pair_number(Ad, dt, g["grid"], precision="fp64", scheme="rk4")
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(steps):
+        N, n = pp.pair_number(Ad, dt, g["grid"], precision="fp64", scheme="rk4", want_n=True)
+    e1.record(st)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / steps
+    if pp.sync_status() != pp.PP_OK:
+        raise RuntimeError("device status after the single-field solve")
+    gr = g["grid"]
+    modes = gr["nx"] * gr["ny"] * gr["nz"]
+    flop = WORK[("fp64", "rk4")][0]
+    achieved = flop * modes * ns / (ms * 1e-3) / 1e12
+    rec = {"workload": g["name"], "precision": "fp64", "scheme": "rk4", "steps": steps, "warmup": warmup,
+           "ms_per_solve": ms, "mode_steps_per_s": modes * ns / (ms * 1e-3), "N": N.item(),
+           "roofline": {"bound": "alu", "kernel": "propagate_kernel<rk4, double>", "achieved": achieved,
+                        "peak": peaks["fp64_tflops"], "unit": "TFLOP/s",
+                        "frac": achieved / peaks["fp64_tflops"], "peak_source": peaks["fp64_source"],
+                        "flop_per_mode_step": flop,
+                        "note": "whole solve timed (table build, propagation, momentum sum)"},
+           "launch_tuning": tuned, "clocks": clk,
+           "l2": "not flushed: the solve is ALU-bound with a 0.5 MB working set"}
+    if with_oracle:
+        import oracle
+        t0 = time.perf_counter()
+        No, no = oracle.pair_number(A[None], ns, dt, g["grid"])
+        cpu_s = time.perf_counter() - t0
+        nn = n.cpu().numpy().reshape(-1)
+        nov = no.reshape(-1)
+        big = nov >= 1e-6 * nov.max()
+        rec["N_oracle"] = float(No[0])
+        rec["N_rel_err_vs_oracle"] = abs(N.item() / No[0] - 1)
+        rec["n_max_rel_err_vs_oracle_where_n_ge_1e-6_max"] = float(np.abs(nn[big] / nov[big] - 1).max())
+        rec["cpu_baseline"] = {"value": cpu_s * 1e3, "unit": "ms", "cores": oracle.num_threads(0),
+                               "kind": "oracle", "sample": "the whole solve (all 16384 modes)"}
+    return rec
+
+
+def single_main(args):
+    """--workload single: the config-1 solve as its own JSON line."""
+    import torch
+    import paper_1704_08919_gb300 as pp
     ws, rank, local = dist_env()
     if rank != 0:
         return 0
     torch.cuda.set_device(local)
     pp.lib()
-    ns = g["n_steps"]
-    dt = (g["t1"] - g["t0"]) / ns
-    A, _, _ = oracle.gaussian_rotating_field(g["E0"], g["w"], g["tau"], g["t0"], dt / 2, 2 * ns + 1)
-    Ad = torch.tensor(A[None], device="cuda")
-    tuned = None
-    if not args.no_tune:  # 16384 modes: the CTA size decides how many SMs get work
-        chosen, cfg_ms, _ = pp.tune_pair_number(Ad, dt, g["grid"], precision="fp64", scheme="rk4")
-        tuned = {"chosen": pp.launch_configs()[chosen], "ms": [round(x, 2) for x in cfg_ms]}
-    for _ in range(args.warmup):
-        pp.pair_number(Ad, dt, g["grid"], precision="fp64", scheme="rk4")
-    st = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(st)
-    for _ in range(args.steps):
-        N, n = pp.pair_number(Ad, dt, g["grid"], precision="fp64", scheme="rk4", want_n=True)
-    e1.record(st)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
-    if pp.sync_status() != pp.PP_OK:
-        raise RuntimeError("device status")
-    t0 = time.perf_counter()
-    No, no = oracle.pair_number(A[None], ns, dt, g["grid"])
-    cpu_s = time.perf_counter() - t0
-    gr = g["grid"]
-    modes = gr["nx"] * gr["ny"] * gr["nz"]
-    nn = n.cpu().numpy().reshape(-1)
-    nov = no.reshape(-1)
-    big = nov >= 1e-6 * nov.max()
-    rel_N = abs(N.item() / No[0] - 1)
-    flop = WORK[("fp64", "rk4")][0]
-    achieved = flop * modes * ns / (ms * 1e-3) / 1e12
-    print(json.dumps({
+    rec = measure_single(pp, torch, local, device_peaks(local), steps=args.steps, warmup=args.warmup,
+                         tune=not args.no_tune)
+    ms = rec["ms_per_solve"]
+    print(json.dumps(dict({
         "metric": "single-field FP64 solve time (rotating Gaussian, 16384 modes x 4000 RK4 steps)",
         "value": ms, "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": False, "scaling": "none", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic (analytic field)", "config": {"workload": g["name"]},
-        "mode_steps_per_s": modes * ns / (ms * 1e-3),
-        "N": N.item(), "N_oracle": float(No[0]), "N_rel_err_vs_oracle": rel_N,
-        "n_max_rel_err_vs_oracle_where_n_ge_1e-6_max": float(np.abs(nn[big] / nov[big] - 1).max()),
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
-                     "frac": achieved / 1.25, "note": "%d FP64 flop per mode-step; nominal GB300 FP64 "
-                     "peak (no measured FP64 peak)" % flop},
-        "cpu_baseline": {"value": cpu_s * 1e3, "unit": "ms", "cores": oracle.num_threads(0),
-                         "kind": "oracle", "sample": "the whole solve (all 16384 modes)"},
-        "launch_tuning": tuned}), flush=True)
+        "dtype": "f64", "data": "synthetic (analytic field)", "config": {"workload": rec["workload"]}},
+        **{k: v for k, v in rec.items() if k not in ("workload", "steps", "warmup")})), flush=True)
     return 0
 
 
@@ -729,6 +863,59 @@ def surrogate_main(args):
     return 0
 
 
+def measure_de_batch_fp64(pp, torch, local, peaks, pop, fit, seed, gen, lo_t, hi_t, per_t, flush):
+    """Config 2's FP64 arm: one DE generation of the 64-candidate batch through
+    pp_de_step with FP64 RK4 propagation (the parity path), timed with CUDA events
+    and the library's kernel timing; selection is against the population's current
+    fitness.  The scored trials are rescored by the FP32-fast Magnus path for the
+    FP64-vs-FP32 comparison."""
+    spec, grid = inputs.field_spec(CFG), CFG["grid"]
+    dt = CFG["T"] / CFG["n_steps"]
+    NP = pop.shape[0]
+    # warm-up: the FP64 kernel and its table on 4 candidates
+    Aw, _, _ = pp.synth_field(pop[:4].contiguous(), spec)
+    pp.pair_number(Aw, dt, grid, precision="fp64", scheme="rk4")
+    trial = torch.empty_like(pop)
+    tfit = torch.empty_like(fit)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    flush.zero_()
+    pp.profile_begin()
+    e0.record(stream)
+    pp.de_step(pop, fit, spec, grid, lo_t, hi_t, per_t, CFG["F"], CFG["CR"], seed, gen, precision="fp64",
+               scheme="rk4", trial_out=trial, trial_fit_out=tfit)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    kern_ms, launches = pp.profile_end()
+    clk = clocks.stop()
+    if pp.sync_status() != pp.PP_OK:
+        raise RuntimeError("FP64 DE generation: device status")
+    ms = e0.elapsed_time(e1)
+    At, _, _ = pp.synth_field(trial, spec)
+    Nf, _ = pp.pair_number(At, dt, grid, precision="fp32fast", scheme="magnus4")
+    pp.sync_status()
+    units = NP * units_per_candidate()
+    flop = WORK[("fp64", "rk4")][0]
+    per_launch = kern_ms / max(launches, 1)
+    achieved = flop * units / (per_launch * 1e-3) / 1e12
+    return {"workload": CFG["name"], "precision": "fp64", "scheme": "rk4", "generations": 1,
+            "ms_per_generation": ms, "candidates_per_s": NP / (ms * 1e-3),
+            "mode_steps_per_s": units / (ms * 1e-3),
+            "fp32fast_magnus4_vs_fp64_rk4_max_rel_N_on_trials": (Nf / tfit - 1).abs().max().item(),
+            "roofline": {"bound": "alu", "kernel": "propagate_kernel<rk4, double>", "achieved": achieved,
+                         "peak": peaks["fp64_tflops"], "unit": "TFLOP/s",
+                         "frac": achieved / peaks["fp64_tflops"], "peak_source": peaks["fp64_source"],
+                         "flop_per_mode_step": flop, "launch_ms": per_launch,
+                         "kernel_share_of_step": kern_ms / ms},
+            "l2": "flushed before the generation (256 MiB write)",
+            "note": "selection against the population's fitness from the FP32 run (within 1e-6 of FP64)",
+            "clocks": clk, "gpu_launches": 7}
+
+
 # ----------------------------------------------------------------------------- GPU leg
 
 
@@ -760,36 +947,57 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
     pp.lib()
     stream = torch.cuda.current_stream()
+    peaks = device_peaks(local)
 
+    # One population of NP candidates per rank: at N = 1 the DE batch itself; at N > 1
+    # one population of N * NP replicated on every rank, each rank scoring its NP
+    # trials per generation and one allgather of the pair numbers (weak scaling).
     NP, K = args.ncand, CFG["K"]
+    NP_total = NP * ws
+    first, last = shard.shard_bounds(NP_total, ws, rank)
     spec = inputs.field_spec(CFG)
     grid = CFG["grid"]
     dt = CFG["T"] / CFG["n_steps"]
     lo, hi, per = inputs.param_bounds(K)
-    pop_seed, seed = rank_seeds(rank)
-    pop0 = inputs.random_population(NP, K, seed=pop_seed)
+    pop_seed, seed = 1, 1000
+    pop0 = inputs.random_population(NP_total, K, seed=pop_seed)
     lo_t, hi_t = torch.tensor(lo, device=dev), torch.tensor(hi, device=dev)
     per_t = torch.tensor(per, device=dev)
     pop = torch.tensor(pop0, device=dev)
-    A, _, _ = pp.synth_field(pop, spec)
+    A, _, _ = pp.synth_field(pop[first:last].contiguous(), spec)
     tuned = None
     if not args.no_tune:
         chosen, cfg_ms, _ = pp.tune_pair_number(A, dt, grid, precision=args.precision,
                                                 scheme=args.scheme)
         tuned = {"chosen": pp.launch_configs()[chosen], "ms": [round(x, 2) for x in cfg_ms],
                  "configs": pp.launch_configs()}
-    fit, _ = pp.pair_number(A, dt, grid, precision=args.precision, scheme=args.scheme)
+    fit_local, _ = pp.pair_number(A, dt, grid, precision=args.precision, scheme=args.scheme)
+    gather = shard.allgather_fn(dist) if dist is not None else None
+    fit = gather(fit_local, NP_total, ws) if gather else fit_local
     trial = torch.empty_like(pop)
     tfit = torch.empty_like(fit)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     if pp.sync_status() != pp.PP_OK:
         raise RuntimeError("initial scoring failed: %s" % pp.lib().pp_last_error().decode())
+    sharded_steps = {}
+
+    def generation(g, precision):
+        """One DE generation of the population: pp_de_step at N = 1, the sharded
+        generation (replicated proposal, local scoring, allgather, replicated
+        selection) at N > 1."""
+        if dist is None:
+            pp.de_step(pop, fit, spec, grid, lo_t, hi_t, per_t, CFG["F"], CFG["CR"], seed, g,
+                       precision=precision, trial_out=trial, trial_fit_out=tfit, scheme=args.scheme)
+            return
+        if precision not in sharded_steps:
+            sharded_steps[precision] = shard.library_steps(pp, spec, grid, lo_t, hi_t, per_t, CFG["F"],
+                                                           CFG["CR"], seed, precision, args.scheme)
+        propose, score, select = sharded_steps[precision]
+        shard.sharded_generation(propose, score, select, gather, pop, fit, g, rank, ws)
 
     gen = 0
     for _ in range(max(args.warmup, 0)):
-        pp.de_step(pop, fit, spec, grid, lo_t, hi_t, per_t, CFG["F"], CFG["CR"], seed, gen,
-                   precision=args.precision, trial_out=trial, trial_fit_out=tfit,
-                   scheme=args.scheme)
+        generation(gen, args.precision)
         gen += 1
     torch.cuda.synchronize()
 
@@ -807,9 +1015,7 @@ def main():
     for s in range(args.steps):
         flush.zero_()
         starts[s].record(stream)
-        pp.de_step(pop, fit, spec, grid, lo_t, hi_t, per_t, CFG["F"], CFG["CR"], seed, gen,
-                   precision=args.precision, trial_out=trial, trial_fit_out=tfit,
-                   scheme=args.scheme)
+        generation(gen, args.precision)
         ends[s].record(stream)
         gen += 1
     torch.cuda.synchronize()
@@ -828,15 +1034,15 @@ def main():
     # ---- live roofline of the propagation kernel
     per_launch_ms = kern_ms / max(kern_launches, 1)
     flop, inst = WORK[(args.precision, args.scheme)]
-    units = NP * units_per_candidate()
+    units = (last - first) * units_per_candidate()
     achieved = flop * units / (per_launch_ms / 1000.0) / 1e12
     if args.precision in ("fp32", "fp32fast"):
-        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
-        peak_src = "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)"
-        lanes = SM_COUNT * FP32_LANES_PER_SM * 2070e6
+        peak = peaks["fp32_tflops"]
+        peak_src = peaks["fp32_source"]
+        lanes = peaks["fp32_lanes_per_s"]
     else:
-        peak = 1.25
-        peak_src = "nominal GB300 FP64 (no measured FP64 peak available)"
+        peak = peaks["fp64_tflops"]
+        peak_src = peaks["fp64_source"]
         lanes = peak * 1e12 / 2
     roofline = {"bound": "alu", "kernel": "propagate_kernel<%s, %s>" % (args.scheme, {
         "fp32": "float, compensated", "fp32fast": "float", "fp64": "double"}[args.precision]),
@@ -855,7 +1061,8 @@ def main():
 
     # ---- accuracy at the bench config: N of the timed path vs FP64 RK4 (the oracle's
     # algorithm, parity-tested against it) on 4 candidates of the final population
-    Acheck, _, _ = pp.synth_field(pop[:4].contiguous(), spec)
+    pcheck = pop[:4].clone()
+    Acheck, _, _ = pp.synth_field(pcheck, spec)
     N32, _ = pp.pair_number(Acheck, dt, grid, precision=args.precision, scheme=args.scheme)
     N64, n64 = pp.pair_number(Acheck, dt, grid, precision="fp64", scheme="rk4", want_n=True)
     pp.sync_status()
@@ -870,9 +1077,7 @@ def main():
         t0 = time.perf_counter()
         pop.copy_(pop_h, non_blocking=True)
         fit.copy_(fit_h, non_blocking=True)
-        pp.de_step(pop, fit, spec, grid, lo_t, hi_t, per_t, CFG["F"], CFG["CR"], seed, gen,
-                   precision=args.precision, trial_out=trial, trial_fit_out=tfit,
-                   scheme=args.scheme)
+        generation(gen, args.precision)
         pop_h.copy_(pop, non_blocking=True)
         fit_h.copy_(fit, non_blocking=True)
         torch.cuda.synchronize()
@@ -888,16 +1093,14 @@ def main():
         if not args.no_tune:
             pp.tune_pair_number(A, dt, grid, precision="fp32", scheme=args.scheme)
         for _ in range(2):
-            pp.de_step(pop, fit, spec, grid, lo_t, hi_t, per_t, CFG["F"], CFG["CR"], seed, gen,
-                       precision="fp32", trial_out=trial, trial_fit_out=tfit, scheme=args.scheme)
+            generation(gen, "fp32")
             gen += 1
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.alt_steps)]
         for a, b in ev:
             flush.zero_()
             a.record(stream)
-            pp.de_step(pop, fit, spec, grid, lo_t, hi_t, per_t, CFG["F"], CFG["CR"], seed, gen,
-                       precision="fp32", trial_out=trial, trial_fit_out=tfit, scheme=args.scheme)
+            generation(gen, "fp32")
             b.record(stream)
             gen += 1
         torch.cuda.synchronize()
@@ -909,29 +1112,58 @@ def main():
                "ms_per_step": alt_ms / args.alt_steps,
                "n_rel_err_vs_fp64_rk4_max": (Nc / N64 - 1).abs().max().item()}
 
-    # ---- CPU-oracle baseline (rank 0, N = 1 only)
+    # ---- the FP64 oracle on one whole candidate (rank 0, N = 1 only): the metric's own
+    # check (N of the timed path against the oracle's) and the CPU baseline.  The
+    # oracle synthesises the candidate from its parameters itself.
     cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        A_host = Acheck.cpu().numpy()
-        el, n_or, idx, cores = oracle_sample(A_host, 0, args.cpu_modes)
-        cpu_mode_steps = args.cpu_modes * CFG["n_steps"] / el
-        n_gpu = n64[0].reshape(-1).cpu().numpy()[idx]
-        big = n_or >= 1e-6 * n64[0].max().item()
-        cpu = {"value": cpu_mode_steps / units_per_candidate(), "unit": "candidates/s",
-               "cores": cores, "kind": "oracle",
-               "sample": "%d strided modes of one candidate x %d RK4 steps (%.1f s), "
-                         "extrapolated to a full candidate by mode-steps" % (
-                             args.cpu_modes, CFG["n_steps"], el),
-               "mode_steps_per_s": cpu_mode_steps,
-               "gpu_fp64_vs_oracle_max_rel_n": float(np.abs(n_gpu[big] / n_or[big] - 1).max())}
-        el1, _, _, _ = oracle_sample(A_host, 0, 256, seed=1, nthreads=1)
-        cpu["one_core"] = {"mode_steps_per_s": 256 * CFG["n_steps"] / el1,
-                           "value": 256 * CFG["n_steps"] / el1 / units_per_candidate(),
-                           "sample": "256 strided modes x %d steps on one thread (%.2f s)" % (
-                               CFG["n_steps"], el1)}
+    oracle_check = None
+    if rank == 0 and ws == 1 and not args.no_oracle_n:
+        import oracle
+        prm = pcheck[:1].cpu().numpy()
+        Ao, _, _, orc = oracle.synth_field(prm, K, CFG["order"], CFG["w_min"], CFG["w_max"], CFG["T"],
+                                           CFG["fluence"], CFG["n_steps"], want_E=False)
+        t0 = time.perf_counter()
+        No, no = oracle.pair_number(Ao, CFG["n_steps"], dt, grid)
+        el = time.perf_counter() - t0
+        cores = oracle.num_threads(0)
+        n_gpu = n64[0].reshape(-1).cpu().numpy()
+        nov = no.reshape(-1)
+        big = nov >= 1e-6 * nov.max()
+        oracle_check = {
+            "candidate": "population row 0 after the timed generations (all %d modes x %d steps)"
+                         % (units_per_candidate() // CFG["n_steps"], CFG["n_steps"]),
+            "N_oracle": float(No[0]),
+            "n_rel_err_vs_oracle": abs(N32[0].item() / No[0] - 1),
+            "gpu_fp64_rk4_N_rel_err_vs_oracle": abs(N64[0].item() / No[0] - 1),
+            "gpu_fp64_rk4_n_max_rel_err_where_n_ge_1e-6_max": float(np.abs(n_gpu[big] / nov[big] - 1).max()),
+            "oracle_seconds": el, "oracle_cores": cores}
+        if not args.no_cpu_baseline:
+            cpu = {"value": 1.0 / el, "unit": "candidates/s", "cores": cores, "kind": "oracle",
+                   "sample": "one whole candidate: %d modes x %d RK4 steps in FP64 (%.1f s); the "
+                             "oracle's synthesis excluded" % (units_per_candidate() // CFG["n_steps"],
+                                                              CFG["n_steps"], el),
+                   "mode_steps_per_s": units_per_candidate() / el}
+            A_host = Acheck.cpu().numpy()
+            el1, _, _, _ = oracle_sample(A_host, 0, 256, seed=1, nthreads=1)
+            cpu["one_core"] = {"mode_steps_per_s": 256 * CFG["n_steps"] / el1,
+                               "value": 256 * CFG["n_steps"] / el1 / units_per_candidate(),
+                               "sample": "256 strided modes x %d steps on one thread (%.2f s)" % (
+                                   CFG["n_steps"], el1)}
+
+    # ---- the other configurations, each with its own timing, clocks and roofline
+    configs = None
+    if rank == 0 and ws == 1 and not args.no_configs:
+        configs = {"single_fp64": measure_single(pp, torch, local, peaks, tune=not args.no_tune),
+                   "de_batch_fp64": measure_de_batch_fp64(pp, torch, local, peaks, pop, fit, seed, gen,
+                                                          lo_t, hi_t, per_t, flush)}
+        gen += 1
+        configs["uneven"], _ = measure_uneven(pp, torch, local, peaks, 4, tune=not args.no_tune)
 
     if rel_err > 1e-4:
         raise RuntimeError("N error %.3e vs FP64 RK4 exceeds 1e-4: no valid measurement" % rel_err)
+    if oracle_check and oracle_check["n_rel_err_vs_oracle"] > 1e-4:
+        raise RuntimeError("N error %.3e vs the FP64 oracle exceeds 1e-4: no valid measurement"
+                           % oracle_check["n_rel_err_vs_oracle"])
     if rank == 0:
         line = {
             "metric": "candidate pulses scored/s (DE batch, rel. N err <= 1e-4 vs FP64 oracle)",
@@ -941,9 +1173,15 @@ def main():
             "dtype": "f64" if args.precision == "fp64" else "f32",
             "scheme": args.scheme,
             "data": "synthetic (seeded B-spline pulses, uniform in bounds)",
-            "config": workload_config(args.precision, NP, args.scheme),
+            "config": dict(workload_config(args.precision, NP, args.scheme), **(
+                {"population": NP_total,
+                 "sharding": "one population of %d replicated on %d ranks; each rank scores its %d trials "
+                             "per generation; one allgather of the %d pair numbers (NCCL) per generation"
+                             % (NP_total, ws, NP, NP_total)} if ws > 1 else {})),
             "mode_steps_per_s": mode_steps_per_s,
             "n_rel_err_vs_fp64_rk4_max": rel_err,
+            "n_rel_err_vs_oracle": oracle_check["n_rel_err_vs_oracle"] if oracle_check else None,
+            "oracle_check": oracle_check,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "candidates/s", "h2d_bytes_per_step": h2d,
@@ -954,6 +1192,8 @@ def main():
             "clocks": clk,
             "wall_s_timed": t_wall,
             "step_ms": step_ms,
+            "peaks": {k: peaks[k] for k in ("sm_count", "sm_max_mhz", "fp32_tflops", "fp64_tflops")},
+            "configs": configs,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

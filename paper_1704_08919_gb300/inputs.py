@@ -1,8 +1,8 @@
 """Seeded synthetic inputs shared by the tests, the bench and the smoke check.
 
-This module holds workload descriptions and random draws only -- none of the
-method's arithmetic -- so that the CUDA path and the CPU oracle can be fed the
-same inputs without sharing any code.  Numbers are drawn with numpy's PCG64
+This module holds workload descriptions, random draws and the given field of
+the rotating-Gaussian workload -- none of the method's arithmetic -- so that the
+CUDA path and the CPU oracle can be fed the same inputs without sharing any code.  Numbers are drawn with numpy's PCG64
 (`numpy.random.default_rng(seed)`).
 
 Workloads (sizes follow the paper's pulse model, Sec. III, and momentum
@@ -160,6 +160,23 @@ def strided_modes(grid, count, seed):
     nm = grid["nx"] * grid["ny"] * grid["nz"]
     rng = np.random.default_rng(seed)
     return np.sort(rng.choice(nm, size=min(count, nm), replace=False))
+
+
+def rotating_gaussian_potential(cfg, n_samples):
+    """The vector potential of the ROTATING_GAUSSIAN field on n_samples points of
+    its half-step grid, t_k = t0 + k (t1 - t0) / (n_samples - 1): A(t) = -int_{t0}^t E
+    with E_x + i E_y = E0 exp(-t^2/tau^2 + i w t), written in closed form with the
+    complex error function,
+        int exp(-t^2/tau^2 + i w t) dt = (sqrt(pi) tau / 2) exp(-w^2 tau^2 / 4) erf(t/tau - i w tau / 2),
+    so A_x + i A_y = -E0 (sqrt(pi) tau / 2) exp(-w^2 tau^2 / 4) [erf(z(t)) - erf(z(t0))].
+    Returns A[2][n_samples] (rows A_x, A_y)."""
+    from scipy.special import erf
+    E0, w, tau, t0, t1 = cfg["E0"], cfg["w"], cfg["tau"], cfg["t0"], cfg["t1"]
+    t = t0 + np.arange(n_samples) * ((t1 - t0) / (n_samples - 1))
+    pref = E0 * math.sqrt(math.pi) * tau / 2 * math.exp(-(w * tau) ** 2 / 4)
+    z = t / tau - 0.5j * w * tau
+    a = -pref * (erf(z) - erf(t0 / tau - 0.5j * w * tau))
+    return np.stack([a.real, a.imag])
 
 
 def small_grid(nx, ny, nz, ext=2.0, mirror_z=1):
