@@ -363,7 +363,9 @@ def measure_uneven(pp, torch, local, peaks, G, precision="fp32fast", scheme="mag
                         "peak_source": peaks["fp32_source"] if fp32 else peaks["fp64_source"],
                         "flop_per_mode_step": flop,
                         "note": "whole graph timed (proposal, synthesis, tables, propagation, selection)"},
-           "gpu_launches": 8 * G}
+           # per generation: proposal, spectrum, samples, table, propagation (+ its
+           # wide-range twin for Magnus-4), partial sums, selection, generation counter
+           "gpu_launches": (9 if scheme == "magnus4" else 8) * G}
     return rec, total_ms
 
 
@@ -1186,7 +1188,9 @@ def main():
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "candidates/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": h2d},
-            "gpu_launches": 7 * args.steps,
+            # per generation: proposal, spectrum, samples, table, propagation (+ its
+            # wide-range twin for Magnus-4), partial sums, selection
+            "gpu_launches": (8 if args.scheme == "magnus4" else 7) * args.steps,
             "launch_tuning": tuned,
             "alt_compensated": alt,
             "clocks": clk,

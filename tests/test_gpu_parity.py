@@ -314,6 +314,27 @@ def test_de_batch_full_size_sampled_modes(pp):
         assert n_excess(ng, no, cfg["n_steps"]) <= 1.0
 
 
+def test_de_batch_full_grid_against_the_oracle(pp):
+    # The metric's own check at the DE-batch size (Sec. II.A, Eqs. (pair_prod_homo),
+    # (opt_prob)): the oracle's N over the whole 64 x 64 x 32 grid and 8192 RK4 steps of
+    # one candidate, synthesised by each side from the same parameters, against the
+    # timed path (Magnus-4, FP32 without compensation: 1e-4) and the FP64 RK4 path (1e-9).
+    cfg = inputs.DE_BATCH
+    params = inputs.random_population(1, cfg["K"], seed=1)
+    ns, dt = cfg["n_steps"], cfg["T"] / cfg["n_steps"]
+    Ao, _, _, rc = oracle.synth_field(params, cfg["K"], cfg["order"], cfg["w_min"], cfg["w_max"], cfg["T"],
+                                      cfg["fluence"], ns, want_E=False)
+    assert rc == 0
+    No, no = oracle.pair_number(Ao, ns, dt, cfg["grid"])
+    A, _, _ = pp.synth_field(torch.tensor(params, device=DEV), inputs.field_spec(cfg))
+    Nf, _ = pp.pair_number(A, dt, cfg["grid"], precision="fp32fast", scheme="magnus4")
+    N64, n64 = pp.pair_number(A, dt, cfg["grid"], precision="fp64", scheme="rk4", want_n=True)
+    assert pp.sync_status() == pp.PP_OK
+    assert abs(Nf.item() / No[0] - 1) < 1e-4
+    assert abs(N64.item() / No[0] - 1) < 1e-9
+    assert n_excess(n64.cpu().numpy(), no, ns) <= 1.0
+
+
 def test_large_scale_size_sampled_modes(pp):
     """The large-scale configuration's size (K = 16, T = 400, 20000 steps, grid
     128 x 128 x 64 over [-2.5, 2.5]^2 x [0, 2.5]) for one candidate: FP64 RK4 on the

@@ -1,5 +1,7 @@
-"""The N > 1 launch path of bench.py on CPU: two gloo ranks exchange only the
-timing maximum; each rank evolves its own population (weak scaling)."""
+"""The N > 1 launch path of bench.py on CPU: the timing maximum over two gloo
+ranks, the per-rank seeds of the uneven-batch workload (independent populations
+there; the DE batch shards one population, see test_shard_cpu.py), and the
+reference arm under torchrun."""
 import os
 import socket
 
