@@ -205,16 +205,28 @@ __global__ void hann_spectrum_kernel(const double *__restrict__ params, int K, i
                         coef + (size_t)c * 4 * (M + 2), scale_out ? scale_out + c : nullptr, status, normalize);
 }
 
-// Samples: grid (ceil(nsamp / 256), ncand, 2 polarisations).
+// Samples: grid (ceil(nsamp / 256), ncand, 2 polarisations).  Horner's rule in
+// FP64 with explicit fused multiply-adds, per complex step z (x) + X_m:
+// (xr zc - xi zs + Xr, xr zs + xi zc + Xi).  WANT_E / WANT_ED compile the
+// accumulations of E and dE/dt in only when the caller asked for them.
+template <bool WANT_E, bool WANT_ED>
 __global__ void samples_kernel(const double2 *__restrict__ coef, int M, int j0, int n_steps,
                                int ld, double *__restrict__ A, double *__restrict__ E, double dw,
                                double *__restrict__ Ed, double T)
 {
     extern __shared__ double2 sc[];  // [2M]: C then D
+    __shared__ double s_d0i;
     const int c = blockIdx.y, l = blockIdx.z;
     const double2 *cf = coef + ((size_t)c * 2 + l) * 2 * M;
     for (int q = threadIdx.x; q < 2 * M; q += blockDim.x)
         sc[q] = cf[q];
+    __syncthreads();
+    if (threadIdx.x == 0) {  // Im of the sum of D_j (the z = 1 value), the same for every sample
+        double d0i = 0.0;
+        for (int m = M - 1; m >= 0; --m)
+            d0i += sc[M + m].y;
+        s_d0i = d0i;
+    }
     __syncthreads();
     const int nsamp = 2 * n_steps + 1;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -227,35 +239,36 @@ __global__ void samples_kernel(const double2 *__restrict__ coef, int M, int j0, 
     sincospi((double)(((long long)k * j0) % two_n) / (double)n_steps, &js, &jc);
     // Horner: sum_{m=0}^{M-1} X_m z^m
     double cr = 0.0, ci = 0.0, dr = 0.0, di = 0.0, gr = 0.0, gi = 0.0;
-    double d0i = 0.0;  // Im of the sum of D_j (the z = 1 value)
     for (int m = M - 1; m >= 0; --m) {
-        const double2 C = sc[m], D = sc[M + m];
-        double tr = cr * zc - ci * zs + C.x;
-        ci = cr * zs + ci * zc + C.y;
-        cr = tr;
-        tr = dr * zc - di * zs + D.x;
-        di = dr * zs + di * zc + D.y;
+        const double2 D = sc[M + m];
+        const double tr = fma(dr, zc, fma(-di, zs, D.x));
+        di = fma(dr, zs, fma(di, zc, D.y));
         dr = tr;
-        d0i += D.y;
-        if (Ed) {  // dE/dt: coefficients i Omega_j C_j
+        if constexpr (WANT_E) {
+            const double2 C = sc[m];
+            const double ur = fma(cr, zc, fma(-ci, zs, C.x));
+            ci = fma(cr, zs, fma(ci, zc, C.y));
+            cr = ur;
+        }
+        if constexpr (WANT_ED) {  // dE/dt: coefficients i Omega_j C_j
+            const double2 C = sc[m];
             const double W = (double)(j0 + m) * dw;
-            tr = gr * zc - gi * zs - W * C.y;
-            gi = gr * zs + gi * zc + W * C.x;
-            gr = tr;
+            const double vr = fma(gr, zc, fma(-gi, zs, -W * C.y));
+            gi = fma(gr, zs, fma(gi, zc, W * C.x));
+            gr = vr;
         }
     }
     // multiply by z^{j0}
-    const double Cr = cr * jc - ci * js;
-    const double Di = dr * js + di * jc;
+    const double Di = fma(dr, js, di * jc);
     double *Arow = A + ((size_t)c * 2 + l) * ld;
-    double a = -(Di - d0i);
+    double a = -(Di - s_d0i);
     if (j0 == 0)  // DC harmonic (Hann envelope): potential c0 (t_f - t_k)
         a += sc[0].x * ((double)(2 * n_steps - k) * (T / (2.0 * n_steps)));
     Arow[k] = a;
-    if (E)
-        E[((size_t)c * 2 + l) * ld + k] = Cr;
-    if (Ed)
-        Ed[((size_t)c * 2 + l) * ld + k] = gr * jc - gi * js;
+    if constexpr (WANT_E)
+        E[((size_t)c * 2 + l) * ld + k] = fma(cr, jc, -ci * js);
+    if constexpr (WANT_ED)
+        Ed[((size_t)c * 2 + l) * ld + k] = fma(gr, jc, -gi * js);
 }
 
 // ---- chain rule of the un-normalised synthesis (the local search's gradient):
@@ -562,12 +575,12 @@ __global__ void samples_batch_kernel(const double2 *__restrict__ coef, const Syn
     double dr = 0.0, di = 0.0, d0i = 0.0;
     for (int m = M - 1; m >= 0; --m) {
         const double2 D = scf[M + m];
-        const double tr = dr * zc - di * zs + D.x;
-        di = dr * zs + di * zc + D.y;
+        const double tr = fma(dr, zc, fma(-di, zs, D.x));
+        di = fma(dr, zs, fma(di, zc, D.y));
         dr = tr;
         d0i += D.y;
     }
-    const double Di = dr * js + di * jc;
+    const double Di = fma(dr, js, di * jc);
     double a = -(Di - d0i);
     if (d.j0 == 0)  // DC harmonic of the Hann envelope: potential c0 (t_f - t_k)
         a += scf[0].x * ((double)(2 * d.n_steps - k) * (d.T / (2.0 * d.n_steps)));
@@ -672,9 +685,10 @@ int launch_synth(const double *params, int ncand, const pp_field_spec *spec, int
                                                    normalize);
     const int nsamp = 2 * spec->n_steps + 1;
     dim3 g((nsamp + 255) / 256, ncand, 2);
-    samples_kernel<<<g, 256, 2 * Ms * sizeof(double2), stream>>>((const double2 *)coef, Ms, j0s,
-                                                                 spec->n_steps, ld, A, E,
-                                                                 2.0 * M_PI / spec->T, Ed, spec->T);
+    auto kern = E ? (Ed ? samples_kernel<true, true> : samples_kernel<true, false>)
+                  : (Ed ? samples_kernel<false, true> : samples_kernel<false, false>);
+    kern<<<g, 256, 2 * Ms * sizeof(double2), stream>>>((const double2 *)coef, Ms, j0s, spec->n_steps, ld, A, E,
+                                                       2.0 * M_PI / spec->T, Ed, spec->T);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return cuda_fail(e, "synthesis kernel launch");
