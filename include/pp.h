@@ -295,13 +295,20 @@ int pp_mlp_features(const double *params, int32_t B, int32_t D, const double *lo
                     float *X, void *stream);
 
 /* Mini-batch training: `epochs` passes over the n rows of X (device FP32
- * [n][d_in]) and t (device FP32 [n]) in order, in slices of `batch` rows (the
- * last one ragged), one pp_mlp_train_step per slice, the learning rate
- * following a cosine from lr0 (first step) to lr1 (last step).  epoch_loss
- * (device FP32 [epochs], or NULL) receives the loss of each epoch's last slice.
- * Rows are not shuffled: pass data in random order. */
+ * [n][d_in]) and t (device FP32 [n]), in slices of `batch` rows (the last one
+ * ragged), one pp_mlp_train_step per slice, the learning rate following a cosine
+ * from lr0 (first step) to lr1 (last step).  epoch_loss (device FP32 [epochs],
+ * or NULL) receives the loss of each epoch's last slice.
+ * Row order: seed = 0 visits the rows in the order given, every epoch.  Any other
+ * seed visits, in epoch e, rows pi_e(0), pi_e(1), ..., pi_e(n - 1), where pi_e is
+ * a bijection of [0, n): a 4-round Feistel network on b-bit integers (b the least
+ * even number with 2^b >= n, halves of b/2 bits; round i maps (L, R) to
+ * (R, L xor (out(k_i, R) mod 2^(b/2))) with k_i = out(seed, 4 e + i), out(s, k) the
+ * k-th SplitMix64 output of seed s as in pp_de_propose), applied again while the
+ * value is >= n.  The rows of each slice are gathered into buffers of the network;
+ * nothing is allocated. */
 int pp_mlp_fit(pp_mlp *h, const float *X, const float *t, int32_t n, int32_t batch, int32_t epochs,
-               float lr0, float lr1, float *epoch_loss, void *stream);
+               float lr0, float lr1, uint64_t seed, float *epoch_loss, void *stream);
 
 /* Training targets from pair numbers: t[i] = (log10(max(N[i], floor)) - shift)
  * / scale for device FP64 N[n] into device FP32 t[n]; floor > 0, scale != 0. */

@@ -148,7 +148,7 @@ def lib():
                                           ctypes.POINTER(Grid), _i32, _i32, _vp, _vp, _vp, _d, _d,
                                           _u64, _u64, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp]
         L.pp_mlp_fit.argtypes = [_vp, _vp, _vp, _i32, _i32, _i32, ctypes.c_float, ctypes.c_float,
-                                 _vp, _vp]
+                                 ctypes.c_uint64, _vp, _vp]
         L.pp_mlp_log_targets.argtypes = [_vp, _i32, _d, _d, _d, _vp, _vp]
         L.pp_mlp_init.argtypes = [_vp, _u64, _vp]
         L.pp_synth_field_raw.argtypes = [_vp, _i32, ctypes.POINTER(FieldSpec), _vp, _vp, _vp, _i32,
@@ -372,12 +372,13 @@ class Surrogate:
                                        _stream(stream)))
         return loss
 
-    def fit(self, X, t, batch, epochs, lr0, lr1, stream=None):
-        """pp_mlp_fit; returns the loss of each epoch's last slice (FP32 CUDA tensor)."""
+    def fit(self, X, t, batch, epochs, lr0, lr1, seed=0, stream=None):
+        """pp_mlp_fit; seed 0 keeps the row order, others shuffle it per epoch.  Returns
+        the loss of each epoch's last slice (FP32 CUDA tensor)."""
         import torch
         loss = torch.empty(epochs, dtype=torch.float32, device=X.device)
         _check(lib().pp_mlp_fit(self.h, _ptr(X), _ptr(t), X.shape[0], int(batch), int(epochs),
-                                float(lr0), float(lr1), _ptr(loss), _stream(stream)))
+                                float(lr0), float(lr1), int(seed), _ptr(loss), _stream(stream)))
         return loss
 
 

@@ -274,12 +274,58 @@ __global__ void group_select_kernel(double *__restrict__ pop, double *__restrict
 }
 
 // SplitMix64 output k of the generator seeded with s (Steele, Lea, Flood 2014).
-__device__ __forceinline__ uint64_t mlp_sm64_at(uint64_t s, uint64_t k)
+__host__ __device__ __forceinline__ uint64_t mlp_sm64_at(uint64_t s, uint64_t k)
 {
     uint64_t z = s + (k + 1) * 0x9E3779B97F4A7C15ull;
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
     return z ^ (z >> 31);
+}
+
+// Row order of one training epoch: a bijection of [0, n) from a 4-round Feistel
+// network on b-bit integers (b the least even number with 2^b >= n; halves of
+// hb = b/2 bits; round i maps (L, R) to (R, L xor (out(k_i, R) mod 2^hb)), out =
+// SplitMix64), applied again while the value is >= n (cycle walking: the walk
+// stays on the cycle through x, which returns below n within 2^b steps).
+struct RowShuffle {
+    uint64_t k[4];
+    int hb;
+    long long n;
+};
+
+__device__ __forceinline__ long long shuffled_row(const RowShuffle &r, long long x)
+{
+    const uint64_t mask = (1ull << r.hb) - 1ull;
+    const long long dom = 1ll << (2 * r.hb);
+    for (long long it = 0; it < dom; ++it) {
+        uint64_t L = (uint64_t)x >> r.hb, R = (uint64_t)x & mask;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint64_t F = mlp_sm64_at(r.k[i], R) & mask;
+            const uint64_t nL = R;
+            R = L ^ F;
+            L = nL;
+        }
+        x = (long long)((L << r.hb) | R);
+        if (x < r.n)
+            break;
+    }
+    return x;
+}
+
+// Mini-batch rows r0 .. r0 + rows - 1 of an epoch into the staging buffers.
+__global__ void gather_rows_kernel(const float *__restrict__ X, const float *__restrict__ t, int din,
+                                   RowShuffle sh, long long r0, int rows, float *__restrict__ Xs,
+                                   float *__restrict__ ts)
+{
+    const int i = blockIdx.x;
+    if (i >= rows)
+        return;
+    const long long src = shuffled_row(sh, r0 + i);
+    for (int j = threadIdx.x; j < din; j += blockDim.x)
+        Xs[(size_t)i * din + j] = X[(size_t)src * din + j];
+    if (threadIdx.x == 0)
+        ts[i] = t[src];
 }
 
 // He initialisation: parameter i of a weight block with fan-in f is
@@ -334,6 +380,8 @@ struct pp_mlp {
     float *X = nullptr, *Z1 = nullptr, *Z2 = nullptr, *Z3 = nullptr, *A1 = nullptr, *A2 = nullptr,
           *A3 = nullptr, *y = nullptr, *dy = nullptr, *dZ = nullptr, *dA = nullptr, *D = nullptr;
     void *Xp = nullptr, *A1p = nullptr, *A2p = nullptr, *Tp1 = nullptr, *Tp2 = nullptr;
+    // shuffled mini-batches of pp_mlp_fit (bmax rows)
+    float *Xs = nullptr, *ts = nullptr;
 };
 
 namespace {
@@ -346,7 +394,7 @@ void mlp_free(pp_mlp *h)
         return;
     void *ptrs[] = {h->p, h->m, h->v, h->g, h->W1p, h->W2p, h->W3p, h->W2Tp, h->W3Tp, h->X, h->Z1, h->Z2,
                     h->Z3, h->A1, h->A2, h->A3, h->y, h->dy, h->dZ, h->dA, h->D, h->Xp, h->A1p, h->A2p,
-                    h->Tp1, h->Tp2};
+                    h->Tp1, h->Tp2, h->Xs, h->ts};
     for (void *q : ptrs)
         if (q)
             cudaFree(q);
@@ -525,6 +573,8 @@ int pp_mlp_create(int32_t d_in, int32_t hidden, int32_t max_batch, pp_mlp **out)
     const size_t tp = std::max(packed_bytes(h->bmax, hidden), packed_bytes(hidden, h->bmax));
     alloc(&h->Tp1, tp);
     alloc(&h->Tp2, std::max(tp, packed_bytes(h->dinp, h->bmax)));
+    alloc((void **)&h->Xs, sizeof(float) * (size_t)h->bmax * h->din);
+    alloc((void **)&h->ts, sizeof(float) * h->bmax);
     if (e != cudaSuccess) {
         mlp_free(h);
         return cuda_fail(e, "surrogate allocation");
@@ -643,26 +693,44 @@ int pp_mlp_train_step(pp_mlp *h, const float *X, const float *t, int32_t B, floa
 }
 
 int pp_mlp_fit(pp_mlp *h, const float *X, const float *t, int32_t n, int32_t batch, int32_t epochs,
-               float lr0, float lr1, float *epoch_loss, void *stream)
+               float lr0, float lr1, uint64_t seed, float *epoch_loss, void *stream)
 {
     clear_error();
     if (!h || !X || !t || n < 1 || batch < 1 || batch > h->bmax || epochs < 1)
         return fail(PP_ERR_INVALID_ARG, "need a network, X and t, n >= 1, 1 <= batch <= max_batch, epochs >= 1");
     if (!(lr0 >= 0.0f) || !(lr1 >= 0.0f))
         return fail(PP_ERR_INVALID_ARG, "learning rates must be non-negative");
+    cudaStream_t st = (cudaStream_t)stream;
+    RowShuffle sh;
+    sh.n = n;
+    sh.hb = 0;
+    while ((1ll << (2 * sh.hb)) < (long long)n)
+        ++sh.hb;
     const long long per = (n + (long long)batch - 1) / batch, total = per * epochs;
     long long k = 0;
-    for (int e = 0; e < epochs; ++e)
+    for (int e = 0; e < epochs; ++e) {
+        for (int i = 0; i < 4; ++i)
+            sh.k[i] = mlp_sm64_at(seed, 4 * (uint64_t)e + (uint64_t)i);
         for (long long b = 0; b < per; ++b, ++k) {
             const int r0 = (int)(b * batch), rows = (int)std::min<long long>(batch, n - r0);
             // cosine schedule from lr0 (first step) to lr1 (last step)
             const double c = total > 1 ? 0.5 * (1.0 + cos(M_PI * (double)k / (double)(total - 1))) : 1.0;
             const float lr = (float)(lr1 + (lr0 - lr1) * c);
             float *loss = (epoch_loss && b == per - 1) ? epoch_loss + e : nullptr;
-            const int rc = pp_mlp_train_step(h, X + (size_t)r0 * h->din, t + r0, rows, lr, loss, stream);
+            const float *Xb = X + (size_t)r0 * h->din, *tb = t + r0;
+            if (seed != 0) {
+                gather_rows_kernel<<<rows, 64, 0, st>>>(X, t, h->din, sh, r0, rows, h->Xs, h->ts);
+                cudaError_t eg = cudaGetLastError();
+                if (eg != cudaSuccess)
+                    return cuda_fail(eg, "mini-batch gather");
+                Xb = h->Xs;
+                tb = h->ts;
+            }
+            const int rc = pp_mlp_train_step(h, Xb, tb, rows, lr, loss, stream);
             if (rc)
                 return rc;
         }
+    }
     return PP_OK;
 }
 

@@ -91,7 +91,7 @@ def run_de(pp, pop0, fit0, spec, grid, generations, seed, F, CR, net=None, R=8, 
 
     online = (every, epochs, batch, lr) refits the network on all trials the
     exact solver scored so far (plus `seen` = (features, N) scored before the run,
-    if given) every `every` generations; mode is the screening mode of
+    if given) every `every` generations, the rows reshuffled in every epoch; mode is the screening mode of
     pp_de_screened_step ("individual" or "global").  Stops early once the best N
     reaches `target` (if given).  Returns the best N after the initial population
     and after every generation, the exact-evaluation count at each of those
@@ -126,13 +126,10 @@ def run_de(pp, pop0, fit0, spec, grid, generations, seed, F, CR, net=None, R=8, 
                 if (g + 1) % every == 0:
                     X = torch.cat(seen_P)
                     t = lt.targets(pp, torch.cat(seen_N))
-                    perm = torch.randperm(X.shape[0], device=X.device,
-                                          generator=torch.Generator(device=X.device).manual_seed(g))
-                    X, t = X[perm].contiguous(), t[perm].contiguous()
                     before = mean_loss(pp, net, X, t)
                     torch.cuda.synchronize()
                     t_fit = time.perf_counter()
-                    net.fit(X, t, batch, epochs, lr, lr)
+                    net.fit(X, t, batch, epochs, lr, lr, seed=g + 1)  # rows reshuffled every epoch
                     torch.cuda.synchronize()
                     t_fit = time.perf_counter() - t_fit
                     refits.append({"generation": g, "rows": int(X.shape[0]), "loss_before": before,

@@ -117,7 +117,7 @@ def test_host_validation_of_the_extension_entry_points(pp):
     rc = L.pp_de_screened_step(P, P, 16, ctypes.byref(spec), ctypes.byref(grid), 0, 1, P, P, None,
                                0.8, 0.9, 1, 0, 8, 0, None, None, None, None, None, None)
     assert rc == pp.PP_ERR_INVALID_ARG and b"mlp" in L.pp_last_error()
-    rc = L.pp_mlp_fit(None, P, P, 10, 4, 1, 1e-3, 1e-4, None, None)
+    rc = L.pp_mlp_fit(None, P, P, 10, 4, 1, 1e-3, 1e-4, 0, None, None)
     assert rc == pp.PP_ERR_INVALID_ARG
     rc = L.pp_mlp_log_targets(P, 4, 0.0, 0.0, 1.0, P, None)
     assert rc == pp.PP_ERR_INVALID_ARG and b"floor" in L.pp_last_error()

@@ -87,6 +87,68 @@ def test_fit_reduces_loss(pp):
     net.close()
 
 
+M64 = (1 << 64) - 1
+
+
+def sm64(s, k):
+    """SplitMix64 output k of seed s (Steele, Lea, Flood 2014), restated for the test."""
+    z = (s + (k + 1) * 0x9E3779B97F4A7C15) & M64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M64
+    return z ^ (z >> 31)
+
+
+def epoch_order(n, seed, e):
+    """Row order of epoch e as pp.h defines it for pp_mlp_fit: a 4-round Feistel network
+    on b-bit integers (b even, 2^b >= n), applied again while the value is >= n."""
+    hb = 0
+    while (1 << (2 * hb)) < n:
+        hb += 1
+    mask = (1 << hb) - 1
+    keys = [sm64(seed, 4 * e + i) for i in range(4)]
+    out = []
+    for x in range(n):
+        while True:
+            L, R = x >> hb, x & mask
+            for k in keys:
+                L, R = R, L ^ (sm64(k, R) & mask)
+            x = (L << hb) | R
+            if x < n:
+                break
+        out.append(x)
+    return out
+
+
+@pytest.mark.parametrize("seed", [0, 99])
+def test_fit_visits_rows_in_the_documented_order(pp, seed):
+    # pp_mlp_fit equals pp_mlp_train_step on the rows of each slice gathered in the
+    # documented order (seed 0: as given), bit for bit; constant learning rate
+    n, batch, epochs, lr = 700, 128, 3, 1e-3
+    rng = np.random.default_rng(5)
+    X = torch.tensor(rng.uniform(-0.5, 0.5, (n, 32)), dtype=torch.float32, device="cuda")
+    t = torch.tensor(rng.normal(size=n), dtype=torch.float32, device="cuda")
+    a = pp.Surrogate(32, 128, max_batch=128)
+    b = pp.Surrogate(32, 128, max_batch=128)
+    a.init(4)
+    b.init(4)
+    a.fit(X, t, batch, epochs, lr, lr, seed=seed)
+    orders = []
+    for e in range(epochs):
+        order = list(range(n)) if seed == 0 else epoch_order(n, seed, e)
+        assert sorted(order) == list(range(n))
+        orders.append(order)
+        idx = torch.tensor(order, device="cuda")
+        for r0 in range(0, n, batch):
+            rows = idx[r0:r0 + batch]
+            b.train_step(X[rows].contiguous(), t[rows].contiguous(), lr)
+    assert pp.sync_status() == pp.PP_OK
+    assert torch.equal(a.get_params(), b.get_params())
+    if seed:
+        assert orders[0] != orders[1] and orders[0] != list(range(n))
+    a.close()
+    b.close()
+
+
 def test_one_proposal_is_plain_de(pp):
     lo, hi, per = bounds()
     pop0, fit0 = start(pp, 16, 21)
