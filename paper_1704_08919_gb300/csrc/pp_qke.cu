@@ -212,34 +212,37 @@ __device__ __forceinline__ double density(const T d[6])
     return (double)g <= kGrowthTol ? -(double)d[0] : __longlong_as_double(0x7ff8000000000000ll);
 }
 
-// the same values as sample_sens, from precomputed basics
+// The same values as sample_sens, from precomputed basics, with the terms
+// gathered per direction: writing dX/dP_a = 2 (P_a |E|^2 - (E.P) E_a) and
+// dX/dE_a = 2 (omega^2 E_a - (E.P) P_a), the chain rule through Q = sqrt(X)/omega^2,
+// R = eps_perp omega cr / X and omega gives
+//   dJ/dA_a  = -[ Qb hq dX/dP_a - Rb R (dX/dP_a / X) + beta P_a ],
+//   dJ/dE_a  =    Qb hq dX/dE_a - Rb R (dX/dE_a / X) + gam dcr/dE_a,
+//   dJ/dEd_a =    gam dcr/dEd_a,
+// with hq = dQ/dX = 1 / (2 sqrt(X) omega^2), gam = Rb eps_perp omega / X and
+// beta = wb / omega + Rb R / omega^2 - 2 Qb sqrt(X) / omega^4.  dX is divided by X
+// before it meets R (FP32 range near zeros of E).  Where X <= 0, rX = 0 makes
+// every Q and R term vanish, as in sample_sens.
 template <typename T>
 __device__ __forceinline__ void sens_from(const Basics<T> &b, const QkeS<T> &s, T eperp, const T ab[3], T out[6])
 {
     const T w = b.w2 * b.iw, iw2 = b.iw * b.iw;
+    const T sX = b.X * b.rX, iX = b.rX * b.rX;
+    const T Qb = ab[0], Rb = ab[1], wb = ab[2];
+    const T ewX = eperp * w * iX;     // R / cr
+    const T RbR = Rb * (ewX * s.cr);  // Rb R
+    const T Qh = Qb * (T(0.5) * b.rX * iw2);
+    const T gam = Rb * ewX;
+    const T beta = (wb * b.iw + RbR * iw2) - T(2) * Qb * sX * (iw2 * iw2);
     const T P[2] = {b.Px, b.Py}, E[2] = {s.ex, s.ey};
     const T dcr_dE[2] = {s.edy, -s.edx}, dcr_dEd[2] = {-s.ey, s.ex};
-    const T Qb = ab[0], Rb = ab[1], wb = ab[2];
-    const bool pos = b.X > T(0);
-    const T sX = b.X * b.rX, iX = b.rX * b.rX;
-    const T hq = T(0.5) * b.rX * iw2;
-    const T cx = s.cr * iX;
 #pragma unroll
     for (int a = 0; a < 2; ++a) {
-        const T dw_dP = P[a] * b.iw;
-        T dQ_dP = 0, dQ_dE = 0, dR_dP = 0, dR_dE = 0, dR_dEd = 0;
-        if (pos) {
-            const T dX_dP = T(2) * P[a] * s.ee - T(2) * b.EP * E[a];
-            const T dX_dE = T(2) * b.w2 * E[a] - T(2) * b.EP * P[a];
-            dQ_dP = dX_dP * hq - sX * T(2) * P[a] * (iw2 * iw2);
-            dQ_dE = dX_dE * hq;
-            dR_dP = eperp * cx * (dw_dP - w * (dX_dP * iX));
-            dR_dE = eperp * w * iX * (dcr_dE[a] - s.cr * (dX_dE * iX));
-            dR_dEd = eperp * w * dcr_dEd[a] * iX;
-        }
-        out[a] = -((Qb * dQ_dP + Rb * dR_dP) + wb * dw_dP);
-        out[2 + a] = Qb * dQ_dE + Rb * dR_dE;
-        out[4 + a] = Rb * dR_dEd;
+        const T dXP = T(2) * (P[a] * s.ee - b.EP * E[a]);
+        const T dXE = T(2) * (b.w2 * E[a] - b.EP * P[a]);
+        out[a] = -((Qh * dXP - RbR * (dXP * iX)) + beta * P[a]);
+        out[2 + a] = (Qh * dXE - RbR * (dXE * iX)) + gam * dcr_dE[a];
+        out[4 + a] = gam * dcr_dEd[a];
     }
 }
 
