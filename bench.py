@@ -634,12 +634,10 @@ def large_main(args):
         snap_pop, snap_fit, snap_w = pop.clone(), fit.clone(), net.get_params().clone()
         Xs = torch.cat(seen_X)
         ts = lt.targets(pp, torch.cat(seen_N))
-        perm = torch.randperm(Xs.shape[0], device="cuda", generator=torch.Generator(device="cuda").manual_seed(G))
-        Xs, ts = Xs[perm].contiguous(), ts[perm].contiguous()
         loss_before = scr.mean_loss(pp, net, Xs, ts)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        net.fit(Xs, ts, 256, args.refit_epochs, 2e-4, 2e-4)
+        net.fit(Xs, ts, 256, args.refit_epochs, 2e-4, 2e-4, seed=G + 1)  # rows reshuffled every epoch
         torch.cuda.synchronize()
         refit_s = time.perf_counter() - t0
         loss_after = scr.mean_loss(pp, net, Xs, ts)
