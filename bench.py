@@ -42,8 +42,8 @@ WORK = {("fp32", "rk4"): (268, 184), ("fp32", "magnus4"): (138, 96), ("fp32", "s
         ("fp32fast", "split2"): (112, 64),
         ("fp64", "rk4"): (244, 148), ("fp64", "magnus4"): (114, 64), ("fp64", "split2"): (112, 64)}
 # DRAM bytes per candidate per launch of the propagation kernel, from ncu captures
-# (profiles/): the FP32-fast Magnus kernel (256 threads, 8 KiB tiles) read 1.088512 MB for 4 candidates.
-TRAFFIC_PER_CAND = {("fp32fast", "magnus4"): 1.088512e6 / 4}
+# (profiles/): the FP32-fast Magnus kernel (256 threads, 8 KiB tiles) read 1.106944 MB for 4 candidates.
+TRAFFIC_PER_CAND = {("fp32fast", "magnus4"): 1.106944e6 / 4}
 FP32_LANES_PER_SM = 128
 # GB300 FP64 rate from the part's datasheet figure (no measured FP64 peak exists
 # for this pool); FP32 is derived from the device's SM count and maximum clock.
@@ -471,11 +471,11 @@ def gemm_measure(pp, torch, reps=20):
 
 
 # FP32 work per mode-step of the QKE adjoint kernel (forward pass, recomputed
-# forward and backward step), from the kernel's executed SASS counts (ncu,
-# 1.342e8 mode-steps): 288 FFMA + 296 FMUL + 128 FADD thread-instructions,
-# i.e. 1000 flop (FMA = 2) in 712 FP32 instructions.
-QKE_ADJ_FLOP = 1000
-QKE_ADJ_FP32_INSTR = 712
+# forward and backward step), from the kernel's executed instruction counts (ncu,
+# 7 starts x 16384 modes x 4096 steps): 283.4 FFMA + 263.9 FMUL + 128.6 FADD
+# thread-instructions, i.e. 959 flop (FMA = 2) in 676 FP32 instructions.
+QKE_ADJ_FLOP = 959
+QKE_ADJ_FP32_INSTR = 676
 
 
 def localsearch_main(args):
@@ -507,6 +507,9 @@ def localsearch_main(args):
         pp.qke_gradient(Xd, sp, L["grid"], prec)
     st = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
     torch.cuda.synchronize()
     e0.record(st)
     reps = 3
@@ -517,8 +520,6 @@ def localsearch_main(args):
     eval_ms = e0.elapsed_time(e1) / reps
     g = L["grid"]
     mode_steps = g["nx"] * g["ny"] * g["nz"] * L["n_steps"] * S
-    clocks = ClockSampler(local)
-    clocks.start()
     t0 = time.perf_counter()
     if args.eval_only:
         r = None
@@ -1055,7 +1056,7 @@ def main():
         "traffic": (TRAFFIC_PER_CAND[(args.precision, args.scheme)] * NP
                     if (args.precision, args.scheme) in TRAFFIC_PER_CAND else None),
         "traffic_source": ("dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of this kernel "
-                           "at 4 candidates (1.089 MB, nothing written), scaled by candidates: the "
+                           "at 4 candidates (1.107 MB, nothing written), scaled by candidates: the "
                            "per-candidate step table is read from DRAM once, every other access hits L2"
                            if (args.precision, args.scheme) in TRAFFIC_PER_CAND else None)}
 

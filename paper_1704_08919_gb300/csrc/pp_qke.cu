@@ -377,15 +377,22 @@ __global__ void __launch_bounds__(kQThreads) qke_forward_kernel(const QkeS<T> *_
 
 // Forward with checkpoints, then the backward sweep segment by segment.
 // ckpt[c][seg][6][nmp] (T), part[c][blk][6][ldg] (FP64), partJ[c][blk].
+// Segments of S steps are handled in groups of kQGroup: the samples of a group are
+// staged into shared memory once, and the sample sensitivities of a whole group
+// are summed over the CTA's warps once, so a group of kQGroup S steps costs four
+// barriers.  FP32: 2 CTAs per SM with up to 128 registers (no spills; 3 CTAs per
+// SM at 80 registers spilled in the backward step and measured 2.9% slower).
+constexpr int kQGroup = 4;
 template <typename T, int S>
-__global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 3 : 1) qke_adjoint_kernel(const QkeS<T> *__restrict__ tab, int ldt, int n_steps,
+__global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 2 : 1) qke_adjoint_kernel(const QkeS<T> *__restrict__ tab, int ldt, int n_steps,
                                                                 double dt_d, pp_grid g, T *__restrict__ ckpt, int nmp,
                                                                 double *__restrict__ part, int ldg,
                                                                 double *__restrict__ partJ)
 {
+    constexpr int GS = kQGroup * S;  // steps per group
     __shared__ double red[kQWarps];
-    __shared__ double sb[kQWarps][2 * S][6];
-    __shared__ QkeS<T> seg[2 * S + 1];  // the samples of the current segment (broadcast reads)
+    __shared__ double sb[kQWarps][2 * GS][6];
+    __shared__ QkeS<T> seg[2 * GS + 1];  // the samples of the current group (broadcast reads)
     // the segment's recomputed states, one slot per thread: sst[(q * 6 + i) * kQThreads + tid]
     extern __shared__ __align__(16) unsigned char qke_dyn[];
     T *sst = reinterpret_cast<T *>(qke_dyn);
@@ -401,27 +408,31 @@ __global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 3 : 1) qke_adjoint
     T *ck = ckpt + (size_t)c * nseg * 6 * nmp;
     auto stage = [&](int n0, int cnt) {  // samples 2 n0 .. 2 (n0 + cnt) into shared memory
         __syncthreads();
-        if (threadIdx.x < 2 * cnt + 1)
-            seg[threadIdx.x] = tr[2 * n0 + threadIdx.x];
+        for (int k = threadIdx.x; k < 2 * cnt + 1; k += kQThreads)
+            seg[k] = tr[2 * n0 + k];
         __syncthreads();
     };
+    const int ngrp = (nseg + kQGroup - 1) / kQGroup;
 
     // ---- phase A: forward, keeping the state at the start of every segment
     T d[6] = {0, 0, 0, 0, 0, 0};
     {
         Coef<T> c0 = coef_at(tr[0], px, py, pz2, eperp);
-        for (int s = 0; s < nseg; ++s) {
-            if (mg.active)
+        for (int gr = 0; gr < ngrp; ++gr) {
+            const int g0 = gr * kQGroup, n0g = g0 * S;
+            stage(n0g, min(GS, n_steps - n0g));
+            for (int s = g0; s < min(g0 + kQGroup, nseg); ++s) {
+                if (mg.active)
 #pragma unroll
-                for (int i = 0; i < 6; ++i)
-                    ck[((size_t)s * 6 + i) * nmp + mm] = d[i];
-            const int n0 = s * S, cnt = min(S, n_steps - n0);
-            stage(n0, cnt);
-            for (int q = 0; q < cnt; ++q) {
-                const Coef<T> ch = coef_at(seg[2 * q + 1], px, py, pz2, eperp);
-                const Coef<T> c1 = coef_at(seg[2 * q + 2], px, py, pz2, eperp);
-                rk4_step(d, c0, ch, c1, dt);
-                c0 = c1;
+                    for (int i = 0; i < 6; ++i)
+                        ck[((size_t)s * 6 + i) * nmp + mm] = d[i];
+                const int so = (s - g0) * S, cnt = min(S, n_steps - s * S);
+                for (int q = 0; q < cnt; ++q) {
+                    const Coef<T> ch = coef_at(seg[2 * (so + q) + 1], px, py, pz2, eperp);
+                    const Coef<T> c1 = coef_at(seg[2 * (so + q) + 2], px, py, pz2, eperp);
+                    rk4_step(d, c0, ch, c1, dt);
+                    c0 = c1;
+                }
             }
         }
     }
@@ -436,111 +447,117 @@ __global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 3 : 1) qke_adjoint
     T bar[6] = {(T)(-mg.w), 0, 0, 0, 0, 0};
     T pend[3] = {0, 0, 0};  // coefficient adjoints of the sample at the top of the next step
     Coef<T> c1 = coef_at(tr[2 * n_steps], px, py, pz2, eperp);
-    for (int s = nseg - 1; s >= 0; --s) {
-        const int n0 = s * S, cnt = min(S, n_steps - n0);
+    Basics<T> b1 = basics(tr[2 * n_steps], px, py, pz2);  // of the sample at the top of the step
+    for (int gr = ngrp - 1; gr >= 0; --gr) {
+        const int g0 = gr * kQGroup, n0g = g0 * S, cntg = min(GS, n_steps - n0g);
+        stage(n0g, cntg);
+        for (int s = min(g0 + kQGroup, nseg) - 1; s >= g0; --s) {
+            const int so = (s - g0) * S, cnt = min(S, n_steps - s * S);
 #pragma unroll
-        for (int i = 0; i < 6; ++i)
-            d[i] = mg.active ? ck[((size_t)s * 6 + i) * nmp + mm] : T(0);
-        stage(n0, cnt);
-        {
-            Coef<T> c0 = coef_at(seg[0], px, py, pz2, eperp);
-#pragma unroll 1
-            for (int q = 0; q < cnt; ++q) {
-#pragma unroll
-                for (int i = 0; i < 6; ++i)
-                    sst[(q * 6 + i) * kQThreads + threadIdx.x] = d[i];
-                const Coef<T> ch = coef_at(seg[2 * q + 1], px, py, pz2, eperp);
-                const Coef<T> cn = coef_at(seg[2 * q + 2], px, py, pz2, eperp);
-                rk4_step(d, c0, ch, cn, dt);
-                c0 = cn;
-            }
-        }
-#pragma unroll 1
-        for (int q = cnt - 1; q >= 0; --q) {
+            for (int i = 0; i < 6; ++i)
+                d[i] = mg.active ? ck[((size_t)s * 6 + i) * nmp + mm] : T(0);
             {
-                const QkeS<T> e0 = seg[2 * q], eh = seg[2 * q + 1], e1 = seg[2 * q + 2];
-                const Basics<T> bh = basics(eh, px, py, pz2);
-                const Coef<T> c0 = coef_at(e0, px, py, pz2, eperp);
-                const Coef<T> ch = coef_from(bh, eh, eperp);
-                T x[6];
+                Coef<T> c0 = coef_at(seg[2 * so], px, py, pz2, eperp);
+#pragma unroll 1
+                for (int q = 0; q < cnt; ++q) {
 #pragma unroll
-                for (int i = 0; i < 6; ++i)
-                    x[i] = sst[(q * 6 + i) * kQThreads + threadIdx.x];
-                T k1[6], k2[6], k3[6], y2[6], y3[6], y4[6];
-                nmul(c0, x, T(1), k1);
-#pragma unroll
-                for (int i = 0; i < 6; ++i)
-                    y2[i] = x[i] + hd * k1[i];
-                nmul(ch, y2, T(1), k2);
-#pragma unroll
-                for (int i = 0; i < 6; ++i)
-                    y3[i] = x[i] + hd * k2[i];
-                nmul(ch, y3, T(1), k3);
-#pragma unroll
-                for (int i = 0; i < 6; ++i)
-                    y4[i] = x[i] + dt * k3[i];
-                T kb1[6], kb2[6], kb3[6], kb4[6], xb[6], yb[6];
-#pragma unroll
-                for (int i = 0; i < 6; ++i) {
-                    kb1[i] = sx * bar[i];
-                    kb2[i] = T(2) * sx * bar[i];
-                    kb3[i] = kb2[i];
-                    kb4[i] = kb1[i];
-                    xb[i] = bar[i];
+                    for (int i = 0; i < 6; ++i)
+                        sst[(q * 6 + i) * kQThreads + threadIdx.x] = d[i];
+                    const Coef<T> ch = coef_at(seg[2 * (so + q) + 1], px, py, pz2, eperp);
+                    const Coef<T> cn = coef_at(seg[2 * (so + q) + 2], px, py, pz2, eperp);
+                    rk4_step(d, c0, ch, cn, dt);
+                    c0 = cn;
                 }
-                // k4 = N1 (e1 + y4): completes the sample 2n+2
-                coef_adj(kb4, y4, pend);
-                nmul(c1, kb4, T(0), yb);
+            }
+#pragma unroll 1
+            for (int q = cnt - 1; q >= 0; --q) {
+                {
+                    const QkeS<T> e0 = seg[2 * (so + q)], eh = seg[2 * (so + q) + 1], e1 = seg[2 * (so + q) + 2];
+                    const Basics<T> bh = basics(eh, px, py, pz2);
+                    const Basics<T> b0 = basics(e0, px, py, pz2);
+                    const Coef<T> c0 = coef_from(b0, e0, eperp);
+                    const Coef<T> ch = coef_from(bh, eh, eperp);
+                    T x[6];
 #pragma unroll
-                for (int i = 0; i < 6; ++i) {
-                    xb[i] -= yb[i];
-                    kb3[i] -= dt * yb[i];
+                    for (int i = 0; i < 6; ++i)
+                        x[i] = sst[(q * 6 + i) * kQThreads + threadIdx.x];
+                    T k1[6], k2[6], k3[6], y2[6], y3[6], y4[6];
+                    nmul(c0, x, T(1), k1);
+#pragma unroll
+                    for (int i = 0; i < 6; ++i)
+                        y2[i] = x[i] + hd * k1[i];
+                    nmul(ch, y2, T(1), k2);
+#pragma unroll
+                    for (int i = 0; i < 6; ++i)
+                        y3[i] = x[i] + hd * k2[i];
+                    nmul(ch, y3, T(1), k3);
+#pragma unroll
+                    for (int i = 0; i < 6; ++i)
+                        y4[i] = x[i] + dt * k3[i];
+                    T kb1[6], kb2[6], kb3[6], kb4[6], xb[6], yb[6];
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) {
+                        kb1[i] = sx * bar[i];
+                        kb2[i] = T(2) * sx * bar[i];
+                        kb3[i] = kb2[i];
+                        kb4[i] = kb1[i];
+                        xb[i] = bar[i];
+                    }
+                    // k4 = N1 (e1 + y4): completes the sample 2n+2
+                    coef_adj(kb4, y4, pend);
+                    nmul(c1, kb4, T(0), yb);
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) {
+                        xb[i] -= yb[i];
+                        kb3[i] -= dt * yb[i];
+                    }
+                    T hacc[3] = {0, 0, 0};
+                    coef_adj(kb3, y3, hacc);  // k3 = Nh (e1 + y3)
+                    nmul(ch, kb3, T(0), yb);
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) {
+                        xb[i] -= yb[i];
+                        kb2[i] -= hd * yb[i];
+                    }
+                    coef_adj(kb2, y2, hacc);  // k2 = Nh (e1 + y2)
+                    nmul(ch, kb2, T(0), yb);
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) {
+                        xb[i] -= yb[i];
+                        kb1[i] -= hd * yb[i];
+                    }
+                    T nacc[3] = {0, 0, 0};
+                    coef_adj(kb1, x, nacc);  // k1 = N0 (e1 + x)
+                    nmul(c0, kb1, T(0), yb);
+#pragma unroll
+                    for (int i = 0; i < 6; ++i)
+                        bar[i] = xb[i] - yb[i];
+                    // emit samples 2n+2 (values 0..5, slot 2q+1) and 2n+1 (values 6..11, slot 2q)
+                    T o[16];
+                    sens_from(b1, e1, eperp, pend, o);
+                    sens_from(bh, eh, eperp, hacc, o + 6);
+#pragma unroll
+                    for (int i = 12; i < 16; ++i)
+                        o[i] = T(0);
+                    const T tot = warp_sum16(o, lane);
+                    const int vi = (lane >> 1) & 15;
+                    if ((lane & 1) == 0 && vi < 12)
+                        sb[warp][vi < 6 ? 2 * (so + q) + 1 : 2 * (so + q)][vi < 6 ? vi : vi - 6] = (double)tot;
+#pragma unroll
+                    for (int i = 0; i < 3; ++i)
+                        pend[i] = nacc[i];
+                    c1 = c0;
+                    b1 = b0;
                 }
-                T hacc[3] = {0, 0, 0};
-                coef_adj(kb3, y3, hacc);  // k3 = Nh (e1 + y3)
-                nmul(ch, kb3, T(0), yb);
-#pragma unroll
-                for (int i = 0; i < 6; ++i) {
-                    xb[i] -= yb[i];
-                    kb2[i] -= hd * yb[i];
-                }
-                coef_adj(kb2, y2, hacc);  // k2 = Nh (e1 + y2)
-                nmul(ch, kb2, T(0), yb);
-#pragma unroll
-                for (int i = 0; i < 6; ++i) {
-                    xb[i] -= yb[i];
-                    kb1[i] -= hd * yb[i];
-                }
-                T nacc[3] = {0, 0, 0};
-                coef_adj(kb1, x, nacc);  // k1 = N0 (e1 + x)
-                nmul(c0, kb1, T(0), yb);
-#pragma unroll
-                for (int i = 0; i < 6; ++i)
-                    bar[i] = xb[i] - yb[i];
-                // emit samples 2n+2 (values 0..5, slot 2q+1) and 2n+1 (values 6..11, slot 2q)
-                T o[16];
-                sens_from(basics(e1, px, py, pz2), e1, eperp, pend, o);
-                sens_from(bh, eh, eperp, hacc, o + 6);
-#pragma unroll
-                for (int i = 12; i < 16; ++i)
-                    o[i] = T(0);
-                const T tot = warp_sum16(o, lane);
-                const int vi = (lane >> 1) & 15;
-                if ((lane & 1) == 0 && vi < 12)
-                    sb[warp][vi < 6 ? 2 * q + 1 : 2 * q][vi < 6 ? vi : vi - 6] = (double)tot;
-#pragma unroll
-                for (int i = 0; i < 3; ++i)
-                    pend[i] = nacc[i];
-                c1 = c0;
             }
         }
         __syncthreads();
-        for (int t = threadIdx.x; t < 2 * cnt * 6; t += kQThreads) {
-            const int i = t / (2 * cnt), kk = t % (2 * cnt);
+        for (int t = threadIdx.x; t < 2 * cntg * 6; t += kQThreads) {
+            const int i = t / (2 * cntg), kk = t % (2 * cntg);
             double acc = 0.0;
             for (int w = 0; w < kQWarps; ++w)
                 acc += sb[w][kk][i];
-            prow[(size_t)i * ldg + 2 * n0 + 1 + kk] = acc;
+            prow[(size_t)i * ldg + 2 * n0g + 1 + kk] = acc;
         }
         __syncthreads();
     }
