@@ -78,6 +78,8 @@ def parse():
                     help="localsearch: time the batched gradient evaluation only (no search)")
     ap.add_argument("--small", action="store_true",
                     help="localsearch: a 16 x 16 x 8 grid (profiling runs)")
+    ap.add_argument("--qke-steps", type=int, default=None,
+                    help="localsearch: RK4 steps per pulse instead of the workload's 16384 (profiling runs)")
     ap.add_argument("--screen", default="individual", choices=["individual", "global"],
                     help="surrogate: screening mode reported as the value")
     ap.add_argument("--online", type=int, default=0,
@@ -472,10 +474,10 @@ def gemm_measure(pp, torch, reps=20):
 
 # FP32 work per mode-step of the QKE adjoint kernel (forward pass, recomputed
 # forward and backward step), from the kernel's executed instruction counts (ncu,
-# 7 starts x 16384 modes x 4096 steps): 283.4 FFMA + 263.9 FMUL + 128.6 FADD
-# thread-instructions, i.e. 959 flop (FMA = 2) in 676 FP32 instructions.
-QKE_ADJ_FLOP = 959
-QKE_ADJ_FP32_INSTR = 676
+# 7 starts x 16384 modes x 4096 steps): 278.4 FFMA + 252.6 FMUL + 125.6 FADD
+# thread-instructions, i.e. 935 flop (FMA = 2) in 657 FP32 instructions.
+QKE_ADJ_FLOP = 935
+QKE_ADJ_FP32_INSTR = 657
 
 
 def localsearch_main(args):
@@ -489,6 +491,8 @@ def localsearch_main(args):
         return 0
     torch.cuda.set_device(local)
     pp.lib()
+    if args.qke_steps:
+        L = dict(L, n_steps=args.qke_steps)
     sp = inputs.field_spec(dict(L, fluence=1.0))
     K = L["K"]
     S = args.ncand if args.ncand != CFG["NP"] else L["nstart"]
@@ -1180,6 +1184,8 @@ def main():
                              "per generation; one allgather of the %d pair numbers (NCCL) per generation"
                              % (NP_total, ws, NP, NP_total)} if ws > 1 else {})),
             "mode_steps_per_s": mode_steps_per_s,
+            # a mode-step advances both spin channels of one momentum mode
+            "mode_spin_steps_per_s": 2.0 * mode_steps_per_s,
             "n_rel_err_vs_fp64_rk4_max": rel_err,
             "n_rel_err_vs_oracle": oracle_check["n_rel_err_vs_oracle"] if oracle_check else None,
             "oracle_check": oracle_check,
