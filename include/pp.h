@@ -156,9 +156,9 @@ int pp_synth_field(const double *params, int32_t ncand, const pp_field_spec *spe
  *  n_steps (host)   [ncand] steps per candidate (each 2 n_steps[c] + 1 <= ld), or
  *                   NULL: every candidate takes (ld - 1) / 2 steps.
  *  dt      step size (> 0).
- *  grid    (host)   momentum grid shared by all candidates.  (This entry point takes
- *                   one grid; candidates with grids of their own, and their own pulse
- *                   lengths, are scored together by pp_batch_pair_number.)
+ *  grid    (host)   momentum grid shared by all candidates (a grid per candidate:
+ *                   pp_pair_number_grids; with pulse models per candidate as well:
+ *                   the pp_batch_* calls).
  *  precision PP_FP64, PP_FP32 or PP_FP32_FAST.
  *  scheme  PP_RK4, PP_MAGNUS4 or PP_SPLIT2.
  *  N       (device) [ncand] FP64 output.
@@ -169,6 +169,23 @@ int pp_synth_field(const double *params, int32_t ncand, const pp_field_spec *spe
 int pp_pair_number(const double *A, int32_t ncand, int32_t ld, const int32_t *n_steps, double dt,
                    const pp_grid *grid, int32_t precision, int32_t scheme, double *N, double *n_p,
                    void *stream);
+
+/* Pair numbers with a momentum grid per candidate: pp_pair_number's arguments
+ * with grids (host) [n_grids] and n_grids = 1 (one grid shared by all candidates:
+ * exactly pp_pair_number) or n_grids = ncand (candidate c on grids[c]).  Per-
+ * candidate grids run as one persistent launch of the uneven-batch kernel
+ * (pp_batch_pair_number): CTAs take (candidate, block of modes) items, longest
+ * candidates first; N[c] is bitwise what pp_pair_number gives for candidate c on
+ * its own grid, and n_p (device, or NULL) holds the candidates' n(p) arrays
+ * concatenated in candidate order (candidate c's nz*ny*nx values, x fastest).  The
+ * descriptors, work list, step tables and partial sums live in library scratch
+ * (grown with cudaMalloc on demand); the descriptors are copied from host memory
+ * on `stream` in the call.  The launch configuration is the batch kernel's default
+ * for the precision and scheme.  Errors: as pp_pair_number, and INVALID_ARG when
+ * n_grids is neither 1 nor ncand or a grid is invalid (its index named). */
+int pp_pair_number_grids(const double *A, int32_t ncand, int32_t ld, const int32_t *n_steps, double dt,
+                         const pp_grid *grids, int32_t n_grids, int32_t precision, int32_t scheme, double *N,
+                         double *n_p, void *stream);
 
 /* Launch-configuration tuner of the propagation kernel.  FP32 paths can run the
  * kernel with pp_num_launch_configs() launch configurations (threads per CTA x

@@ -49,7 +49,7 @@ EXPORTS = ("pp_synth_field", "pp_pair_number", "pp_de_propose", "pp_de_select", 
            "pp_mlp_train_step", "pp_mlp_features", "pp_de_screened_step", "pp_mlp_fit",
            "pp_mlp_log_targets", "pp_mlp_init", "pp_al_search", "pp_synth_field_raw",
            "pp_synth_vjp", "pp_qke_pair_number", "pp_qke_sample_gradient", "pp_qke_gradient",
-           "pp_local_search", "pp_release_scratch")
+           "pp_local_search", "pp_release_scratch", "pp_pair_number_grids")
 
 
 class ALOptions(ctypes.Structure):
@@ -116,6 +116,7 @@ def lib():
         L.pp_launch_config.argtypes = [_i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]
         L.pp_clear_tuning.restype = None
         L.pp_pair_number_static.argtypes = L.pp_pair_number.argtypes
+        L.pp_pair_number_grids.argtypes = [_vp, _i32, _i32, _vp, _d, _vp, _i32, _i32, _i32, _vp, _vp, _vp]
         L.pp_static_scratch_bytes.restype = ctypes.c_size_t
         L.pp_batch_create.argtypes = [_i32, ctypes.POINTER(FieldSpec), ctypes.POINTER(Grid), _i32,
                                       _i32, _d, ctypes.POINTER(_vp)]
@@ -260,6 +261,26 @@ def pair_number_static(A, dt, grid, precision="fp32", n_steps=None, want_n=False
     _check(lib().pp_pair_number_static(_ptr(A), ncand, ld, ns, float(dt), ctypes.byref(g),
                                        PRECISIONS[precision], SCHEMES[scheme], _ptr(N), _ptr(n),
                                        _stream(stream)))
+    return N, n
+
+
+def pair_number_grids(A, dt, grids, precision="fp32", n_steps=None, want_n=False, stream=None, scheme="rk4"):
+    """pp_pair_number_grids: A [ncand, 2, ld] float64 CUDA and a grid per candidate (or one) ->
+    N [ncand] (and n, the candidates' n(p) concatenated, 1-D)."""
+    import torch
+    gs = [_grid(g) for g in grids]
+    ncand, _, ld = A.shape
+    arr = (Grid * len(gs))(*gs)
+    N = torch.empty(ncand, dtype=torch.float64, device=A.device)
+    nmodes = [g.nx * g.ny * g.nz for g in gs] if len(gs) == ncand else [gs[0].nx * gs[0].ny * gs[0].nz] * ncand
+    n = torch.empty(sum(nmodes), dtype=torch.float64, device=A.device) if want_n else None
+    ns = None
+    if n_steps is not None:
+        nsa = (ctypes.c_int32 * ncand)(*[int(x) for x in n_steps])
+        ns = ctypes.cast(nsa, ctypes.c_void_p)
+    _check(lib().pp_pair_number_grids(_ptr(A), ncand, ld, ns, float(dt), ctypes.cast(arr, ctypes.c_void_p),
+                                      len(gs), PRECISIONS[precision], SCHEMES[scheme], _ptr(N), _ptr(n),
+                                      _stream(stream)))
     return N, n
 
 

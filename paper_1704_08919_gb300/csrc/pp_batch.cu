@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <map>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "pp_policies.cuh"
@@ -666,3 +667,112 @@ int pp_batch_de_run(pp_batch *b, double *pop, double *fit, const double *lo, con
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- per-candidate grids
+// pp_pair_number with a grid per candidate: one persistent launch of the batch
+// kernel over (candidate, block of modes) items, longest first, with the
+// descriptors, work list, step tables and partial sums in library scratch.
+int pp_pair_number_grids(const double *A, int32_t ncand, int32_t ld, const int32_t *n_steps, double dt,
+                         const pp_grid *grids, int32_t n_grids, int32_t precision, int32_t scheme, double *N,
+                         double *n_p, void *stream)
+{
+    clear_error();
+    if (n_grids == 1)
+        return pp_pair_number(A, ncand, ld, n_steps, dt, grids, precision, scheme, N, n_p, stream);
+    if (ncand < 0 || ncand > 65535)
+        return fail(PP_ERR_INVALID_ARG, "ncand must be in [0, 65535]");
+    if (n_grids != ncand)
+        return fail(PP_ERR_INVALID_ARG, "n_grids (%d) must be 1 or ncand (%d)", n_grids, ncand);
+    if (ncand == 0)
+        return PP_OK;
+    if (!A || !N || !grids)
+        return fail(PP_ERR_INVALID_ARG, "A, N and grids must not be NULL");
+    if (!(dt > 0.0) || !isfinite(dt))
+        return fail(PP_ERR_INVALID_ARG, "dt must be positive and finite");
+    if (precision != PP_FP64 && precision != PP_FP32 && precision != PP_FP32_FAST)
+        return fail(PP_ERR_INVALID_ARG, "precision must be PP_FP64, PP_FP32 or PP_FP32_FAST");
+    if (scheme != PP_RK4 && scheme != PP_MAGNUS4 && scheme != PP_SPLIT2)
+        return fail(PP_ERR_INVALID_ARG, "scheme must be PP_RK4, PP_MAGNUS4 or PP_SPLIT2");
+    if (ld < 3)
+        return fail(PP_ERR_INVALID_ARG, "ld must be >= 3");
+    for (int c = 0; c < ncand; ++c) {
+        if (check_grid(grids + c)) {
+            const std::string why = pp_last_error();
+            return fail(PP_ERR_INVALID_ARG, "candidate %d: %s", c, why.c_str());
+        }
+        const long long ns = n_steps ? n_steps[c] : (ld - 1) / 2;
+        if (ns < 1 || 2 * ns + 1 > ld)
+            return fail(PP_ERR_INVALID_ARG, "candidate %d: n_steps %lld needs 2 n_steps + 1 <= ld (%d)", c, ns, ld);
+    }
+    const BatchTable &tab = batch_table(precision, scheme);
+    const int cfg = tab.default_cfg;
+    const int threads = kBCfgThreads[cfg];
+    const int row_quantum = 32768 / tab.entry_bytes;
+    std::vector<BatchCand> hc(ncand);
+    std::vector<int> order(ncand);
+    long long toff = 0, noff = 0, poff = 0;
+    int max_padded = 0;
+    for (int c = 0; c < ncand; ++c) {
+        const int ns = n_steps ? n_steps[c] : (ld - 1) / 2;
+        const int padded = ((ns + row_quantum - 1) / row_quantum) * row_quantum;
+        const long long nm = (long long)grids[c].nx * grids[c].ny * grids[c].nz;
+        max_padded = std::max(max_padded, padded);
+        hc[c].g = grids[c];
+        hc[c].ns = ns;
+        hc[c].ngroups = (int)((nm + kGroup - 1) / kGroup);
+        hc[c].table_off = toff;
+        hc[c].n_off = noff;
+        hc[c].part_off = poff;
+        toff += padded;
+        noff += nm;
+        poff += hc[c].ngroups;
+        order[c] = c;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int z) { return hc[a].ns > hc[z].ns; });
+    std::vector<int2> work;
+    for (int c : order) {
+        const long long nm = (long long)grids[c].nx * grids[c].ny * grids[c].nz;
+        for (int blk = 0; blk < (int)((nm + threads - 1) / threads); ++blk)
+            work.push_back(make_int2(c, blk));
+    }
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t o_work = al(sizeof(BatchCand) * ncand);
+    const size_t o_table = o_work + al(sizeof(int2) * work.size());
+    const size_t o_part = o_table + al((size_t)toff * tab.entry_bytes);
+    const size_t o_count = o_part + al(sizeof(double) * (size_t)poff);
+    const size_t total = o_count + al(sizeof(int) * (2 + (size_t)ncand));
+    void *base = nullptr;
+    int rc = scratch(SCR_GRIDS, total, &base);
+    if (rc)
+        return rc;
+    char *b = (char *)base;
+    cudaStream_t st = (cudaStream_t)stream;
+    // from pageable host memory: each call returns once its source has been staged
+    cudaError_t e = cudaMemcpyAsync(b, hc.data(), sizeof(BatchCand) * ncand, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b + o_work, work.data(), sizeof(int2) * work.size(), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "grid descriptors");
+    int dev = 0, sms = 0, blocks = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return fail(PP_ERR_CUDA, "multiprocessor count");
+    if ((rc = tab.occ[cfg](&blocks)))
+        return rc;
+    BatchLaunch L;
+    L.A = A;
+    L.ld = ld;
+    L.cands = (const BatchCand *)b;
+    L.work = (const int2 *)(b + o_work);
+    L.nwork = (int)work.size();
+    L.counter = (int *)(b + o_count);
+    L.table = b + o_table;
+    L.row_quantum = row_quantum;
+    L.ncand = ncand;
+    L.max_padded = max_padded;
+    L.dt = dt;
+    L.n_p = n_p;
+    L.partial = (double *)(b + o_part);
+    L.N = N;
+    L.grid_ctas = std::max(1, std::min((int)work.size(), sms * std::max(blocks, 1)));
+    return tab.run[cfg](L, st);
+}

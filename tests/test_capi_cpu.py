@@ -125,6 +125,28 @@ def test_host_validation_of_the_extension_entry_points(pp):
     assert rc == pp.PP_ERR_INVALID_ARG
 
 
+def test_per_candidate_grids_are_checked_on_the_host(pp):
+    L = pp.lib()
+    good = pp.Grid(4, 4, 4, -1, 1, -1, 1, 0, 1, 1)
+    bad = pp.Grid(4, 4, 4, -1, 1, -1, 1, 0.5, 1, 1)  # mirror_z needs z0 = 0
+    arr = (pp.Grid * 3)(good, good, good)
+    P = ctypes.c_void_p(8)
+    rc = L.pp_pair_number_grids(P, 2, 101, None, 0.1, ctypes.cast(arr, ctypes.c_void_p), 3, 0, 0, P, None, None)
+    assert rc == pp.PP_ERR_INVALID_ARG and b"n_grids" in L.pp_last_error()
+    arr = (pp.Grid * 3)(good, bad, good)
+    rc = L.pp_pair_number_grids(P, 3, 101, None, 0.1, ctypes.cast(arr, ctypes.c_void_p), 3, 0, 0, P, None, None)
+    assert rc == pp.PP_ERR_INVALID_ARG and b"candidate 1" in L.pp_last_error()
+    assert b"mirror_z" in L.pp_last_error()
+    arr = (pp.Grid * 2)(good, good)
+    ns = (ctypes.c_int32 * 2)(50, 60)  # 2 * 60 + 1 > ld
+    rc = L.pp_pair_number_grids(P, 2, 101, ctypes.cast(ns, ctypes.c_void_p), 0.1, ctypes.cast(arr, ctypes.c_void_p),
+                                2, 0, 0, P, None, None)
+    assert rc == pp.PP_ERR_INVALID_ARG and b"candidate 1" in L.pp_last_error()
+    rc = L.pp_pair_number_grids(P, 2, 101, None, 0.1, None, 2, 0, 0, P, None, None)
+    assert rc == pp.PP_ERR_INVALID_ARG
+    assert L.pp_pair_number_grids(None, 0, 101, None, 0.1, None, 0, 0, 0, None, None, None) == pp.PP_OK
+
+
 def test_product_package_does_not_import_the_oracle():
     pkg = os.path.join(ROOT, "paper_1704_08919_gb300")
     for dirpath, _, files in os.walk(pkg):

@@ -246,3 +246,27 @@ def test_batch_with_the_hann_envelope(pp):
             No, _ = oracle.pair_number(Ao, ns, DT, g)
             assert abs(N[c].item() / No[0] - 1) < 1e-9
     b.close()
+
+
+@pytest.mark.parametrize("precision,scheme", [("fp64", "rk4"), ("fp32fast", "magnus4"), ("fp32", "rk4")])
+def test_pair_number_with_a_grid_per_candidate(pp, precision, scheme):
+    # pp_pair_number_grids: candidate c on grids[c] equals pp_pair_number of c alone on that grid,
+    # bit for bit (N and n(p), the n(p) arrays concatenated), with uneven step counts; one
+    # shared grid is pp_pair_number itself
+    params = inputs.random_population(len(STEPS), K, seed=61)
+    b = pp.Batch(specs(), grids(), DT, precision="fp64", scheme="rk4")
+    A = b.synth(torch.tensor(params, device=DEV))
+    N, n = pp.pair_number_grids(A, DT, grids(), precision=precision, scheme=scheme, n_steps=STEPS, want_n=True)
+    assert pp.sync_status() == pp.PP_OK
+    off = 0
+    for c, (ns, g) in enumerate(zip(STEPS, grids())):
+        Nu, nu = pp.pair_number(A[c:c + 1, :, :2 * ns + 1].contiguous(), DT, g, precision=precision, scheme=scheme,
+                                want_n=True)
+        nm = g["nx"] * g["ny"] * g["nz"]
+        assert torch.equal(N[c:c + 1], Nu)
+        assert torch.equal(n[off:off + nm], nu.reshape(-1))
+        off += nm
+    Ns, _ = pp.pair_number_grids(A, DT, [grids()[0]], precision=precision, scheme=scheme, n_steps=STEPS)
+    Nu, _ = pp.pair_number(A, DT, grids()[0], precision=precision, scheme=scheme, n_steps=STEPS)
+    assert torch.equal(Ns, Nu)
+    b.close()
