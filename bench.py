@@ -1032,6 +1032,13 @@ def main():
         raise RuntimeError("device status %d after the timed region" % st)
     step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
     total_ms = max_over_ranks(sum(step_ms), dist, dev)
+    replicas = None
+    if dist is not None:
+        # every rank must hold the same population and fitness after the sharded generations
+        chk = float(torch.sum(pop).item() + torch.sum(fit).item())
+        replicas = max_over_ranks(chk, dist, dev) == -max_over_ranks(-chk, dist, dev)
+        if not replicas:
+            raise RuntimeError("the ranks' populations diverged")
     ms_per_step = total_ms / args.steps
     cand_per_s = throughput(ws, NP, args.steps, total_ms)
     mode_steps_per_s = cand_per_s * units_per_candidate()
@@ -1196,6 +1203,7 @@ def main():
             # per generation: proposal, spectrum, samples, table, propagation (+ its
             # wide-range twin for Magnus-4), partial sums, selection
             "gpu_launches": (8 if args.scheme == "magnus4" else 7) * args.steps,
+            "replicas_identical": replicas,
             "launch_tuning": tuned,
             "alt_compensated": alt,
             "clocks": clk,
