@@ -60,7 +60,7 @@ def test_single_process_needs_no_process_group():
 
 
 def test_reference_arm_under_torchrun_prints_one_line():
-    """bench.py --impl reference launched as the driver launches N > 1: rank 0 times
+    """bench.py --impl reference launched under torchrun with two ranks: rank 0 times
     the oracle and prints one JSON line, the other rank exits 0 without work."""
     import json
     import subprocess
