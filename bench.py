@@ -850,6 +850,12 @@ def surrogate_main(args):
         raise RuntimeError("device status after the surrogate run")
     gains = {m: [r[m]["gain_in_exact_calls"] for r in per_seed] for m in per_seed[0] if m not in ("seed", "plain")}
     med = {m: statistics.median(v) for m, v in gains.items()}
+    # exact calls saved per search (plain minus screened, to plain DE's best N) and the number of
+    # searches after which the training evaluations have paid for themselves
+    saved = {m: [r["plain"]["calls_to_best"] - r[m]["calls_to_plain_best"] for r in per_seed
+                 if r[m]["calls_to_plain_best"]] for m in gains}
+    break_even = {m: (n_train / statistics.median(v) if v and statistics.median(v) > 0 else None)
+                  for m, v in saved.items()}
     print(json.dumps({
         "metric": "exact solver calls to reach plain-DE best N, plain / surrogate-screened "
                   "(median over seeds, %s screening)" % args.screen,
@@ -861,6 +867,10 @@ def surrogate_main(args):
                    "epochs": S["epochs"], "batch": S["batch"], "generations": G,
                    "seeds": args.seeds},
         "gain_median": med, "gains": gains,
+        "gain_range": {m: [min(v), max(v)] for m, v in gains.items()},
+        "seeds_below_4x": {m: sum(1 for x in v if x < 4.0) for m, v in gains.items()},
+        "exact_calls_saved_per_search": saved,
+        "searches_to_repay_training": break_even,
         "training": {"pulses": n_train, "seconds_generate": t_gen, "seconds_fit": t_fit,
                      "final_epoch_loss": float(losses[-1].item())},
         "heldout": held, "per_seed": per_seed, "gemm": gemm_measure(pp, torch),
