@@ -114,15 +114,17 @@ __device__ __forceinline__ Coef<T> coef_from(const Basics<T> &b, const QkeS<T> &
     return c;
 }
 
-// out = N (one e_1 + v)
-template <typename T>
-__device__ __forceinline__ void nmul(const Coef<T> &c, const T v[6], T one, T out[6])
+// out = N (e_1 + v) (ONE) or N v; Q (1 + v_0) is formed as Q + Q v_0 in one FMA,
+// which also keeps the low bits of the small v_0.
+template <bool ONE, typename T>
+__device__ __forceinline__ void nmul(const Coef<T> &c, const T v[6], T out[6])
 {
     out[0] = -c.Q * v[1];
-    out[1] = c.Q * (one + v[0]) - c.W2 * v[2] + c.R * v[3];
-    out[2] = c.W2 * v[1] - c.R * v[4];
-    out[3] = -c.R * v[1] + c.W2 * v[4];
-    out[4] = c.R * v[2] - c.W2 * v[3] + c.Q * v[5];
+    const T q1 = ONE ? fma(c.Q, v[0], c.Q) : c.Q * v[0];
+    out[1] = fma(c.R, v[3], fma(-c.W2, v[2], q1));
+    out[2] = fma(c.W2, v[1], -c.R * v[4]);
+    out[3] = fma(c.W2, v[4], -c.R * v[1]);
+    out[4] = fma(c.Q, v[5], fma(-c.W2, v[3], c.R * v[2]));
     out[5] = -c.Q * v[4];
 }
 
@@ -132,35 +134,46 @@ __device__ __forceinline__ void rk4_step(T d[6], const Coef<T> &c0, const Coef<T
 {
     const T hd = T(0.5) * dt, sx = dt / T(6);
     T k1[6], k2[6], k3[6], k4[6], y[6];
-    nmul(c0, d, T(1), k1);
+    nmul<true>(c0, d, k1);
 #pragma unroll
     for (int i = 0; i < 6; ++i)
         y[i] = d[i] + hd * k1[i];
-    nmul(ch, y, T(1), k2);
+    nmul<true>(ch, y, k2);
 #pragma unroll
     for (int i = 0; i < 6; ++i)
         y[i] = d[i] + hd * k2[i];
-    nmul(ch, y, T(1), k3);
+    nmul<true>(ch, y, k3);
 #pragma unroll
     for (int i = 0; i < 6; ++i)
         y[i] = d[i] + dt * k3[i];
-    nmul(c1, y, T(1), k4);
+    nmul<true>(c1, y, k4);
 #pragma unroll
     for (int i = 0; i < 6; ++i)
         d[i] = d[i] + sx * (((k1[i] + T(2) * k2[i]) + T(2) * k3[i]) + k4[i]);
 }
 
-// Adjoints of (Q, R, omega) from one stage k = N (e_1 + y) with stage adjoint kb.
+// Adjoints of (Q, R, omega) from one stage k = N (e_1 + y) with stage adjoint kb,
+// accumulated term by term: acc[0] += Qb, acc[1] += Rb, acc[2] += wb / 2 (the
+// factor 2 of N's omega entries is applied once per sample, in sens_from).
 template <typename T>
 __device__ __forceinline__ void coef_adj(const T kb[6], const T y[6], T acc[3])
 {
-    acc[0] += (-kb[0] * y[1] + kb[1] * (T(1) + y[0])) + (kb[4] * y[5] - kb[5] * y[4]);
-    acc[1] += (kb[1] * y[3] - kb[2] * y[4]) + (kb[4] * y[2] - kb[3] * y[1]);
-    acc[2] += T(2) * ((kb[2] * y[1] - kb[1] * y[2]) + (kb[3] * y[4] - kb[4] * y[3]));
+    T a = fma(kb[1], y[0], acc[0] + kb[1]);
+    a = fma(-kb[0], y[1], a);
+    a = fma(kb[4], y[5], a);
+    acc[0] = fma(-kb[5], y[4], a);
+    a = fma(kb[1], y[3], acc[1]);
+    a = fma(-kb[2], y[4], a);
+    a = fma(kb[4], y[2], a);
+    acc[1] = fma(-kb[3], y[1], a);
+    a = fma(kb[2], y[1], acc[2]);
+    a = fma(-kb[1], y[2], a);
+    a = fma(kb[3], y[4], a);
+    acc[2] = fma(-kb[4], y[3], a);
 }
 
 // Sensitivities (A_x, A_y, E_x, E_y, Ed_x, Ed_y) of one sample from the
-// adjoints (Qb, Rb, wb) of its coefficients.
+// adjoints (Qb, Rb, wb / 2) of its coefficients, as coef_adj accumulates them.
 template <typename T>
 __device__ __forceinline__ void sample_sens(const QkeS<T> &s, T px, T py, T pz2, T eperp, const T ab[3], T out[6])
 {
@@ -171,7 +184,7 @@ __device__ __forceinline__ void sample_sens(const QkeS<T> &s, T px, T py, T pz2,
     const T X = w2 * s.ee - EP * EP;
     const T P[2] = {Px, Py}, E[2] = {s.ex, s.ey};
     const T dcr_dE[2] = {s.edy, -s.edx}, dcr_dEd[2] = {-s.ey, s.ex};
-    const T Qb = ab[0], Rb = ab[1], wb = ab[2];
+    const T Qb = ab[0], Rb = ab[1], wb = ab[2] + ab[2];
     const bool pos = X > T(0);
     const T rX = pos ? rsq(X) : T(0);
     const T sX = X * rX, iX = rX * rX;
@@ -212,37 +225,55 @@ __device__ __forceinline__ double density(const T d[6])
     return (double)g <= kGrowthTol ? -(double)d[0] : __longlong_as_double(0x7ff8000000000000ll);
 }
 
-// The same values as sample_sens, from precomputed basics, with the terms
-// gathered per direction: writing dX/dP_a = 2 (P_a |E|^2 - (E.P) E_a) and
+// Per-mode terms of one sample's sensitivities, from precomputed basics and the
+// adjoints (Qb, Rb, wb / 2).  Writing dX/dP_a = 2 (P_a |E|^2 - (E.P) E_a) and
 // dX/dE_a = 2 (omega^2 E_a - (E.P) P_a), the chain rule through Q = sqrt(X)/omega^2,
-// R = eps_perp omega cr / X and omega gives
-//   dJ/dA_a  = -[ Qb hq dX/dP_a - Rb R (dX/dP_a / X) + beta P_a ],
-//   dJ/dE_a  =    Qb hq dX/dE_a - Rb R (dX/dE_a / X) + gam dcr/dE_a,
-//   dJ/dEd_a =    gam dcr/dEd_a,
-// with hq = dQ/dX = 1 / (2 sqrt(X) omega^2), gam = Rb eps_perp omega / X and
-// beta = wb / omega + Rb R / omega^2 - 2 Qb sqrt(X) / omega^4.  dX is divided by X
-// before it meets R (FP32 range near zeros of E).  Where X <= 0, rX = 0 makes
+// R = eps_perp omega cr / X and omega gives, per mode,
+//   dJ/dA_a  = -(mu P_a) + nu E_a,
+//   dJ/dE_a  = (2 kappa omega^2) E_a - (nu P_a) + gam dcr/dE_a,
+//   dJ/dEd_a = gam dcr/dEd_a,
+// with kappa = Qb hq - Rb R / X, hq = dQ/dX = 1 / (2 sqrt(X) omega^2),
+// gam = Rb eps_perp omega / X, beta = wb / omega + Rb R / omega^2 - 2 Qb sqrt(X) / omega^4,
+// mu = 2 kappa |E|^2 + beta and nu = 2 kappa (E.P).  E, Ed and cr are the same for
+// every mode, so only the seven mode-dependent factors are summed over the modes:
+//   out = (mu P_x, mu P_y, nu, 2 kappa omega^2, nu P_x, nu P_y, gam),
+// and sample_sens_from_sums applies the sample's constants once.  R is divided by
+// X before it meets dX (FP32 range near zeros of E).  Where X <= 0, rX = 0 makes
 // every Q and R term vanish, as in sample_sens.
+constexpr int kSensTerms = 7;
+
 template <typename T>
-__device__ __forceinline__ void sens_from(const Basics<T> &b, const QkeS<T> &s, T eperp, const T ab[3], T out[6])
+__device__ __forceinline__ void sens_from(const Basics<T> &b, const QkeS<T> &s, T eperp, const T ab[3], T out[7])
 {
     const T w = b.w2 * b.iw, iw2 = b.iw * b.iw;
     const T sX = b.X * b.rX, iX = b.rX * b.rX;
-    const T Qb = ab[0], Rb = ab[1], wb = ab[2];
+    const T Qb = ab[0], Rb = ab[1], wb = ab[2] + ab[2];
     const T ewX = eperp * w * iX;     // R / cr
     const T RbR = Rb * (ewX * s.cr);  // Rb R
-    const T Qh = Qb * (T(0.5) * b.rX * iw2);
     const T gam = Rb * ewX;
     const T beta = (wb * b.iw + RbR * iw2) - T(2) * Qb * sX * (iw2 * iw2);
-    const T P[2] = {b.Px, b.Py}, E[2] = {s.ex, s.ey};
-    const T dcr_dE[2] = {s.edy, -s.edx}, dcr_dEd[2] = {-s.ey, s.ex};
-#pragma unroll
-    for (int a = 0; a < 2; ++a) {
-        const T dXP = T(2) * (P[a] * s.ee - b.EP * E[a]);
-        const T dXE = T(2) * (b.w2 * E[a] - b.EP * P[a]);
-        out[a] = -((Qh * dXP - RbR * (dXP * iX)) + beta * P[a]);
-        out[2 + a] = (Qh * dXE - RbR * (dXE * iX)) + gam * dcr_dE[a];
-        out[4 + a] = gam * dcr_dEd[a];
+    const T k2 = Qb * (b.rX * iw2) - T(2) * (RbR * iX);  // 2 kappa
+    const T mu = fma(k2, s.ee, beta), nu = k2 * b.EP;
+    out[0] = mu * b.Px;
+    out[1] = mu * b.Py;
+    out[2] = nu;
+    out[3] = k2 * b.w2;
+    out[4] = nu * b.Px;
+    out[5] = nu * b.Py;
+    out[6] = gam;
+}
+
+// The sensitivity i of a sample (E, Ed) from the sums over modes u[0..6] of sens_from.
+__device__ __forceinline__ double sample_sens_from_sums(int i, double ex, double ey, double edx, double edy,
+                                                        const double u[7])
+{
+    switch (i) {
+    case 0: return -u[0] + ex * u[2];
+    case 1: return -u[1] + ey * u[2];
+    case 2: return (ex * u[3] - u[4]) + edy * u[6];
+    case 3: return (ey * u[3] - u[5]) - edx * u[6];
+    case 4: return -ey * u[6];
+    default: return ex * u[6];
     }
 }
 
@@ -391,7 +422,7 @@ __global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 2 : 1) qke_adjoint
 {
     constexpr int GS = kQGroup * S;  // steps per group
     __shared__ double red[kQWarps];
-    __shared__ double sb[kQWarps][2 * GS][6];
+    __shared__ double sb[kQWarps][2 * GS][kSensTerms];
     __shared__ QkeS<T> seg[2 * GS + 1];  // the samples of the current group (broadcast reads)
     // the segment's recomputed states, one slot per thread: sst[(q * 6 + i) * kQThreads + tid]
     extern __shared__ __align__(16) unsigned char qke_dyn[];
@@ -457,12 +488,15 @@ __global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 2 : 1) qke_adjoint
             for (int i = 0; i < 6; ++i)
                 d[i] = mg.active ? ck[((size_t)s * 6 + i) * nmp + mm] : T(0);
             {
+                // the segment's states x_0 .. x_{cnt-1}; x_cnt (the next checkpoint) is not needed
                 Coef<T> c0 = coef_at(seg[2 * so], px, py, pz2, eperp);
 #pragma unroll 1
-                for (int q = 0; q < cnt; ++q) {
+                for (int q = 0;; ++q) {
 #pragma unroll
                     for (int i = 0; i < 6; ++i)
                         sst[(q * 6 + i) * kQThreads + threadIdx.x] = d[i];
+                    if (q + 1 >= cnt)
+                        break;
                     const Coef<T> ch = coef_at(seg[2 * (so + q) + 1], px, py, pz2, eperp);
                     const Coef<T> cn = coef_at(seg[2 * (so + q) + 2], px, py, pz2, eperp);
                     rk4_step(d, c0, ch, cn, dt);
@@ -482,15 +516,15 @@ __global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 2 : 1) qke_adjoint
                     for (int i = 0; i < 6; ++i)
                         x[i] = sst[(q * 6 + i) * kQThreads + threadIdx.x];
                     T k1[6], k2[6], k3[6], y2[6], y3[6], y4[6];
-                    nmul(c0, x, T(1), k1);
+                    nmul<true>(c0, x, k1);
 #pragma unroll
                     for (int i = 0; i < 6; ++i)
                         y2[i] = x[i] + hd * k1[i];
-                    nmul(ch, y2, T(1), k2);
+                    nmul<true>(ch, y2, k2);
 #pragma unroll
                     for (int i = 0; i < 6; ++i)
                         y3[i] = x[i] + hd * k2[i];
-                    nmul(ch, y3, T(1), k3);
+                    nmul<true>(ch, y3, k3);
 #pragma unroll
                     for (int i = 0; i < 6; ++i)
                         y4[i] = x[i] + dt * k3[i];
@@ -505,7 +539,7 @@ __global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 2 : 1) qke_adjoint
                     }
                     // k4 = N1 (e1 + y4): completes the sample 2n+2
                     coef_adj(kb4, y4, pend);
-                    nmul(c1, kb4, T(0), yb);
+                    nmul<false>(c1, kb4, yb);
 #pragma unroll
                     for (int i = 0; i < 6; ++i) {
                         xb[i] -= yb[i];
@@ -513,14 +547,14 @@ __global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 2 : 1) qke_adjoint
                     }
                     T hacc[3] = {0, 0, 0};
                     coef_adj(kb3, y3, hacc);  // k3 = Nh (e1 + y3)
-                    nmul(ch, kb3, T(0), yb);
+                    nmul<false>(ch, kb3, yb);
 #pragma unroll
                     for (int i = 0; i < 6; ++i) {
                         xb[i] -= yb[i];
                         kb2[i] -= hd * yb[i];
                     }
                     coef_adj(kb2, y2, hacc);  // k2 = Nh (e1 + y2)
-                    nmul(ch, kb2, T(0), yb);
+                    nmul<false>(ch, kb2, yb);
 #pragma unroll
                     for (int i = 0; i < 6; ++i) {
                         xb[i] -= yb[i];
@@ -528,21 +562,22 @@ __global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 2 : 1) qke_adjoint
                     }
                     T nacc[3] = {0, 0, 0};
                     coef_adj(kb1, x, nacc);  // k1 = N0 (e1 + x)
-                    nmul(c0, kb1, T(0), yb);
+                    nmul<false>(c0, kb1, yb);
 #pragma unroll
                     for (int i = 0; i < 6; ++i)
                         bar[i] = xb[i] - yb[i];
-                    // emit samples 2n+2 (values 0..5, slot 2q+1) and 2n+1 (values 6..11, slot 2q)
+                    // emit samples 2n+2 (terms 0..6, slot 2q+1) and 2n+1 (terms 7..13, slot 2q)
                     T o[16];
                     sens_from(b1, e1, eperp, pend, o);
-                    sens_from(bh, eh, eperp, hacc, o + 6);
+                    sens_from(bh, eh, eperp, hacc, o + kSensTerms);
 #pragma unroll
-                    for (int i = 12; i < 16; ++i)
+                    for (int i = 2 * kSensTerms; i < 16; ++i)
                         o[i] = T(0);
                     const T tot = warp_sum16(o, lane);
                     const int vi = (lane >> 1) & 15;
-                    if ((lane & 1) == 0 && vi < 12)
-                        sb[warp][vi < 6 ? 2 * (so + q) + 1 : 2 * (so + q)][vi < 6 ? vi : vi - 6] = (double)tot;
+                    if ((lane & 1) == 0 && vi < 2 * kSensTerms)
+                        sb[warp][vi < kSensTerms ? 2 * (so + q) + 1 : 2 * (so + q)]
+                          [vi < kSensTerms ? vi : vi - kSensTerms] = (double)tot;
 #pragma unroll
                     for (int i = 0; i < 3; ++i)
                         pend[i] = nacc[i];
@@ -552,12 +587,21 @@ __global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 2 : 1) qke_adjoint
             }
         }
         __syncthreads();
+        // sample 2 n0g + 1 + kk: its seven terms summed over the warps (fixed
+        // order), then its sensitivity i from the sample's E and Ed
         for (int t = threadIdx.x; t < 2 * cntg * 6; t += kQThreads) {
             const int i = t / (2 * cntg), kk = t % (2 * cntg);
-            double acc = 0.0;
-            for (int w = 0; w < kQWarps; ++w)
-                acc += sb[w][kk][i];
-            prow[(size_t)i * ldg + 2 * n0g + 1 + kk] = acc;
+            double u[kSensTerms];
+#pragma unroll
+            for (int j = 0; j < kSensTerms; ++j) {
+                double acc = 0.0;
+                for (int w = 0; w < kQWarps; ++w)
+                    acc += sb[w][kk][j];
+                u[j] = acc;
+            }
+            const QkeS<T> &e = seg[kk + 1];
+            prow[(size_t)i * ldg + 2 * n0g + 1 + kk] =
+                sample_sens_from_sums(i, (double)e.ex, (double)e.ey, (double)e.edx, (double)e.edy, u);
         }
         __syncthreads();
     }

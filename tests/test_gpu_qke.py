@@ -238,13 +238,26 @@ def test_local_search_improves_and_holds_the_fluence(pp):
     feas = ok & (np.abs(r["C"]) < 0.1 * 2.0)
     assert feas.any()
     assert r["J"][feas].max() > np.nanmax(J0)
-    # the result's J by the oracle agrees with the GPU's FP32 value (the search may end
-    # on the edge of the rejected region, where FP32 and FP64 can decide differently)
-    Jo = np.array([oracle.al_objective(r["x"][i], spec(n), grid, 2.0, 0.0, 1.0)["J"]
-                   for i in np.nonzero(ok)[0]])
-    both = np.isfinite(Jo)
-    assert both.sum() >= 1
-    assert np.all(np.abs(r["J"][ok][both] / Jo[both] - 1) < 1e-3)
+    # The result's densities by the oracle agree with the GPU's FP32 ones mode by mode.
+    # The search ends where J stops rising, which can be the edge of the rejected
+    # region: there a mode's |chi|^2 sits at 1 + 1e-3 and FP32 and FP64 can decide
+    # differently, so modes the oracle rejects are left out (a few at most), and J is
+    # compared where the oracle accepts every mode.
+    p, w = oracle.grid_modes(grid)
+    dt = 20.0 / n
+    for i in np.nonzero(ok)[0]:
+        A, E, Ed, _ = oracle.synth_raw(r["x"][i][None], *ARGS, n)
+        fo = oracle.qke6_modes(A[0], E[0], Ed[0], n, dt, p)
+        J32, f32 = pp.qke_pair_number(dev(A), dev(E), dev(Ed), dt, grid, "fp32", want_n=True)
+        f32 = f32.cpu().numpy().reshape(-1)
+        assert np.all(np.isfinite(f32))
+        assert abs(J32.item() / r["J"][i] - 1) < 1e-6  # the search reports the J of its x
+        fin = np.isfinite(fo)
+        assert fin.sum() >= 0.75 * len(fo)
+        assert np.all(np.abs(f32[fin] - fo[fin]) <= 1e-3 * np.abs(fo[fin]) + 1e-6 * np.abs(fo[fin]).max())
+        if fin.all():
+            assert abs(r["J"][i] / float(np.sum(w * fo)) - 1) < 1e-3
+    assert pp.sync_status() == pp.PP_OK
 
 
 def test_rk4_growth_is_rejected_like_the_oracle(pp):
