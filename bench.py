@@ -78,6 +78,9 @@ def parse():
                     help="localsearch: time the batched gradient evaluation only (no search)")
     ap.add_argument("--small", action="store_true",
                     help="localsearch: a 16 x 16 x 8 grid (profiling runs)")
+    ap.add_argument("--qke-state-budget", type=float, default=None,
+                    help="localsearch: GiB of device memory the QKE adjoint may keep forward states in "
+                         "(default: the library's, half the device memory)")
     ap.add_argument("--qke-steps", type=int, default=None,
                     help="localsearch: RK4 steps per pulse instead of the workload's 16384 (profiling runs)")
     ap.add_argument("--screen", default="individual", choices=["individual", "global"],
@@ -491,6 +494,11 @@ def localsearch_main(args):
         return 0
     torch.cuda.set_device(local)
     pp.lib()
+    if args.qke_state_budget is not None:
+        pp.set_qke_state_budget(int(args.qke_state_budget * 2 ** 30))
+    cur = pp.set_qke_state_budget(-1)
+    pp.set_qke_state_budget(cur)
+    budget_gib = "default: half the device memory" if cur < 0 else cur / 2 ** 30
     if args.qke_steps:
         L = dict(L, n_steps=args.qke_steps)
     sp = inputs.field_spec(dict(L, fluence=1.0))
@@ -545,7 +553,7 @@ def localsearch_main(args):
         "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64",
         "data": "synthetic (seeded B-spline pulses scaled to U_const)",
         "config": {"workload": L["name"], "precision": prec, "grid": "%dx%dx%d" % (g["nx"], g["ny"], g["nz"]),
-                   "n_steps": L["n_steps"], "T": L["T"], "nstart": S,
+                   "n_steps": L["n_steps"], "T": L["T"], "nstart": S, "qke_state_budget_gib": budget_gib,
                    "options": {k: L[k] for k in ("mu0", "xi", "outer", "max_iter", "gtol", "ctol")}},
         "mode_steps_per_s": mode_steps / (eval_ms * 1e-3),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",

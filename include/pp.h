@@ -435,7 +435,8 @@ int pp_de_step(double *pop, double *fit, int32_t NP, const pp_field_spec *spec,
 int pp_sync_status(void *stream);
 
 /* Frees the library's scratch on the current device (it only grows otherwise: the
- * QKE adjoint, for instance, keeps up to ~8 GiB of checkpoints).  Synchronises the
+ * QKE adjoint, for instance, keeps up to its state budget, by default half of
+ * the device's memory).  Synchronises the
  * device first; the next call that needs scratch allocates it again.  Do not call
  * it while a CUDA graph that uses the scratch may still be launched. */
 int pp_release_scratch(void);
@@ -531,9 +532,14 @@ int pp_al_search(int32_t n, int32_t nstart, double *x, pp_objective_fn fn, void 
  * pp_qke_sample_gradient: J[c] and g[c][6][ldg] = dJ/d(every sample of A_x, A_y,
  *   E_x, E_y, Ed_x, Ed_y): the exact derivative of the discrete J, computed by
  *   the adjoint of the RK4 map (adjoint final value lambda_1 = -1 of Eq. (adj)
- *   scaled by w(p), the inner product of Eq. (grad) taken stage by stage), the
- *   forward states kept at every 4th (FP64) or 8th (FP32) step and recomputed.
- *   Candidates are processed in chunks that keep the work buffers near 8 GiB.
+ *   scaled by w(p), the inner product of Eq. (grad) taken stage by stage).  The
+ *   forward states are kept in device scratch for the backward sweep: every
+ *   step's state when the states of enough candidates to fill the GPU once fit
+ *   within the state budget (pp_set_qke_state_budget, by default half of the
+ *   device's memory), else every 4th (FP64) or 8th (FP32) step's, the others
+ *   recomputed.  Candidates are processed in chunks whose work buffers fit the
+ *   budget (one candidate per chunk at least), sized so that partial waves of
+ *   CTAs cost least.  J and g do not depend on either choice.
  * pp_qke_gradient: params -> raw field -> J[c], gJ[c][4K] = dJ/dparams (may be
  *   NULL: J only), U[c] and dU[c][4K] (each may be NULL); all device pointers.
  * pp_local_search: the multistart search of pp_al_search with this objective:
@@ -554,6 +560,15 @@ int pp_qke_sample_gradient(const double *A, const double *E, const double *Ed, i
                            int32_t ldg, void *stream);
 int pp_qke_gradient(const double *params, int32_t ncand, const pp_field_spec *spec, const pp_grid *grid,
                     int32_t precision, double *J, double *gJ, double *U, double *dU, void *stream);
+
+/* Device bytes the QKE adjoint (pp_qke_sample_gradient, pp_qke_gradient,
+ * pp_local_search) may use for kept forward states and per-CTA partial rows.
+ * A negative value selects the default, half of the device's memory; 0 selects
+ * the recomputing variant with one candidate per launch.  If the kept states do
+ * not fit in free device memory, the adjoint recomputes instead.  The scratch
+ * stays allocated until pp_release_scratch.  Host-only setting for every device,
+ * read at each call.  Returns the previous setting (-1: the default). */
+int64_t pp_set_qke_state_budget(int64_t bytes);
 int pp_local_search(double *x, int32_t nstart, const pp_field_spec *spec, const pp_grid *grid, int32_t precision,
                     double U_const, const pp_al_options *opt, double *J_out, double *C_out, double *lam_out,
                     int32_t *evals_out, int32_t *outer_out, int32_t *status_out, void *stream);

@@ -49,7 +49,8 @@ EXPORTS = ("pp_synth_field", "pp_pair_number", "pp_de_propose", "pp_de_select", 
            "pp_mlp_train_step", "pp_mlp_features", "pp_de_screened_step", "pp_mlp_fit",
            "pp_mlp_log_targets", "pp_mlp_init", "pp_al_search", "pp_synth_field_raw",
            "pp_synth_vjp", "pp_qke_pair_number", "pp_qke_sample_gradient", "pp_qke_gradient",
-           "pp_local_search", "pp_release_scratch", "pp_pair_number_grids")
+           "pp_local_search", "pp_release_scratch", "pp_pair_number_grids",
+           "pp_set_qke_state_budget")
 
 
 class ALOptions(ctypes.Structure):
@@ -107,6 +108,8 @@ def lib():
         L.pp_sync_status.argtypes = [_vp]
         L.pp_set_wait_limit.argtypes = [ctypes.c_int64]
         L.pp_set_wait_limit.restype = ctypes.c_int64
+        L.pp_set_qke_state_budget.argtypes = [ctypes.c_int64]
+        L.pp_set_qke_state_budget.restype = ctypes.c_int64
         L.pp_set_skip_copies.argtypes = [ctypes.c_int]
         L.pp_last_error.restype = ctypes.c_char_p
         L.pp_profile_end.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
@@ -564,6 +567,13 @@ def set_wait_limit(limit):
 
 def set_skip_copies(skip):
     return lib().pp_set_skip_copies(int(skip))
+
+
+def set_qke_state_budget(nbytes):
+    """pp_set_qke_state_budget: device bytes the QKE adjoint may keep for forward states
+    (negative: the default, half the device's memory).  Returns the previous setting
+    (-1: the default)."""
+    return lib().pp_set_qke_state_budget(int(nbytes))
 
 
 def al_search(x0, fn, mu0=1.0, xi=0.5, outer=10, max_iter=200, gtol=1e-6, ctol=1e-8):

@@ -28,6 +28,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include "pp_policies.cuh"
@@ -406,25 +407,49 @@ __global__ void __launch_bounds__(kQThreads) qke_forward_kernel(const QkeS<T> *_
         part[(size_t)c * gridDim.x + blk] = s;
 }
 
+// Per-thread asynchronous copies of one 4- or 8-byte value global -> shared
+// (cp.async), one commit group per step, so that a thread can wait for its own
+// copies without a barrier.
+template <typename T>
+__device__ __forceinline__ void cp_async_value(T *smem, const T *gmem)
+{
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "cp.async copies 4, 8 or 16 bytes");
+    const unsigned int sa = (unsigned int)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"((int)sizeof(T))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 // Forward with checkpoints, then the backward sweep segment by segment.
 // ckpt[c][seg][6][nmp] (T), part[c][blk][6][ldg] (FP64), partJ[c][blk].
-// Segments of S steps are handled in groups of kQGroup: the samples of a group are
+// S = 1: every step's state is kept, and the backward sweep reads it back through
+// a per-thread ring of kQRing shared-memory slots filled kQRing - 1 steps ahead by
+// cp.async (no recomputation).  S > 1: one state per S steps, and each segment is
+// recomputed into per-thread shared-memory slots before its backward steps.
+// The steps are handled in groups of kQGroupSteps: the samples of a group are
 // staged into shared memory once, and the sample sensitivities of a whole group
-// are summed over the CTA's warps once, so a group of kQGroup S steps costs four
-// barriers.  FP32: 2 CTAs per SM with up to 128 registers (no spills; 3 CTAs per
-// SM at 80 registers spilled in the backward step and measured 2.9% slower).
-constexpr int kQGroup = 4;
+// are summed over the CTA's warps once, so a group costs four barriers whatever S
+// is, and J and the gradient do not depend on S.  FP32: 2 CTAs per SM with up to
+// 128 registers (no spills; 3 CTAs per SM at 80 registers spilled in the backward
+// step and measured 2.9% slower).
+constexpr int kQGroupSteps = 32;
+constexpr int kQRing = 4;
 template <typename T, int S>
 __global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 2 : 1) qke_adjoint_kernel(const QkeS<T> *__restrict__ tab, int ldt, int n_steps,
                                                                 double dt_d, pp_grid g, T *__restrict__ ckpt, int nmp,
                                                                 double *__restrict__ part, int ldg,
                                                                 double *__restrict__ partJ)
 {
-    constexpr int GS = kQGroup * S;  // steps per group
+    static_assert(kQGroupSteps % S == 0, "a group holds whole segments");
+    constexpr int kQGroup = kQGroupSteps / S;  // segments per group
+    constexpr int GS = kQGroupSteps;           // steps per group
     __shared__ double red[kQWarps];
     __shared__ double sb[kQWarps][2 * GS][kSensTerms];
     __shared__ QkeS<T> seg[2 * GS + 1];  // the samples of the current group (broadcast reads)
-    // the segment's recomputed states, one slot per thread: sst[(q * 6 + i) * kQThreads + tid]
+    // per-thread state slots, sst[(q * 6 + i) * kQThreads + tid]: the segment's
+    // recomputed states (S > 1) or the prefetch ring (S = 1, slot q = step % kQRing)
     extern __shared__ __align__(16) unsigned char qke_dyn[];
     T *sst = reinterpret_cast<T *>(qke_dyn);
     const int c = blockIdx.y, blk = blockIdx.x, nblk = gridDim.x;
@@ -479,15 +504,34 @@ __global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 2 : 1) qke_adjoint
     T pend[3] = {0, 0, 0};  // coefficient adjoints of the sample at the top of the next step
     Coef<T> c1 = coef_at(tr[2 * n_steps], px, py, pz2, eperp);
     Basics<T> b1 = basics(tr[2 * n_steps], px, py, pz2);  // of the sample at the top of the step
+    // S = 1: this thread's stored state at the start of step n into ring slot n % kQRing
+    auto prefetch = [&](int n) {
+        if (n >= 0) {
+            T *dst = sst + (size_t)(n % kQRing) * 6 * kQThreads + threadIdx.x;
+            const T *src = ck + (size_t)n * 6 * nmp + mm;
+#pragma unroll
+            for (int i = 0; i < 6; ++i)
+                cp_async_value(dst + i * kQThreads, src + (size_t)i * nmp);
+        }
+        cp_async_commit();  // one group per step, empty below step 0
+    };
+    if constexpr (S == 1)
+        for (int n = n_steps - 1; n > n_steps - kQRing; --n)
+            prefetch(n);
     for (int gr = ngrp - 1; gr >= 0; --gr) {
         const int g0 = gr * kQGroup, n0g = g0 * S, cntg = min(GS, n_steps - n0g);
         stage(n0g, cntg);
         for (int s = min(g0 + kQGroup, nseg) - 1; s >= g0; --s) {
             const int so = (s - g0) * S, cnt = min(S, n_steps - s * S);
+            const T *xs = sst;  // the states x_q of this segment: xs[(q * 6 + i) * kQThreads + tid]
+            if constexpr (S == 1) {
+                prefetch(s - (kQRing - 1));
+                cp_async_wait<kQRing - 1>();  // this thread's copy of step s has landed
+                xs = sst + (size_t)(s % kQRing) * 6 * kQThreads;
+            } else {
 #pragma unroll
-            for (int i = 0; i < 6; ++i)
-                d[i] = mg.active ? ck[((size_t)s * 6 + i) * nmp + mm] : T(0);
-            {
+                for (int i = 0; i < 6; ++i)
+                    d[i] = mg.active ? ck[((size_t)s * 6 + i) * nmp + mm] : T(0);
                 // the segment's states x_0 .. x_{cnt-1}; x_cnt (the next checkpoint) is not needed
                 Coef<T> c0 = coef_at(seg[2 * so], px, py, pz2, eperp);
 #pragma unroll 1
@@ -514,7 +558,7 @@ __global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 2 : 1) qke_adjoint
                     T x[6];
 #pragma unroll
                     for (int i = 0; i < 6; ++i)
-                        x[i] = sst[(q * 6 + i) * kQThreads + threadIdx.x];
+                        x[i] = xs[(q * 6 + i) * kQThreads + threadIdx.x];
                     T k1[6], k2[6], k3[6], y2[6], y3[6], y4[6];
                     nmul<true>(c0, x, k1);
 #pragma unroll
@@ -676,40 +720,82 @@ int forward(const double *A, const double *E, const double *Ed, int ncand, int l
     return e == cudaSuccess ? PP_OK : pp::cuda_fail(e, "QKE forward launch");
 }
 
-// Candidates per launch of the adjoint so that checkpoints and partial rows stay
-// within about 8 GiB.
-template <typename T, int S>
-int adjoint_chunk(int ncand, int n_steps, int nmodes)
+// Per-candidate scratch of the adjoint that keeps one state per S steps: the
+// states and the per-CTA partial rows.
+template <typename T>
+size_t adjoint_bytes(int S, int n_steps, int nmodes, int ldg)
 {
     const int nblk = (nmodes + kQThreads - 1) / kQThreads;
     const size_t ck = sizeof(T) * 6 * (size_t)((n_steps + S - 1) / S) * nmodes;
-    const size_t pr = sizeof(double) * 6 * (size_t)nblk * (2 * n_steps + 1);
-    const size_t per = ck + pr;
-    const size_t budget = (size_t)8 << 30;
-    return (int)std::max<size_t>(1, std::min<size_t>((size_t)ncand, budget / std::max<size_t>(per, 1)));
+    const size_t pr = sizeof(double) * 6 * (size_t)nblk * ldg;
+    return ck + pr;
+}
+
+int sm_count()
+{
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 1;
+    return std::max(1, n);
+}
+
+// Relative duration of a launch of n equal CTAs, ctas_per_sm at a time on each of
+// sms SMs: every full wave costs 1; a last partial wave costs 1 if some SM runs
+// more than one CTA of it, else kLoneWave (a CTA alone on its SM runs faster:
+// measured 0.61 for the FP32 adjoint at 2 CTAs per SM).
+constexpr double kLoneWave = 0.61;
+double launch_cost(long long n, int ctas_per_sm, int sms)
+{
+    const long long slots = (long long)ctas_per_sm * sms;
+    const long long full = n / slots, r = n % slots;
+    return (double)full + (r == 0 ? 0.0 : (r > sms || ctas_per_sm == 1 ? 1.0 : kLoneWave));
+}
+
+// Candidates per launch: at most budget / per (one at least), chosen to minimise
+// the summed launch_cost of the launches (ties: the larger chunk, fewer launches).
+int wave_chunk(int ncand, size_t per, size_t budget, int nblk, int ctas_per_sm, int sms)
+{
+    const int cap = (int)std::max<size_t>(1, std::min<size_t>((size_t)ncand, budget / std::max<size_t>(per, 1)));
+    int best = cap;
+    double best_cost = 1e300;
+    for (int c = cap; c >= 1; --c) {
+        const int nfull = ncand / c, rest = ncand % c;
+        const double cost = nfull * launch_cost((long long)c * nblk, ctas_per_sm, sms) +
+                            (rest ? launch_cost((long long)rest * nblk, ctas_per_sm, sms) : 0.0);
+        if (cost < best_cost - 1e-9) {
+            best_cost = cost;
+            best = c;
+        }
+    }
+    return best;
+}
+
+// Scratch of an adjoint launch sequence with one state per S steps, chunk candidates per launch.
+struct AdjointScratch {
+    void *ck = nullptr, *part = nullptr, *pj = nullptr;
+};
+
+template <typename T, int S>
+int adjoint_scratch(int n_steps, int nmodes, int ldg, int chunk, AdjointScratch *a)
+{
+    const int nblk = (nmodes + kQThreads - 1) / kQThreads;
+    const int nseg = (n_steps + S - 1) / S;
+    int rc = pp::scratch(pp::SCR_QKE_CKPT, sizeof(T) * 6 * (size_t)nseg * nmodes * chunk, &a->ck);
+    if (!rc)
+        rc = pp::scratch(pp::SCR_QKE_PART, sizeof(double) * 6 * (size_t)nblk * ldg * chunk, &a->part);
+    if (!rc)
+        rc = pp::scratch(pp::SCR_QKE_X, sizeof(double) * (size_t)nblk * chunk, &a->pj);
+    return rc;
 }
 
 template <typename T, int S>
-int gradient(const double *A, const double *E, const double *Ed, int ncand, int ld, int n_steps, double dt,
-             const pp_grid *g, double *J, double *gs, int ldg, cudaStream_t st)
+int run_adjoint(const void *tab, int ldt, int ncand, int n_steps, double dt, const pp_grid *g, int chunk,
+                const AdjointScratch &a, double *J, double *gs, int ldg, cudaStream_t st)
 {
-    void *tab = nullptr, *ck = nullptr, *part = nullptr, *pj = nullptr;
-    int ldt = 0;
-    int rc = build_table<T>(A, E, Ed, ncand, ld, n_steps, &tab, &ldt, st);
-    if (rc)
-        return rc;
+    void *ck = a.ck, *part = a.part, *pj = a.pj;
     const int nmodes = g->nx * g->ny * g->nz;
     const int nblk = (nmodes + kQThreads - 1) / kQThreads;
-    const int nseg = (n_steps + S - 1) / S;
-    const int chunk = adjoint_chunk<T, S>(ncand, n_steps, nmodes);
-    rc = pp::scratch(pp::SCR_QKE_CKPT, sizeof(T) * 6 * (size_t)nseg * nmodes * chunk, &ck);
-    if (!rc)
-        rc = pp::scratch(pp::SCR_QKE_PART, sizeof(double) * 6 * (size_t)nblk * ldg * chunk, &part);
-    if (!rc)
-        rc = pp::scratch(pp::SCR_QKE_X, sizeof(double) * (size_t)nblk * chunk, &pj);
-    if (rc)
-        return rc;
-    const size_t dyn = sizeof(T) * S * 6 * kQThreads;
+    const size_t dyn = sizeof(T) * (S == 1 ? kQRing : S) * 6 * kQThreads;
     cudaError_t ea = cudaFuncSetAttribute(qke_adjoint_kernel<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)dyn);
     if (ea != cudaSuccess)
@@ -725,6 +811,57 @@ int gradient(const double *A, const double *E, const double *Ed, int ncand, int 
     }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? PP_OK : pp::cuda_fail(e, "QKE adjoint launch");
+}
+
+// State budget: bytes set by pp_set_qke_state_budget, or -1 for the default, half
+// of the device's memory.
+std::atomic<int64_t> g_state_budget{-1};
+
+size_t state_budget()
+{
+    const int64_t b = g_state_budget.load();
+    if (b >= 0)
+        return (size_t)b;
+    size_t free_b = 0, total = 0;
+    if (cudaMemGetInfo(&free_b, &total) != cudaSuccess) {
+        cudaGetLastError();
+        return (size_t)8 << 30;
+    }
+    return total / 2;
+}
+
+// Every step's state is kept (no recomputation) when the states of enough
+// candidates to fill the GPU once (2 CTAs per SM for FP32, 1 for FP64) fit the
+// budget and can be allocated; otherwise one state per SR steps.
+template <typename T, int SR>
+int gradient(const double *A, const double *E, const double *Ed, int ncand, int ld, int n_steps, double dt,
+             const pp_grid *g, double *J, double *gs, int ldg, cudaStream_t st)
+{
+    void *tab = nullptr;
+    int ldt = 0;
+    int rc = build_table<T>(A, E, Ed, ncand, ld, n_steps, &tab, &ldt, st);
+    if (rc)
+        return rc;
+    const int nmodes = g->nx * g->ny * g->nz;
+    const int nblk = (nmodes + kQThreads - 1) / kQThreads;
+    const size_t budget = state_budget();
+    const int sms = sm_count(), per_sm = sizeof(T) == 4 ? 2 : 1;
+    const int wave = std::min(ncand, (sms * per_sm + nblk - 1) / nblk);
+    AdjointScratch a;
+    const size_t per1 = adjoint_bytes<T>(1, n_steps, nmodes, ldg);
+    if (per1 * (size_t)wave <= budget) {
+        const int chunk = wave_chunk(ncand, per1, budget, nblk, per_sm, sms);
+        if (adjoint_scratch<T, 1>(n_steps, nmodes, ldg, chunk, &a) == PP_OK)
+            return run_adjoint<T, 1>(tab, ldt, ncand, n_steps, dt, g, chunk, a, J, gs, ldg, st);
+        cudaGetLastError();  // the kept states did not fit in free memory: recompute instead
+        pp::clear_error();
+    }
+    const size_t perR = adjoint_bytes<T>(SR, n_steps, nmodes, ldg);
+    const int chunk = wave_chunk(ncand, perR, budget, nblk, per_sm, sms);
+    rc = adjoint_scratch<T, SR>(n_steps, nmodes, ldg, chunk, &a);
+    if (rc)
+        return rc;
+    return run_adjoint<T, SR>(tab, ldt, ncand, n_steps, dt, g, chunk, a, J, gs, ldg, st);
 }
 
 }  // namespace
@@ -921,6 +1058,11 @@ int pp_qke_sample_gradient(const double *A, const double *E, const double *Ed, i
     if (ldg < 2 * n_steps + 1)
         return fail(PP_ERR_INVALID_ARG, "ldg must be >= 2 n_steps + 1");
     return launch_qke_gradient(A, E, Ed, ncand, ld, n_steps, dt, grid, precision, J, g, ldg, (cudaStream_t)stream);
+}
+
+int64_t pp_set_qke_state_budget(int64_t bytes)
+{
+    return g_state_budget.exchange(bytes < 0 ? -1 : bytes);
 }
 
 int pp_qke_gradient(const double *params, int32_t ncand, const pp_field_spec *spec, const pp_grid *grid,

@@ -189,3 +189,15 @@ def test_surrogate_sizes_are_checked_on_the_host(pp):
         assert rc == pp.PP_ERR_INVALID_ARG and not h.value, hidden
     assert L.pp_mlp_create(0, 256, 256, ctypes.byref(h)) == pp.PP_ERR_INVALID_ARG
     assert L.pp_mlp_create(300, 256, 256, ctypes.byref(h)) == pp.PP_ERR_INVALID_ARG
+
+
+def test_qke_state_budget_is_a_host_setting(pp):
+    """pp_set_qke_state_budget returns the previous setting; a negative value selects
+    the default (half the device's memory), reported as -1.  No device work."""
+    old = pp.set_qke_state_budget(12345)
+    try:
+        assert pp.set_qke_state_budget(0) == 12345
+        assert pp.set_qke_state_budget(-7) == 0
+        assert pp.set_qke_state_budget(-1) == -1
+    finally:
+        pp.set_qke_state_budget(old)

@@ -290,10 +290,10 @@ def test_rejects_bad_arguments(pp):
 
 
 def test_chunked_gradient_equals_single_start_calls(pp):
-    """At the local-search size one start's checkpoints take ~0.8 GB, so 12 starts
-    exceed the adjoint's 8 GiB working budget and run in two chunks.  Every start's
-    work is independent and its sums run in a fixed order, so the batched J and
-    gradient equal those of single-start calls bit for bit."""
+    """At the local-search size one start's kept states take 6.5 GB, so with a 40 GiB
+    state budget the 12 starts run in several launches (six starts each at most).
+    Every start's work is independent and its sums run in a fixed order, so the
+    batched J and gradient equal those of single-start calls bit for bit."""
     cfg = inputs.LOCAL_SEARCH
     sp = dict(inputs.field_spec(dict(cfg, fluence=1.0)))
     Kf = cfg["K"]
@@ -303,12 +303,37 @@ def test_chunked_gradient_equals_single_start_calls(pp):
     X[:, :Kf] *= sc[:, None]
     X[:, 2 * Kf:3 * Kf] *= sc[:, None]
     Xd = dev(X)
-    J, gJ, U, dU = pp.qke_gradient(Xd, sp, cfg["grid"], "fp32")
-    assert pp.sync_status() == pp.PP_OK
-    for c in (0, 5, 9, 10, 11):
-        J1, g1, U1, dU1 = pp.qke_gradient(Xd[c:c + 1].contiguous(), sp, cfg["grid"], "fp32")
+    old = pp.set_qke_state_budget(40 << 30)
+    try:
+        J, gJ, U, dU = pp.qke_gradient(Xd, sp, cfg["grid"], "fp32")
         assert pp.sync_status() == pp.PP_OK
-        assert torch.equal(J[c:c + 1], J1) or (torch.isnan(J[c]) and torch.isnan(J1[0]))
-        assert torch.equal(gJ[c:c + 1], g1) or (torch.isnan(J[c]) and torch.isnan(J1[0]))
-        assert torch.equal(U[c:c + 1], U1) and torch.equal(dU[c:c + 1], dU1)
+        for c in (0, 5, 9, 10, 11):
+            J1, g1, U1, dU1 = pp.qke_gradient(Xd[c:c + 1].contiguous(), sp, cfg["grid"], "fp32")
+            assert pp.sync_status() == pp.PP_OK
+            assert torch.equal(J[c:c + 1], J1) or (torch.isnan(J[c]) and torch.isnan(J1[0]))
+            assert torch.equal(gJ[c:c + 1], g1) or (torch.isnan(J[c]) and torch.isnan(J1[0]))
+            assert torch.equal(U[c:c + 1], U1) and torch.equal(dU[c:c + 1], dU1)
+    finally:
+        pp.set_qke_state_budget(old)
     assert torch.isfinite(J).sum() >= 6
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_kept_and_recomputed_states_give_the_same_gradient(pp, precision):
+    """The adjoint keeps every step's state when the state budget allows and
+    otherwise recomputes all but every 8th (FP32) or 4th (FP64) step's; both walk
+    the same steps in the same groups, so J and the gradient are equal bit for bit.
+    2003 steps: ragged against the groups of 32 steps and against the segments."""
+    n = 2003
+    grid = inputs.small_grid(17, 9, 3)  # 459 modes: a partial CTA
+    X = params(2, 6)
+    A, E, Ed, _ = oracle.synth_raw(X, *ARGS, n)
+    dt = 20.0 / n
+    J1, g1 = pp.qke_sample_gradient(dev(A), dev(E), dev(Ed), dt, grid, precision)
+    old = pp.set_qke_state_budget(0)  # too small to keep every state: recompute, one start per launch
+    try:
+        J2, g2 = pp.qke_sample_gradient(dev(A), dev(E), dev(Ed), dt, grid, precision)
+    finally:
+        pp.set_qke_state_budget(old)
+    assert pp.sync_status() == pp.PP_OK
+    assert torch.isfinite(J1).all() and torch.equal(J1, J2) and torch.equal(g1, g2)
