@@ -475,12 +475,13 @@ def gemm_measure(pp, torch, reps=20):
     return out
 
 
-# FP32 work per mode-step of the QKE adjoint kernel (forward pass, recomputed
-# forward and backward step), from the kernel's executed instruction counts (ncu,
-# 7 starts x 16384 modes x 4096 steps): 278.4 FFMA + 252.6 FMUL + 125.6 FADD
-# thread-instructions, i.e. 935 flop (FMA = 2) in 657 FP32 instructions.
-QKE_ADJ_FLOP = 935
-QKE_ADJ_FP32_INSTR = 657
+# FP32 work per mode-step of the QKE adjoint kernel with every forward state kept
+# (forward step and backward step; the variant the default state budget selects at
+# the local-search size), from the kernel's executed instruction counts (ncu,
+# 7 starts x 16384 modes x 1024 steps): 219.0 FFMA + 157.1 FMUL + 71.0 FADD
+# thread-instructions, i.e. 666 flop (FMA = 2) in 447 FP32 instructions.
+QKE_ADJ_FLOP = 666
+QKE_ADJ_FP32_INSTR = 447
 
 
 def localsearch_main(args):
@@ -561,8 +562,8 @@ def localsearch_main(args):
                      "pipe_frac": QKE_ADJ_FP32_INSTR * mode_steps / (eval_ms * 1e-3)
                      / pk["fp32_lanes_per_s"],
                      "peak_source": pk["fp32_source"],
-                     "note": "%d FP32 flop (%d instructions) per mode-step from ncu SASS counts; "
-                             "whole evaluation (synthesis, adjoint, chain rule) timed"
+                     "note": "%d FP32 flop (%d instructions) per mode-step from ncu SASS counts of the "
+                             "kept-state adjoint; whole evaluation (synthesis, adjoint, chain rule) timed"
                              % (QKE_ADJ_FLOP, QKE_ADJ_FP32_INSTR)},
         "search": None if r is None else {
             "seconds": wall, "evals_total": int(r["evals"].sum()),
