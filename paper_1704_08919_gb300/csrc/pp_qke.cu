@@ -631,21 +631,22 @@ __global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 2 : 1) qke_adjoint
             }
         }
         __syncthreads();
-        // sample 2 n0g + 1 + kk: its seven terms summed over the warps (fixed
-        // order), then its sensitivity i from the sample's E and Ed
+        // sample 2 n0g + 1 + kk: each of its seven terms summed over the warps in
+        // fixed order (into warp 0's slot, which only this thread touches), then
+        // its six sensitivities from the sample's E and Ed
+        for (int t = threadIdx.x; t < 2 * cntg * kSensTerms; t += kQThreads) {
+            const int j = t / (2 * cntg), kk = t % (2 * cntg);
+            double acc = sb[0][kk][j];
+            for (int w = 1; w < kQWarps; ++w)
+                acc += sb[w][kk][j];
+            sb[0][kk][j] = acc;
+        }
+        __syncthreads();
         for (int t = threadIdx.x; t < 2 * cntg * 6; t += kQThreads) {
             const int i = t / (2 * cntg), kk = t % (2 * cntg);
-            double u[kSensTerms];
-#pragma unroll
-            for (int j = 0; j < kSensTerms; ++j) {
-                double acc = 0.0;
-                for (int w = 0; w < kQWarps; ++w)
-                    acc += sb[w][kk][j];
-                u[j] = acc;
-            }
             const QkeS<T> &e = seg[kk + 1];
             prow[(size_t)i * ldg + 2 * n0g + 1 + kk] =
-                sample_sens_from_sums(i, (double)e.ex, (double)e.ey, (double)e.edx, (double)e.edy, u);
+                sample_sens_from_sums(i, (double)e.ex, (double)e.ey, (double)e.edx, (double)e.edy, sb[0][kk]);
         }
         __syncthreads();
     }
