@@ -428,13 +428,15 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // a per-thread ring of kQRing shared-memory slots filled kQRing - 1 steps ahead by
 // cp.async (no recomputation).  S > 1: one state per S steps, and each segment is
 // recomputed into per-thread shared-memory slots before its backward steps.
-// The steps are handled in groups of kQGroupSteps: the samples of a group are
+// The steps are handled in groups of q_group_steps: the samples of a group are
 // staged into shared memory once, and the sample sensitivities of a whole group
-// are summed over the CTA's warps once, so a group costs four barriers whatever S
+// are summed over the CTA's warps once, so a group costs five barriers whatever S
 // is, and J and the gradient do not depend on S.  FP32: 2 CTAs per SM with up to
 // 128 registers (no spills; 3 CTAs per SM at 80 registers spilled in the backward
 // step and measured 2.9% slower).
-constexpr int kQGroupSteps = 32;
+// steps per group: 64 in FP32, 32 in FP64 (static shared memory stays under 48 KB)
+template <typename T>
+constexpr int q_group_steps() { return sizeof(T) == 4 ? 64 : 32; }
 constexpr int kQRing = 4;
 template <typename T, int S>
 __global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 2 : 1) qke_adjoint_kernel(const QkeS<T> *__restrict__ tab, int ldt, int n_steps,
@@ -442,11 +444,12 @@ __global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 2 : 1) qke_adjoint
                                                                 double *__restrict__ part, int ldg,
                                                                 double *__restrict__ partJ)
 {
-    static_assert(kQGroupSteps % S == 0, "a group holds whole segments");
-    constexpr int kQGroup = kQGroupSteps / S;  // segments per group
-    constexpr int GS = kQGroupSteps;           // steps per group
+    constexpr int GS = q_group_steps<T>();  // steps per group
+    static_assert(GS % S == 0, "a group holds whole segments");
+    constexpr int kQGroup = GS / S;  // segments per group
     __shared__ double red[kQWarps];
-    __shared__ double sb[kQWarps][2 * GS][kSensTerms];
+    __shared__ T sb[kQWarps][2 * GS][kSensTerms];       // per-warp sums of the terms
+    __shared__ double usum[2 * GS][kSensTerms];         // their sums over the warps
     __shared__ QkeS<T> seg[2 * GS + 1];  // the samples of the current group (broadcast reads)
     // per-thread state slots, sst[(q * 6 + i) * kQThreads + tid]: the segment's
     // recomputed states (S > 1) or the prefetch ring (S = 1, slot q = step % kQRing)
@@ -621,7 +624,7 @@ __global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 2 : 1) qke_adjoint
                     const int vi = (lane >> 1) & 15;
                     if ((lane & 1) == 0 && vi < 2 * kSensTerms)
                         sb[warp][vi < kSensTerms ? 2 * (so + q) + 1 : 2 * (so + q)]
-                          [vi < kSensTerms ? vi : vi - kSensTerms] = (double)tot;
+                          [vi < kSensTerms ? vi : vi - kSensTerms] = tot;
 #pragma unroll
                     for (int i = 0; i < 3; ++i)
                         pend[i] = nacc[i];
@@ -632,21 +635,20 @@ __global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 2 : 1) qke_adjoint
         }
         __syncthreads();
         // sample 2 n0g + 1 + kk: each of its seven terms summed over the warps in
-        // fixed order (into warp 0's slot, which only this thread touches), then
-        // its six sensitivities from the sample's E and Ed
+        // fixed order (FP64), then its six sensitivities from the sample's E and Ed
         for (int t = threadIdx.x; t < 2 * cntg * kSensTerms; t += kQThreads) {
             const int j = t / (2 * cntg), kk = t % (2 * cntg);
-            double acc = sb[0][kk][j];
+            double acc = (double)sb[0][kk][j];
             for (int w = 1; w < kQWarps; ++w)
-                acc += sb[w][kk][j];
-            sb[0][kk][j] = acc;
+                acc += (double)sb[w][kk][j];
+            usum[kk][j] = acc;
         }
         __syncthreads();
         for (int t = threadIdx.x; t < 2 * cntg * 6; t += kQThreads) {
             const int i = t / (2 * cntg), kk = t % (2 * cntg);
             const QkeS<T> &e = seg[kk + 1];
             prow[(size_t)i * ldg + 2 * n0g + 1 + kk] =
-                sample_sens_from_sums(i, (double)e.ex, (double)e.ey, (double)e.edx, (double)e.edy, sb[0][kk]);
+                sample_sens_from_sums(i, (double)e.ex, (double)e.ey, (double)e.edx, (double)e.edy, usum[kk]);
         }
         __syncthreads();
     }
@@ -658,13 +660,13 @@ __global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 2 : 1) qke_adjoint
         for (int i = 0; i < 6; ++i) {
             const T v = warp_sum(o[i]);
             if (lane == 0)
-                sb[warp][0][i] = (double)v;
+                sb[warp][0][i] = v;
         }
         __syncthreads();
         if (threadIdx.x < 6) {
             double acc = 0.0;
             for (int w = 0; w < kQWarps; ++w)
-                acc += sb[w][0][threadIdx.x];
+                acc += (double)sb[w][0][threadIdx.x];
             prow[(size_t)threadIdx.x * ldg] = acc;
         }
     }
