@@ -278,6 +278,7 @@ __global__ void samples_kernel(const double2 *__restrict__ coef, int M, int j0, 
 // polarisation l, candidate): dEP = (dJ/dE_j, dJ/dPhi_j) from dJ/d(samples)
 // g[c][q][k], q = (A_x, A_y, E_x, E_y, Ed_x, Ed_y).
 constexpr int kVjpThreads = 256;
+constexpr int kVjpResync = 32;
 __global__ void __launch_bounds__(kVjpThreads) vjp_modes_kernel(
     const double *__restrict__ params, int K, int order, double wmin, double wmax, double T, int j0,
     int n_steps, const double *__restrict__ g, int ldg, double2 *__restrict__ dEP)
@@ -310,14 +311,23 @@ __global__ void __launch_bounds__(kVjpThreads) vjp_modes_kernel(
     const double *gE = g + ((size_t)c * 6 + 2 + l) * ldg;
     const double *gD = g + ((size_t)c * 6 + 4 + l) * ldg;
     const long long two_n = 2ll * n_steps;
-    double dE = 0.0, dP = 0.0;
-    for (int k = threadIdx.x; k <= 2 * n_steps; k += kVjpThreads) {
-        double sa, ca;
-        sincospi((double)(((long long)j * k) % two_n) / (double)n_steps, &sa, &ca);
+    // (sin, cos)(pi j k / n) by rotation from sample to sample (stride kVjpThreads),
+    // recomputed exactly every kVjpResync samples
+    double sr, cr;
+    sincospi((double)(((long long)j * kVjpThreads) % two_n) / (double)n_steps, &sr, &cr);
+    const double iW = 1.0 / W, EjiW = Ej / W, EjW = Ej * W;
+    double dE = 0.0, dP = 0.0, sa = 0.0, ca = 1.0;
+    int it = 0;
+    for (int k = threadIdx.x; k <= 2 * n_steps; k += kVjpThreads, ++it) {
+        if (it % kVjpResync == 0)
+            sincospi((double)(((long long)j * k) % two_n) / (double)n_steps, &sa, &ca);
         const double ck = ca * cb + sa * sb, sk = sa * cb - ca * sb;
         const double ga = gA[k], ge = gE[k], gd = gD[k];
-        dE += ga * (-(sk - si) / W) + ge * ck + gd * (-W * sk);
-        dP += ga * (Ej * (ck - ci) / W) + ge * (Ej * sk) + gd * (Ej * W * ck);
+        dE += ga * (-(sk - si) * iW) + ge * ck + gd * (-W * sk);
+        dP += ga * ((ck - ci) * EjiW) + ge * (Ej * sk) + gd * (EjW * ck);
+        const double sn = fma(sa, cr, ca * sr);
+        ca = fma(ca, cr, -sa * sr);
+        sa = sn;
     }
     red[0][threadIdx.x] = dE;
     red[1][threadIdx.x] = dP;
@@ -400,16 +410,23 @@ __global__ void __launch_bounds__(kVjpThreads) hann_vjp_harmonics_kernel(
     const double *gE = g + ((size_t)c * 6 + 2 + l) * ldg;
     const double *gD = g + ((size_t)c * 6 + 4 + l) * ldg;
     const long long two_n = 2ll * n_steps;
-    double gre = 0.0, gim = 0.0;
-    for (int k = threadIdx.x; k <= 2 * n_steps; k += kVjpThreads) {
+    double sr, cr;  // rotation by kVjpThreads samples, as in vjp_modes_kernel
+    sincospi((double)(((long long)j * kVjpThreads) % two_n) / (double)n_steps, &sr, &cr);
+    const double iW = j ? 1.0 / W : 0.0;
+    double gre = 0.0, gim = 0.0, sz = 0.0, cz = 1.0;
+    int it = 0;
+    for (int k = threadIdx.x; k <= 2 * n_steps; k += kVjpThreads, ++it) {
         const double ga = gA[k], ge = gE[k], gd = gD[k];
         if (j == 0) {
             gre += ga * ((double)(2 * n_steps - k) * h) + ge;
         } else {
-            double sz, cz;
-            sincospi((double)(((long long)j * k) % two_n) / (double)n_steps, &sz, &cz);
-            gre += ga * (-sz / W) + ge * cz + gd * (-W * sz);
-            gim += ga * (-(cz - 1.0) / W) + ge * (-sz) + gd * (-W * cz);
+            if (it % kVjpResync == 0)
+                sincospi((double)(((long long)j * k) % two_n) / (double)n_steps, &sz, &cz);
+            gre += ga * (-sz * iW) + ge * cz + gd * (-W * sz);
+            gim += ga * (-(cz - 1.0) * iW) + ge * (-sz) + gd * (-W * cz);
+            const double sn = fma(sz, cr, cz * sr);
+            cz = fma(cz, cr, -sz * sr);
+            sz = sn;
         }
     }
     red[0][threadIdx.x] = gre;
