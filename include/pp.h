@@ -76,16 +76,20 @@ typedef enum {
  *  PP_MAGNUS4 fourth-order Magnus step exp(Omega), Omega = -i dt/6 (H_0 + 4 H_h +
  *             H_1) + dt^2/12 [H_0, H_1]: unitary; the fourth-order scheme the
  *             paper's outlook (Sec. V.C.2) calls for.  On each 2-level system the
- *             step is exp(-i th n.sigma) with th = |dt h_eff|; cos th - 1 and
- *             sin th / th come from even polynomials, which hold (to FP32/FP64
- *             rounding) for th <= 0.2.  The step table bounds th per step over the
- *             whole momentum grid (corner momenta and the step's potential terms);
- *             every tile of steps in which that bound exceeds 0.2 takes an
- *             argument-halved form instead (th halved k times into the range, the
- *             polynomials there, k double-angle steps back), which is exact for th
- *             up to 0.2 * 2^60 and costs about 2k more instructions per step.  The
- *             workloads here stay near th = 0.11-0.14 (dt ~ 0.02, |p| <= 2.5), where
- *             only the polynomials run.
+ *             step is exp(-i th n.sigma) with th = |dt h_eff|, from even
+ *             polynomials in th that hold (to FP32/FP64 rounding) for th <= 0.2:
+ *             in FP32 the step is taken as (cos th)^-1 exp(-i th n.sigma) =
+ *             1 - i tan th n.sigma (tan th / th one polynomial) and the state's
+ *             norm, which then grows, is divided out at the projection (power-of-
+ *             two rescaling between tiles keeps it in range exactly); in FP64
+ *             cos th - 1 and sin th / th are used.  The step table bounds th per
+ *             step over the whole momentum grid (corner momenta and the step's
+ *             potential terms); a candidate with any step beyond 0.2 takes, for all
+ *             its steps, an argument-halved form instead (th halved k times into
+ *             the range, cos th - 1 and sin th / th there, k double-angle steps
+ *             back), which is exact for th up to 0.2 * 2^60 and costs about 2k more
+ *             instructions per step.  The workloads here stay near th = 0.11-0.14
+ *             (dt ~ 0.02, |p| <= 2.5), where only the polynomials run.
  *  PP_SPLIT2  second-order Strang split operator, the paper's own integrator
  *             (Sec. II.A): free part alpha.p + beta (two half steps), coupling
  *             -alpha.A(t_n + dt/2) (one full step), each factor an exact
