@@ -38,8 +38,8 @@ CFG = inputs.DE_BATCH
 #  magnus4: dt h_eff, |.|^2, tan(th)/th polynomial (FP32, tracked norm; FP64: cos-1 and
 #           sinc polynomials), scaled vector, increment, Fast2Sum
 #  split2:  coupling factor, stage, free factor, Fast2Sum
-WORK = {("fp32", "rk4"): (268, 184), ("fp32", "magnus4"): (120, 86), ("fp32", "split2"): (144, 96),
-        ("fp32fast", "rk4"): (244, 160), ("fp32fast", "magnus4"): (96, 54),
+WORK = {("fp32", "rk4"): (268, 184), ("fp32", "magnus4"): (116, 84), ("fp32", "split2"): (144, 96),
+        ("fp32fast", "rk4"): (244, 160), ("fp32fast", "magnus4"): (92, 52),
         ("fp32fast", "split2"): (112, 64),
         ("fp64", "rk4"): (244, 148), ("fp64", "magnus4"): (114, 64), ("fp64", "split2"): (112, 64)}
 # DRAM bytes per candidate per launch of the propagation kernel, from ncu captures
