@@ -43,8 +43,8 @@ WORK = {("fp32", "rk4"): (268, 184), ("fp32", "magnus4"): (116, 84), ("fp32", "s
         ("fp32fast", "split2"): (112, 64),
         ("fp64", "rk4"): (244, 148), ("fp64", "magnus4"): (114, 64), ("fp64", "split2"): (112, 64)}
 # DRAM bytes per candidate per launch of the propagation kernel, from ncu captures
-# (profiles/): the FP32-fast Magnus kernel (256 threads, 8 KiB tiles) read 1.09696 MB for 4 candidates.
-TRAFFIC_PER_CAND = {("fp32fast", "magnus4"): 1.09696e6 / 4}
+# (profiles/): the FP32-fast Magnus kernel (256 threads, 8 KiB tiles) read 1.090816 MB for 4 candidates.
+TRAFFIC_PER_CAND = {("fp32fast", "magnus4"): 1.090816e6 / 4}
 FP32_LANES_PER_SM = 128
 # GB300 FP64 rate from the part's datasheet figure (no measured FP64 peak exists
 # for this pool); FP32 is derived from the device's SM count and maximum clock.
@@ -1087,7 +1087,7 @@ def main():
         "traffic": (TRAFFIC_PER_CAND[(args.precision, args.scheme)] * NP
                     if (args.precision, args.scheme) in TRAFFIC_PER_CAND else None),
         "traffic_source": ("dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of this kernel "
-                           "at 4 candidates (1.097 MB, nothing written), scaled by candidates: the "
+                           "at 4 candidates (1.091 MB, nothing written), scaled by candidates: the "
                            "per-candidate step table is read from DRAM once, every other access hits L2"
                            if (args.precision, args.scheme) in TRAFFIC_PER_CAND else None)}
 
