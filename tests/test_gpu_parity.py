@@ -474,6 +474,33 @@ def test_magnus_beyond_the_series_range(pp, target, precision):
         assert abs(N[0] / No - 1) < 1e-4
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp32fast"])
+def test_magnus_fp32_tracked_norm_over_many_tiles(pp, precision):
+    # The FP32 series step applies exp(-i H.sigma) / cos th, so the state grows by
+    # 1 / cos th per step: here th ~ 0.19 for ~2600 steps (a growth of ~1e21 without
+    # the power-of-two rescaling between tiles, past the FP32 range in its square).
+    # N must match the oracle twin, and the rescaling, being exact, must not show:
+    # every launch configuration (tiles of 256 or 1024 steps) gives the same N bit for bit.
+    grid = inputs.small_grid(6, 5, 3, ext=1.3)
+    dt, T = 0.05, 312.0
+    for _ in range(3):
+        ns = int(round(T / dt))
+        A, _, _ = oracle.gaussian_rotating_field(0.3, 0.9, 3.0, -0.5 * ns * dt, dt / 2, 2 * ns + 1)
+        dt *= 0.19 / magnus_theta_bound(A, dt, grid)
+    ns = int(round(T / dt))
+    A, _, _ = oracle.gaussian_rotating_field(0.3, 0.9, 3.0, -0.5 * ns * dt, dt / 2, 2 * ns + 1)
+    assert ns > 2000 and abs(magnus_theta_bound(A, dt, grid) - 0.19) < 0.01
+    No = weighted_N(grid, oracle.dirac_magnus_modes(A, ns, dt, inputs.grid_points(grid))[0])
+    At = torch.tensor(A[None], device=DEV)
+    pp.clear_tuning()
+    N0, _ = pp.pair_number(At, dt, grid, precision=precision, scheme="magnus4")
+    _, ms, N_last = pp.tune_pair_number(At, dt, grid, precision=precision, scheme="magnus4")
+    assert pp.sync_status() == pp.PP_OK
+    pp.clear_tuning()
+    assert np.isfinite(N0.item()) and abs(N0.item() / No - 1) < 1e-4
+    assert torch.equal(N0, N_last)
+
+
 @pytest.mark.parametrize("precision,scheme", [("fp32", "magnus4"), ("fp32fast", "magnus4"),
                                               ("fp32", "rk4"), ("fp32fast", "split2"),
                                               ("fp64", "rk4")])
