@@ -104,8 +104,9 @@ def parse():
 def device_peaks(local):
     """ALU peaks of this GPU for the roofline: FP32 = SMs (read from the device) x 128
     lanes x 2 flop x the maximum SM clock (nvidia-smi clocks.max.sm, else the clock
-    recorded in MEASURED_PEAKS.json); FP64 = the nominal datasheet figure.  Neither
-    is a measured peak: MEASURED_PEAKS.json holds HBM and BF16 figures only."""
+    recorded in MEASURED_PEAKS.json); FP64 = the nominal datasheet figure
+    (MEASURED_PEAKS.json holds HBM and BF16 figures only).  Beside them, the FMA
+    rates this GPU sustains in FP32 and FP64, measured by pp_fma_rate."""
     import torch
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     clk, src = None, None
@@ -123,12 +124,27 @@ def device_peaks(local):
         except (OSError, KeyError, ValueError):
             clk, src = 2070.0, "GB300 maximum SM clock (datasheet)"
     fp32 = sms * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12
+    if local not in _FMA_RATES:  # the FMA rate this GPU sustains, measured once per process
+        import paper_1704_08919_gb300 as pp
+        _FMA_RATES[local] = (pp.fma_rate("fp32") / 1e12, pp.fma_rate("fp64") / 1e12)
+    m32, m64 = _FMA_RATES[local]
     return {"sm_count": sms, "sm_max_mhz": clk, "fp32_tflops": fp32, "fp64_tflops": FP64_NOMINAL_TFLOPS,
             "fp32_lanes_per_s": sms * FP32_LANES_PER_SM * clk * 1e6,
             "fp32_source": "nominal, derived: %d SMs (device) x %d FP32 lanes x 2 flop x %g MHz (%s)"
                            % (sms, FP32_LANES_PER_SM, clk, src),
-            "fp64_source": "nominal: GB300 FP64 %.2f TFLOP/s datasheet figure (no measured FP64 peak)"
-                           % FP64_NOMINAL_TFLOPS}
+            "fp64_source": "nominal: GB300 FP64 %.2f TFLOP/s datasheet figure" % FP64_NOMINAL_TFLOPS,
+            "fp32_measured_tflops": m32, "fp64_measured_tflops": m64,
+            "measured_source": "pp_fma_rate: a kernel of independent FMA chains only, a multiple of the SM "
+                               "count in CTAs, timed with CUDA events in this process"}
+
+
+_FMA_RATES = {}
+
+
+def measured_peak(peaks, fp32, achieved):
+    """Roofline fields against the FMA rate measured on this GPU (beside the derived peak)."""
+    m = peaks["fp32_measured_tflops"] if fp32 else peaks["fp64_measured_tflops"]
+    return {"peak_measured": m, "frac_of_measured": achieved / m, "peak_measured_source": peaks["measured_source"]}
 
 
 def dist_env():
@@ -367,6 +383,7 @@ def measure_uneven(pp, torch, local, peaks, G, precision="fp32fast", scheme="mag
            "roofline": {"bound": "alu", "kernel": "propagate_batch_kernel<%s>" % scheme,
                         "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
                         "peak_source": peaks["fp32_source"] if fp32 else peaks["fp64_source"],
+                        **measured_peak(peaks, fp32, achieved),
                         "flop_per_mode_step": flop,
                         "note": "whole graph timed (proposal, synthesis, tables, propagation, selection)"},
            # per generation: proposal, spectrum, samples, table, propagation (+ its
@@ -563,6 +580,7 @@ def localsearch_main(args):
                      "pipe_frac": QKE_ADJ_FP32_INSTR * mode_steps / (eval_ms * 1e-3)
                      / pk["fp32_lanes_per_s"],
                      "peak_source": pk["fp32_source"],
+                     **measured_peak(pk, True, achieved),
                      "note": "%d FP32 flop (%d instructions) per mode-step from ncu SASS counts of the "
                              "kept-state adjoint; whole evaluation (synthesis, adjoint, chain rule) timed"
                              % (QKE_ADJ_FLOP, QKE_ADJ_FP32_INSTR)},
@@ -739,6 +757,7 @@ def measure_single(pp, torch, local, peaks, steps=10, warmup=3, tune=True, with_
            "roofline": {"bound": "alu", "kernel": "propagate_kernel<rk4, double>", "achieved": achieved,
                         "peak": peaks["fp64_tflops"], "unit": "TFLOP/s",
                         "frac": achieved / peaks["fp64_tflops"], "peak_source": peaks["fp64_source"],
+                        **measured_peak(peaks, False, achieved),
                         "flop_per_mode_step": flop,
                         "note": "whole solve timed (table build, propagation, momentum sum)"},
            "launch_tuning": tuned, "clocks": clk,
@@ -934,6 +953,7 @@ def measure_de_batch_fp64(pp, torch, local, peaks, pop, fit, seed, gen, lo_t, hi
             "roofline": {"bound": "alu", "kernel": "propagate_kernel<rk4, double>", "achieved": achieved,
                          "peak": peaks["fp64_tflops"], "unit": "TFLOP/s",
                          "frac": achieved / peaks["fp64_tflops"], "peak_source": peaks["fp64_source"],
+                         **measured_peak(peaks, False, achieved),
                          "flop_per_mode_step": flop, "launch_ms": per_launch,
                          "kernel_share_of_step": kern_ms / ms},
             "l2": "flushed before the generation (256 MiB write)",
@@ -1080,6 +1100,7 @@ def main():
         "fp32": "float, compensated", "fp32fast": "float", "fp64": "double"}[args.precision]),
         "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
         "frac": achieved / peak, "peak_source": peak_src,
+        **measured_peak(peaks, args.precision in ("fp32", "fp32fast"), achieved),
         "flop_per_mode_step": flop, "inst_per_mode_step": inst,
         "pipe_frac": inst * units / (per_launch_ms / 1000.0) / lanes,
         "launch_ms": per_launch_ms,
@@ -1229,7 +1250,8 @@ def main():
             "clocks": clk,
             "wall_s_timed": t_wall,
             "step_ms": step_ms,
-            "peaks": {k: peaks[k] for k in ("sm_count", "sm_max_mhz", "fp32_tflops", "fp64_tflops")},
+            "peaks": {k: peaks[k] for k in ("sm_count", "sm_max_mhz", "fp32_tflops", "fp64_tflops",
+                                            "fp32_measured_tflops", "fp64_measured_tflops")},
             "configs": configs,
         }
         print(json.dumps(line), flush=True)

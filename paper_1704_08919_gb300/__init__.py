@@ -50,7 +50,7 @@ EXPORTS = ("pp_synth_field", "pp_pair_number", "pp_de_propose", "pp_de_select", 
            "pp_mlp_log_targets", "pp_mlp_init", "pp_al_search", "pp_synth_field_raw",
            "pp_synth_vjp", "pp_qke_pair_number", "pp_qke_sample_gradient", "pp_qke_gradient",
            "pp_local_search", "pp_release_scratch", "pp_pair_number_grids",
-           "pp_set_qke_state_budget")
+           "pp_set_qke_state_budget", "pp_fma_rate")
 
 
 class ALOptions(ctypes.Structure):
@@ -110,6 +110,7 @@ def lib():
         L.pp_set_wait_limit.restype = ctypes.c_int64
         L.pp_set_qke_state_budget.argtypes = [ctypes.c_int64]
         L.pp_set_qke_state_budget.restype = ctypes.c_int64
+        L.pp_fma_rate.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
         L.pp_set_skip_copies.argtypes = [ctypes.c_int]
         L.pp_last_error.restype = ctypes.c_char_p
         L.pp_profile_end.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
@@ -567,6 +568,13 @@ def set_wait_limit(limit):
 
 def set_skip_copies(skip):
     return lib().pp_set_skip_copies(int(skip))
+
+
+def fma_rate(precision="fp32", stream=None):
+    """pp_fma_rate: the FMA rate this GPU sustains in flop/s (the roofline denominator)."""
+    out = ctypes.c_double(0.0)
+    _check(lib().pp_fma_rate(PRECISIONS[precision], ctypes.byref(out), _stream(stream)))
+    return out.value
 
 
 def set_qke_state_budget(nbytes):

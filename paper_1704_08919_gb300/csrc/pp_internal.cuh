@@ -30,7 +30,7 @@ void clear_error();
 enum ScratchSlot {
     SCR_TABLE = 0, SCR_PARTIAL, SCR_A, SCR_TRIAL, SCR_TFIT, SCR_COEF,
     SCR_SCREEN_PROPS, SCR_SCREEN_X, SCR_SCREEN_Y, SCR_SCREEN_KEPT,
-    SCR_VJP, SCR_QKE_TABLE, SCR_QKE_CKPT, SCR_QKE_PART, SCR_QKE_G, SCR_QKE_FIELD, SCR_QKE_X, SCR_GRIDS,
+    SCR_VJP, SCR_QKE_TABLE, SCR_QKE_CKPT, SCR_QKE_PART, SCR_QKE_G, SCR_QKE_FIELD, SCR_QKE_X, SCR_GRIDS, SCR_RATE,
     SCR_NSLOTS
 };
 int scratch(int slot, size_t bytes, void **ptr);

@@ -201,3 +201,12 @@ def test_qke_state_budget_is_a_host_setting(pp):
         assert pp.set_qke_state_budget(-1) == -1
     finally:
         pp.set_qke_state_budget(old)
+
+
+def test_fma_rate_arguments_are_checked_on_the_host(pp):
+    """Refused before any device work: an unknown precision and a NULL output."""
+    L = pp.lib()
+    out = ctypes.c_double(0.0)
+    assert L.pp_fma_rate(7, ctypes.byref(out), None) == pp.PP_ERR_INVALID_ARG
+    assert b"precision" in L.pp_last_error()
+    assert L.pp_fma_rate(pp.PP_FP32, None, None) == pp.PP_ERR_INVALID_ARG
