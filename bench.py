@@ -84,8 +84,9 @@ def parse():
                          "(default: the library's, half the device memory)")
     ap.add_argument("--qke-steps", type=int, default=None,
                     help="localsearch: RK4 steps per pulse instead of the workload's 16384 (profiling runs)")
-    ap.add_argument("--screen", default="individual", choices=["individual", "global"],
-                    help="surrogate: screening mode reported as the value")
+    ap.add_argument("--screen", default="global", choices=["individual", "global"],
+                    help="surrogate: screening mode reported as the value (default: global, the top NP "
+                         "of all 8 NP proposals kept for exact scoring)")
     ap.add_argument("--online", type=int, default=0,
                     help="surrogate: also run a screened DE refitted every N generations (0: off)")
     ap.add_argument("--ncand", type=int, default=CFG["NP"],
