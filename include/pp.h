@@ -470,8 +470,9 @@ int pp_profile_end(double *total_ms, int64_t *launches);
  * precision PP_FP64 or PP_FP32 (PP_FP32_FAST is the same): a kernel of eight
  * independent FMA chains per thread and nothing else, a multiple of the SM count
  * in CTAs, timed with CUDA events on `stream` after one untimed launch (about 6 ms
- * for FP64 and 12 ms for FP32 on a GB300).  The denominator of the roofline
- * fractions of the ALU-bound kernels.  Synchronous: waits for its own events.
+ * for FP64 and 12 ms for FP32 on a GB300): a measured denominator for the
+ * roofline fractions of the ALU-bound kernels.  Synchronous: waits for its own
+ * events.
  * Errors: PP_ERR_INVALID_ARG (precision, NULL output), PP_ERR_CUDA. */
 int pp_fma_rate(int32_t precision, double *flop_per_s, void *stream);
 
