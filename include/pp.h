@@ -20,7 +20,7 @@
  *    non-finite result, a zero-fluence pulse) are recorded in a device status
  *    word and returned by pp_sync_status().
  *  - The library keeps a private per-device scratch area (the per-step field
- *    table of pp_pair_number, the per-block partial sums, the QKE checkpoints,
+ *    table of pp_pair_number, the per-block partial sums, the QKE forward states,
  *    the screening buffers).  It grows on demand with cudaMalloc after a device
  *    synchronisation; call an entry point once with the largest sizes before
  *    capturing it in a CUDA graph.  Because the scratch is per device, work that
