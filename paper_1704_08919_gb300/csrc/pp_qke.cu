@@ -129,6 +129,18 @@ __device__ __forceinline__ void nmul(const Coef<T> &c, const T v[6], T out[6])
     out[5] = -c.Q * v[4];
 }
 
+// out = base - N v, each component one chain of FMAs (N as in nmul).
+template <typename T>
+__device__ __forceinline__ void nmul_sub(const Coef<T> &c, const T v[6], const T base[6], T out[6])
+{
+    out[0] = fma(c.Q, v[1], base[0]);
+    out[1] = fma(-c.R, v[3], fma(c.W2, v[2], fma(-c.Q, v[0], base[1])));
+    out[2] = fma(c.R, v[4], fma(-c.W2, v[1], base[2]));
+    out[3] = fma(-c.W2, v[4], fma(c.R, v[1], base[3]));
+    out[4] = fma(-c.Q, v[5], fma(c.W2, v[3], fma(-c.R, v[2], base[4])));
+    out[5] = fma(c.Q, v[4], base[5]);
+}
+
 // One RK4 step of delta: chi = e_1 + delta.
 template <typename T>
 __device__ __forceinline__ void rk4_step(T d[6], const Coef<T> &c0, const Coef<T> &ch, const Coef<T> &c1, T dt)
@@ -609,10 +621,7 @@ __global__ void __launch_bounds__(kQThreads, sizeof(T) == 4 ? 2 : 1) qke_adjoint
                     }
                     T nacc[3] = {0, 0, 0};
                     coef_adj(kb1, x, nacc);  // k1 = N0 (e1 + x)
-                    nmul<false>(c0, kb1, yb);
-#pragma unroll
-                    for (int i = 0; i < 6; ++i)
-                        bar[i] = xb[i] - yb[i];
+                    nmul_sub(c0, kb1, xb, bar);
                     // emit samples 2n+2 (terms 0..6, slot 2q+1) and 2n+1 (terms 7..13, slot 2q)
                     T o[16];
                     sens_from(b1, e1, eperp, pend, o);
