@@ -497,10 +497,10 @@ def gemm_measure(pp, torch, reps=20):
 # FP32 work per mode-step of the QKE adjoint kernel with every forward state kept
 # (forward step and backward step; the variant the default state budget selects at
 # the local-search size), from the kernel's executed instruction counts (ncu,
-# 7 starts x 16384 modes x 1024 steps): 219.0 FFMA + 157.1 FMUL + 71.0 FADD
-# thread-instructions, i.e. 666 flop (FMA = 2) in 447 FP32 instructions.
+# 7 starts x 16384 modes x 1024 steps): 223.0 FFMA + 153.1 FMUL + 67.0 FADD
+# thread-instructions, i.e. 666 flop (FMA = 2) in 443 FP32 instructions.
 QKE_ADJ_FLOP = 666
-QKE_ADJ_FP32_INSTR = 447
+QKE_ADJ_FP32_INSTR = 443
 
 
 def localsearch_main(args):
